@@ -1,0 +1,259 @@
+"""FP64 CPU oracle of the active lattice Boltzmann update (arXiv:1902.00530).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  It shares no code
+with the CUDA path (``paper_1902_00530_gb300``) and never imports it.
+
+The arithmetic lives in ``lbm_oracle.c`` (plain C, compiled with gcc at
+``-O2 -ffp-contract=off`` so no fused multiply-adds change its rounding on any
+host).  This module only compiles it, loads it with ctypes and moves numpy
+arrays in and out.  Populations are numpy arrays of shape (9, ny, nx).
+
+Functions and the passages they follow:
+  step / run          App. A.2 (steps 1-6), Eq. (fevolution2)
+  equilibrium         Eq. (fssD2Q7), D2Q9 form with c_s^2 = 1/3
+  negative_correction App. A.3
+  gradient            Sec. 3 isotropic stencil, lattice-general form
+  ustar               Eqs. (bu_mips), (bu_CIL), (U0) and the U_max clamp
+  init                App. C.2 initialisation (f = f^SS of seeded rho, u)
+  observables         Eq. (phi); App. D (rho_y std, zeta)
+  noise_variates      Eq. (noiseDensityConservation) draws, Philox4x32-10
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lbm_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LOCK = threading.Lock()
+_LIBS: dict[int, ctypes.CDLL] = {}
+
+MODELS = {"passive": 0, "mips": 1, "cil": 2}
+
+
+class OrcParams(ctypes.Structure):
+    _fields_ = [
+        ("tau", ctypes.c_double),
+        ("sigma", ctypes.c_double),
+        ("C", ctypes.c_double),
+        ("rho_star", ctypes.c_double),
+        ("u_max", ctypes.c_double),
+        ("A", ctypes.c_double),
+        ("B", ctypes.c_double),
+    ]
+
+
+def _lib_path(bits: int) -> str:
+    return os.path.join(_BUILD, f"liblbm_oracle{bits}.so")
+
+
+def build(force: bool = False) -> None:
+    """Compile the FP64 and FP32 builds of the oracle with gcc."""
+    os.makedirs(_BUILD, exist_ok=True)
+    for bits, real in ((64, "double"), (32, "float")):
+        out = _lib_path(bits)
+        if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(_SRC):
+            continue
+        tmp = out + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", f"-DREAL={real}",
+               "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, out)
+
+
+def _lib(bits: int = 64) -> ctypes.CDLL:
+    with _LOCK:
+        if bits in _LIBS:
+            return _LIBS[bits]
+        build()
+        lib = ctypes.CDLL(_lib_path(bits))
+        real_p = ctypes.POINTER(ctypes.c_double if bits == 64 else ctypes.c_float)
+        dbl_p = ctypes.POINTER(ctypes.c_double)
+        u32, u64, i32, i64 = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int, ctypes.c_int64
+        prm = ctypes.POINTER(OrcParams)
+        lib.orc_step.argtypes = [real_p, real_p, i32, i32, i32, prm, u64, u32, u32]
+        lib.orc_step.restype = i32
+        lib.orc_run.argtypes = [real_p, i32, i32, i32, prm, u64, u32, i64, u32]
+        lib.orc_run.restype = i32
+        lib.orc_init.argtypes = [real_p, i32, i32, u64, u32, ctypes.c_double, ctypes.c_double,
+                                 i32, ctypes.c_double, ctypes.c_double, ctypes.c_double, prm]
+        lib.orc_init.restype = None
+        lib.orc_from_moments.argtypes = [real_p, i32, i32, dbl_p, dbl_p, dbl_p]
+        lib.orc_moments.argtypes = [real_p, i32, i32, dbl_p, dbl_p, dbl_p]
+        lib.orc_observables.argtypes = [real_p, i32, i32, ctypes.c_double, dbl_p]
+        lib.orc_observables.restype = i32
+        lib.orc_equilibrium.argtypes = [ctypes.c_double if bits == 64 else ctypes.c_float] * 3 + [real_p]
+        lib.orc_negative_correction.argtypes = [real_p, ctypes.c_double if bits == 64 else ctypes.c_float]
+        lib.orc_negative_correction.restype = i32
+        lib.orc_gradient.argtypes = [real_p, i32, i32, i32, i32, real_p]
+        rl = ctypes.c_double if bits == 64 else ctypes.c_float
+        lib.orc_ustar.argtypes = [i32, prm, rl, rl, rl, real_p, real_p]
+        lib.orc_philox4x32_10.argtypes = [ctypes.POINTER(u32), ctypes.POINTER(u32), ctypes.POINTER(u32)]
+        lib.orc_noise_variates.argtypes = [u64, u32, u32, u32, u32, dbl_p]
+        lib.orc_init_uniforms.argtypes = [u64, u32, u32, u32, dbl_p]
+        lib.orc_real_bytes.restype = i32
+        assert lib.orc_real_bytes() * 8 == bits
+        _LIBS[bits] = lib
+        return lib
+
+
+def _dtype(bits: int):
+    return np.float64 if bits == 64 else np.float32
+
+
+def _ptr(a: np.ndarray, ctype):
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def _rp(a: np.ndarray, bits: int):
+    return _ptr(a, ctypes.c_double if bits == 64 else ctypes.c_float)
+
+
+def params(tau=1.0, sigma=0.0, C=0.0, rho_star=1.0, u_max=1.0, A=0.0, B=0.0, **_ignored) -> OrcParams:
+    return OrcParams(tau, sigma, C, rho_star, u_max, A, B)
+
+
+def _check_f(f: np.ndarray, bits: int) -> None:
+    if f.ndim != 3 or f.shape[0] != 9:
+        raise ValueError("populations must have shape (9, ny, nx)")
+    if f.dtype != _dtype(bits) or not f.flags.c_contiguous:
+        raise ValueError(f"populations must be C-contiguous {_dtype(bits).__name__}")
+
+
+def init(nx: int, ny: int, seed: int, lattice_id: int = 0, rho_mean: float = 1.0,
+         rho_amp: float = 0.0, u_kind: int = 0, u_amp: float = 0.0, ux0: float = 0.0,
+         uy0: float = 0.0, prm: OrcParams | None = None, bits: int = 64) -> np.ndarray:
+    """Seeded initial populations f = f^SS(rho, u) (App. C.2)."""
+    lib = _lib(bits)
+    f = np.empty((9, ny, nx), dtype=_dtype(bits))
+    lib.orc_init(_rp(f, bits), nx, ny, seed, lattice_id, rho_mean, rho_amp, u_kind, u_amp,
+                 ux0, uy0, ctypes.byref(prm if prm is not None else params()))
+    return f
+
+
+def from_moments(rho: np.ndarray, ux: np.ndarray, uy: np.ndarray, bits: int = 64) -> np.ndarray:
+    """f_i = xi_i(rho, u) per site for given (ny, nx) moment fields."""
+    lib = _lib(bits)
+    rho, ux, uy = (np.ascontiguousarray(a, dtype=np.float64) for a in (rho, ux, uy))
+    ny, nx = rho.shape
+    f = np.empty((9, ny, nx), dtype=_dtype(bits))
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.orc_from_moments(_rp(f, bits), nx, ny, _ptr(rho, ctypes.c_double),
+                         _ptr(ux, ctypes.c_double), _ptr(uy, ctypes.c_double))
+    del dp
+    return f
+
+
+def step(f: np.ndarray, model: str, prm: OrcParams, seed: int, t: int, lattice_id: int = 0,
+         bits: int = 64) -> np.ndarray:
+    """One step t -> t+1 (App. A.2); returns new populations."""
+    _check_f(f, bits)
+    lib = _lib(bits)
+    out = np.empty_like(f)
+    rc = lib.orc_step(_rp(f, bits), _rp(out, bits), f.shape[2], f.shape[1], MODELS[model],
+                      ctypes.byref(prm), seed, t, lattice_id)
+    if rc != 0:
+        raise MemoryError("oracle step failed")
+    return out
+
+
+def run(f: np.ndarray, model: str, prm: OrcParams, seed: int, t0: int, nsteps: int,
+        lattice_id: int = 0, bits: int = 64) -> np.ndarray:
+    """nsteps steps from t0 (returns a new array; the input is untouched)."""
+    g = np.array(f, dtype=_dtype(bits), order="C", copy=True)
+    _check_f(g, bits)
+    lib = _lib(bits)
+    rc = lib.orc_run(_rp(g, bits), g.shape[2], g.shape[1], MODELS[model], ctypes.byref(prm),
+                     seed, t0, nsteps, lattice_id)
+    if rc != 0:
+        raise MemoryError("oracle run failed")
+    return g
+
+
+def moments(f: np.ndarray, bits: int | None = None):
+    """(rho, ux, uy) as float64 (ny, nx) arrays."""
+    bits = 64 if f.dtype == np.float64 else 32
+    _check_f(f, bits)
+    lib = _lib(bits)
+    ny, nx = f.shape[1:]
+    rho, ux, uy = (np.empty((ny, nx)) for _ in range(3))
+    lib.orc_moments(_rp(f, bits), nx, ny, _ptr(rho, ctypes.c_double),
+                    _ptr(ux, ctypes.c_double), _ptr(uy, ctypes.c_double))
+    return rho, ux, uy
+
+
+OBS_NAMES = ("mass", "phi", "drho_y", "drho_x", "var_rho", "zeta")
+
+
+def observables(f: np.ndarray, B: float = 0.0) -> dict:
+    """mass, phi (Eq. (phi)), drho_y / drho_x (App. D), var_rho, zeta (App. D)."""
+    bits = 64 if f.dtype == np.float64 else 32
+    _check_f(f, bits)
+    lib = _lib(bits)
+    out = np.zeros(6)
+    rc = lib.orc_observables(_rp(f, bits), f.shape[2], f.shape[1], B, _ptr(out, ctypes.c_double))
+    if rc != 0:
+        raise MemoryError("oracle observables failed")
+    return dict(zip(OBS_NAMES, out.tolist()))
+
+
+def equilibrium(rho: float, ux: float, uy: float, bits: int = 64) -> np.ndarray:
+    lib = _lib(bits)
+    out = np.empty(9, dtype=_dtype(bits))
+    lib.orc_equilibrium(rho, ux, uy, _rp(out, bits))
+    return out
+
+
+def negative_correction(f9, rho: float, bits: int = 64):
+    """Returns (corrected copy, changed flag) (App. A.3)."""
+    lib = _lib(bits)
+    g = np.array(f9, dtype=_dtype(bits), copy=True)
+    changed = lib.orc_negative_correction(_rp(g, bits), rho)
+    return g, bool(changed)
+
+
+def gradient(rho: np.ndarray, x: int, y: int, bits: int = 64) -> np.ndarray:
+    lib = _lib(bits)
+    r = np.ascontiguousarray(rho, dtype=_dtype(bits))
+    g = np.empty(2, dtype=_dtype(bits))
+    lib.orc_gradient(_rp(r, bits), r.shape[1], r.shape[0], x, y, _rp(g, bits))
+    return g
+
+
+def ustar(model: str, prm: OrcParams, rho: float, ux: float, uy: float, g=(0.0, 0.0),
+          bits: int = 64) -> np.ndarray:
+    lib = _lib(bits)
+    ga = np.array(g, dtype=_dtype(bits))
+    us = np.empty(2, dtype=_dtype(bits))
+    lib.orc_ustar(MODELS[model], ctypes.byref(prm), rho, ux, uy, _rp(ga, bits), _rp(us, bits))
+    return us
+
+
+def philox4x32_10(ctr, key) -> np.ndarray:
+    lib = _lib(64)
+    c = (ctypes.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in ctr])
+    k = (ctypes.c_uint32 * 2)(*[int(v) & 0xFFFFFFFF for v in key])
+    o = (ctypes.c_uint32 * 4)()
+    lib.orc_philox4x32_10(c, k, o)
+    return np.array(list(o), dtype=np.uint32)
+
+
+def noise_variates(seed: int, x: int, y: int, t: int, lattice_id: int = 0) -> np.ndarray:
+    """The nine s_i in (-1, 1) of site (x, y) at step t; eta~_i = sigma s_i."""
+    lib = _lib(64)
+    s = np.empty(9)
+    lib.orc_noise_variates(seed, x, y, t, lattice_id, _ptr(s, ctypes.c_double))
+    return s
+
+
+def init_uniforms(seed: int, x: int, y: int, lattice_id: int = 0) -> np.ndarray:
+    lib = _lib(64)
+    u = np.empty(4)
+    lib.orc_init_uniforms(seed, x, y, lattice_id, _ptr(u, ctypes.c_double))
+    return u

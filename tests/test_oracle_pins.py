@@ -1,0 +1,460 @@
+"""Pins of the FP64 oracle to what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: a closed
+form, a textbook identity, an invariant the paper states, a brute-force
+property, or the paper's own Chapman-Enskog linear analysis.  A plausible
+slip in the oracle (a dropped term, a wrong sign, a wrong opposite direction,
+a transposed stream) fails at least one of them.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+EX = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1])
+EY = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1])
+CS2 = 1.0 / 3.0
+
+
+def prm_of(name, **kw):
+    d = W.preset(name, **kw)
+    return d.pop("model"), O.params(**d)
+
+
+# ----------------------------------------------------------------- P2 ------
+def test_equilibrium_moments_textbook_d2q9():
+    """Sum xi = rho, sum xi e = rho u, sum xi e e = rho (c_s^2 I + u u)
+    (the moments f^SS must carry, Sec. 2 and App. A.1; D2Q9 c_s^2 = 1/3)."""
+    rng = np.random.default_rng(1)
+    for _ in range(200):
+        rho = rng.uniform(0.1, 3.0)
+        u = rng.uniform(-0.2, 0.2, 2)
+        xi = O.equilibrium(rho, u[0], u[1])
+        assert abs(xi.sum() - rho) <= 1e-15 * rho * 4
+        assert abs((xi * EX).sum() - rho * u[0]) <= 1e-15 * 8
+        assert abs((xi * EY).sum() - rho * u[1]) <= 1e-15 * 8
+        pxx = (xi * EX * EX).sum()
+        pyy = (xi * EY * EY).sum()
+        pxy = (xi * EX * EY).sum()
+        assert abs(pxx - rho * (CS2 + u[0] ** 2)) <= 1e-14
+        assert abs(pyy - rho * (CS2 + u[1] ** 2)) <= 1e-14
+        assert abs(pxy - rho * u[0] * u[1]) <= 1e-14
+
+
+def test_equilibrium_at_rest_is_weights():
+    xi = O.equilibrium(2.0, 0.0, 0.0)
+    np.testing.assert_allclose(xi, 2.0 * np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4), rtol=1e-15)
+
+
+def test_d2q7_coefficients_follow_from_cs_form():
+    """The lift writes Eq. (fssD2Q7) as w rho [1 + e.u/c_s^2 + (e.u)^2/(2c_s^4) - u^2/(2c_s^2)];
+    with the paper's D2Q7 c_s^2 = 1/4 this gives its printed 4, 8, -2."""
+    g = json.load(open(os.path.join(HERE, "golden", "paper_parameters.json")))["d2q7"]
+    cs2 = g["cs2"]
+    assert 1 / cs2 == g["coef_eu"] and 1 / (2 * cs2 ** 2) == g["coef_eu2"]
+    assert -1 / (2 * cs2) == g["coef_u2"]
+    # and on D2Q9 (c_s^2 = 1/3) the same form gives the oracle's 3, 9/2, -3/2:
+    rho, ux, uy = 1.3, 0.05, -0.02
+    xi = O.equilibrium(rho, ux, uy)
+    e1u = ux
+    assert abs(xi[1] - (1 / 9) * rho * (1 + 3 * e1u + 4.5 * e1u ** 2 - 1.5 * (ux * ux + uy * uy))) < 1e-15
+
+
+# ----------------------------------------------------------------- P8 ------
+def test_negative_correction_bruteforce():
+    """App. A.3: output >= 0, sum = rho, identity on non-negative input, and the
+    move to the opposite population keeps the momentum direction."""
+    rng = np.random.default_rng(2)
+    for trial in range(3000):
+        f = rng.uniform(-0.05, 0.3, 9)
+        if trial % 3 == 0:  # adversarial: both members of a pair negative
+            i = rng.integers(1, 5)
+            f[i] = -rng.uniform(0, 0.05)
+            f[i + 2 if i <= 2 else i - 2] = -rng.uniform(0, 0.05)
+        rho = max(f.sum(), 1e-3)
+        g, changed = O.negative_correction(f, rho)
+        assert (g >= 0).all()
+        if not changed:
+            np.testing.assert_array_equal(g, f)
+            continue
+        assert abs(g.sum() - rho) <= 1e-14 * max(rho, 1)
+        jx_in, jy_in = (f * EX).sum(), (f * EY).sum()
+        jx, jy = (g * EX).sum(), (g * EY).sum()
+        # j_out = j_in * rho / S for some S > 0: parallel, same sense
+        cross = jx * jy_in - jy * jx_in
+        assert abs(cross) <= 1e-13
+        if abs(jx_in) + abs(jy_in) > 1e-6:
+            assert jx * jx_in + jy * jy_in > 0
+    f = np.abs(rng.uniform(0.01, 0.2, 9))
+    g, changed = O.negative_correction(f, f.sum())
+    assert not changed and np.array_equal(g, f)
+
+
+def test_negative_correction_examples():
+    """Worked cases of App. A.3 by hand."""
+    f = np.array([-0.1, 0.2, 0.1, 0.1, 0.1, 0.05, 0.05, 0.05, 0.05])
+    g, _ = O.negative_correction(f, 0.6)
+    # f0 -> 0, sum becomes 0.7, rescale by 0.6/0.7
+    np.testing.assert_allclose(g, np.r_[0.0, f[1:]] * (0.6 / 0.7), rtol=1e-15)
+    f = np.array([0.4, -0.02, 0.1, 0.1, 0.1, 0.05, 0.05, 0.05, 0.05])
+    g, _ = O.negative_correction(f, 0.88)
+    h = f.copy(); h[3] += 0.02; h[1] = 0.0  # opposite of 1 is 3
+    np.testing.assert_allclose(g, h * (0.88 / h.sum()), rtol=1e-15)
+    f = np.array([0.4, 0.1, 0.1, 0.1, 0.1, -0.01, 0.05, -0.03, 0.05])  # 5 <-> 7 both negative
+    g, _ = O.negative_correction(f, 0.86)
+    h = f.copy(); h[7] += 0.01; h[5] = 0.0; h[5] += -h[7]; h[7] = 0.0
+    np.testing.assert_allclose(g, h * (0.86 / h.sum()), rtol=1e-14)
+
+
+# ----------------------------------------------------------------- P6 ------
+@pytest.mark.parametrize("n,m", [(16, 1), (24, 5), (7, 2)])
+def test_gradient_stencil_single_mode(n, m):
+    """rho = a + b sin(k.r): the isotropic stencil (Sec. 3) gives exactly
+    g_x = b sin(kx)(2 + cos ky)/3 cos(k.r), and the same with x, y swapped."""
+    a, b = 1.0, 0.1
+    kx, ky = 2 * np.pi * m / n, 2 * np.pi * ((m + 1) % n) / n
+    y, x = np.mgrid[0:n, 0:n]
+    rho = a + b * np.sin(kx * x + ky * y)
+    for (px, py) in [(0, 0), (3, 1), (n - 1, n - 2)]:
+        g = O.gradient(rho, px, py)
+        ph = kx * px + ky * py
+        gx = b * math.sin(kx) * (2 + math.cos(ky)) / 3 * math.cos(ph)
+        gy = b * math.sin(ky) * (2 + math.cos(kx)) / 3 * math.cos(ph)
+        assert abs(g[0] - gx) < 1e-14 and abs(g[1] - gy) < 1e-14
+    rho1 = a + b * np.sin(kx * x)
+    g = O.gradient(rho1, 2, 0)
+    assert abs(g[0] - b * math.sin(kx) * math.cos(kx * 2)) < 1e-14 and abs(g[1]) < 1e-14
+
+
+# ------------------------------------------------------------- u* closures --
+def test_ustar_closures():
+    """Eqs. (bu_mips), (bu_CIL), (U0) and the U_max clamp at chosen points."""
+    p = O.params(C=2.0, rho_star=1.5, u_max=0.3, A=0.1, B=0.3)
+    us = O.ustar("mips", p, 1.0, 0.5, 0.5, g=(0.03, -0.04))
+    np.testing.assert_allclose(us, 2.0 * (1 - 1 / 1.5) * np.array([0.03, -0.04]), rtol=1e-15)
+    us = O.ustar("mips", p, 1.6, 0.0, 0.0, g=(0.03, -0.04))  # rho >= rho*: no flow
+    assert (us == 0).all()
+    us = O.ustar("mips", p, 0.5, 0.0, 0.0, g=(3.0, 4.0))  # clamp keeps the direction
+    np.testing.assert_allclose(us, [0.18, 0.24], rtol=1e-15)
+    us = O.ustar("cil", p, 1.0, 0.03, 0.04)  # U0 = 0.2 along u
+    np.testing.assert_allclose(us, [0.12, 0.16], rtol=1e-15)
+    us = O.ustar("cil", p, 2.0, 0.03, 0.04)  # B < A rho^2: U0 = 0
+    assert (us == 0).all()
+    us = O.ustar("cil", p, 1.0, 0.0, 0.0)  # no direction: u* = 0
+    assert (us == 0).all()
+    us = O.ustar("passive", p, 1.0, 0.01, -0.02)
+    np.testing.assert_array_equal(us, [0.01, -0.02])
+
+
+# ----------------------------------------------------------------- P1 ------
+@pytest.mark.parametrize("name", ["MIPS_RHO1", "CIL_RHO1", "MIPS_PAPER_LITERAL", "PASSIVE"])
+def test_mass_conservation(name):
+    """Streaming, BGK with f^SS(rho, u*), the zero-sum noise of Eq.
+    (noiseDensityConservation) and the rescaled negative correction all keep
+    sum rho (Sec. 2: 'conserves mass density')."""
+    model, p = prm_of(name)
+    if name == "PASSIVE":
+        p.sigma = 0.02
+    f = O.init(32, 24, W.seed(1), **W.INIT_CONFIG2, prm=p)
+    m0 = O.observables(f)["mass"]
+    g = O.run(f, model, p, W.seed(1), 0, 1000)
+    assert abs(O.observables(g)["mass"] - m0) / m0 < 1e-13
+
+
+# ----------------------------------------------------------------- P3 ------
+@pytest.mark.parametrize("case", ["passive_u", "cil_U0", "mips_rest", "cil_rest"])
+def test_fixed_points(case):
+    """Uniform states the update leaves unchanged (sigma = 0)."""
+    n = 12
+    rho = np.full((n, n), 1.1)
+    if case == "passive_u":
+        model, p, u = "passive", O.params(tau=1.3), (0.03, -0.02)
+    elif case == "cil_U0":
+        p = O.params(tau=1.7, A=0.1, B=0.3)
+        U0 = 0.3 - 0.1 * 1.1 ** 2
+        model, u = "cil", (U0 * 0.6, U0 * 0.8)
+    elif case == "mips_rest":
+        model, p, u = "mips", O.params(tau=1.2, C=6, rho_star=5 / 3, u_max=0.3), (0.0, 0.0)
+    else:
+        model, p, u = "cil", O.params(tau=1.0, A=0.1, B=0.3), (0.0, 0.0)
+    f = O.from_moments(rho, np.full((n, n), u[0]), np.full((n, n), u[1]))
+    g = O.run(f, model, p, 5, 0, 1000)
+    np.testing.assert_allclose(g, f, rtol=0, atol=1e-14)
+
+
+# ----------------------------------------------------------------- P4 ------
+@pytest.mark.parametrize("tau", [1.0, 1.5, 2.0])
+def test_homogeneous_relaxation_closed_forms(tau):
+    """Uniform rho and u, sigma = 0: momentum obeys j' = j - (j - rho u*)/tau, so
+    PASSIVE keeps u, MIPS (grad rho = 0, u* = 0) gives u_n = (1-1/tau)^n u_0, and
+    CIL gives |u_n| - U0 = (1-1/tau)^n (|u_0| - U0) at fixed direction."""
+    n = 8
+    rho = np.full((n, n), 0.9)
+    u0 = np.array([0.05, 0.12])
+    f = O.from_moments(rho, np.full((n, n), u0[0]), np.full((n, n), u0[1]))
+    lam = 1 - 1 / tau
+    for nsteps in (1, 3, 7):
+        g = O.run(f, "passive", O.params(tau=tau), 1, 0, nsteps)
+        _, ux, uy = O.moments(g)
+        assert abs(ux[0, 0] - u0[0]) < 1e-14 and abs(uy[0, 0] - u0[1]) < 1e-14
+        g = O.run(f, "mips", O.params(tau=tau, C=6, rho_star=5 / 3, u_max=0.3), 1, 0, nsteps)
+        _, ux, uy = O.moments(g)
+        np.testing.assert_allclose([ux[3, 4], uy[3, 4]], lam ** nsteps * u0, atol=1e-14)
+        A, B = 0.1, 0.3
+        U0 = B - A * 0.81
+        g = O.run(f, "cil", O.params(tau=tau, A=A, B=B), 1, 0, nsteps)
+        _, ux, uy = O.moments(g)
+        mag = math.hypot(ux[2, 5], uy[2, 5])
+        assert abs((mag - U0) - lam ** nsteps * (np.linalg.norm(u0) - U0)) < 1e-14
+        assert abs(ux[2, 5] * u0[1] - uy[2, 5] * u0[0]) < 1e-14
+
+
+# ----------------------------------------------------------------- P5 ------
+@pytest.mark.parametrize("tau", [0.8, 1.0, 1.7])
+def test_passive_shear_wave_viscosity(tau):
+    """Passive limit: u_x = U sin(2 pi y / N) decays as exp(-nu k^2 t),
+    nu = (2 tau - 1) c_s^2 / 2 = (tau - 1/2)/3 (App. B, with D2Q9 c_s^2 = 1/3)."""
+    ny, U = 128, 1e-4
+    k = 2 * np.pi / ny
+    y = np.arange(ny)[:, None]
+    ux = U * np.sin(k * y) * np.ones((1, 1))
+    f = O.from_moments(np.ones((ny, 1)), ux, np.zeros((ny, 1)))
+    nu = (tau - 0.5) / 3
+    t1, t2 = 50, 650
+    p = O.params(tau=tau)
+    g1 = O.run(f, "passive", p, 1, 0, t1)
+    g2 = O.run(g1, "passive", p, 1, t1, t2 - t1)
+    a = [abs(np.sum(O.moments(g)[1][:, 0] * np.sin(k * y[:, 0]))) for g in (g1, g2)]
+    nu_meas = -math.log(a[1] / a[0]) / ((t2 - t1) * k * k)
+    assert abs(nu_meas - nu) / nu < 2e-3
+
+
+# ----------------------------------------------------------------- P7 ------
+def _growth_rate(model, p, u0, nx, t1=20, t2=100):
+    k = 2 * np.pi / nx
+    x = np.arange(nx)
+    rho = (1 + 1e-6 * np.cos(k * x))[None, :]
+    f = O.from_moments(rho, np.full((1, nx), u0), np.zeros((1, nx)))
+
+    def amp(g):
+        r = O.moments(g)[0][0]
+        return abs(np.sum((r - r.mean()) * np.exp(-1j * k * x)))
+
+    g1 = O.run(f, model, p, 1, 0, t1)
+    g2 = O.run(g1, model, p, 1, t1, t2 - t1)
+    return math.log(amp(g2) / amp(g1)) / (t2 - t1), k
+
+
+@pytest.mark.parametrize("tau,C", [(1.0, 0.0), (1.5, 0.2), (1.0, 1.0)])
+def test_mips_growth_rate_matches_chapman_enskog(tau, C):
+    """App. B: F_MIPS = 2 rho/(2tau-1) (C(1-rho/rho*) grad rho - v) with pressure
+    c_s^2 rho.  Linearised about rest: s = -k^2 (c_s^2 - gamma rho0 C (1 - rho0/rho*))/gamma,
+    gamma = 2/(2 tau - 1).  C = 1 is in the unstable (MIPS) range.  The lattice
+    result approaches the continuum one as O(k^2)."""
+    p = O.params(tau=tau, C=C, rho_star=5 / 3, u_max=0.3)
+    gam = 2 / (2 * tau - 1)
+    errs = []
+    for nx in (128, 256):
+        s, k = _growth_rate("mips", p, 0.0, nx)
+        ce = -k * k * (CS2 - gam * 1.0 * C * (1 - 0.6)) / gam
+        errs.append(abs(s - ce) / abs(ce))
+    assert errs[0] < 3e-3 and errs[1] < 1e-3
+    assert errs[1] < errs[0] / 2.5 or errs[1] < 1e-6  # O(k^2) convergence (or exact)
+
+
+@pytest.mark.parametrize("A,B", [(0.06845, 0.3), (0.4, 0.5)])
+def test_cil_growth_rate_matches_banding_condition(A, B):
+    """Sec. 6 Eq. (BandingInstabilityCondition) with alpha0 = 1/(2tau-1),
+    beta = alpha0/U0^2 (Eq. (beta)) and alpha1 = 2 alpha0 U0'/U0:
+    Re s = k^2 (2tau-1)(U0'^2 rho0^2 - c_s^2)/2 about the moving state |u| = U0.
+    (A, B) = (0.4, 0.5) has 2 A rho0^2 > c_s: the banding-unstable side."""
+    p = O.params(tau=1.0, A=A, B=B)
+    U0, dU0 = B - A, -2 * A
+    errs = []
+    for nx in (128, 256):
+        s, k = _growth_rate("cil", p, U0, nx)
+        ce = k * k * (dU0 ** 2 - CS2) / 2
+        errs.append(abs(s - ce) / abs(ce))
+    assert errs[0] < 3e-3 and errs[1] < 1e-3
+    assert errs[1] < errs[0] / 2.5 or errs[1] < 1e-6
+
+
+# ----------------------------------------------------------------- P9 ------
+@pytest.mark.parametrize("name", ["MIPS_RHO1", "CIL_RHO1"])
+@pytest.mark.parametrize("bits", [64, 32])
+def test_density_rescaling_symmetry_bitwise(name, bits):
+    """(f, C, rho*, A, sigma) -> (2f, C/2, 2 rho*, A/4, 2 sigma) maps the trajectory to
+    exactly twice itself: every operation of the update commutes with an exact
+    power-of-two scaling of the densities."""
+    d = W.preset(name)
+    model = d.pop("model")
+    p1 = O.params(**d)
+    p2 = O.params(**dict(d, C=d["C"] / 2, rho_star=d["rho_star"] * 2, A=d["A"] / 4,
+                         sigma=d["sigma"] * 2))
+    f = O.init(20, 12, 77, **W.INIT_CONFIG2, prm=p1, bits=bits)
+    g1 = O.run(f, model, p1, 77, 0, 60, bits=bits)
+    g2 = O.run(2 * f, model, p2, 77, 0, 60, bits=bits)
+    np.testing.assert_array_equal(g2, 2 * g1)
+
+
+# ---------------------------------------------------------------- P11 ------
+ROT = np.array([0, 2, 3, 4, 1, 6, 7, 8, 5])  # e_ROT[i] = R90 e_i
+
+
+def _rotate(f):
+    """Rotate a square periodic state by 90 degrees: f'_{R i}(R r) = f_i(r)."""
+    n = f.shape[1]
+    g = np.empty_like(f)
+    y, x = np.mgrid[0:n, 0:n]
+    for i in range(9):
+        g[ROT[i], x, (-y) % n] = f[i, y, x]
+    return g
+
+
+def test_rotation_table_matches_velocity_set():
+    for i in range(9):
+        assert (EX[ROT[i]], EY[ROT[i]]) == (-EY[i], EX[i])
+
+
+@pytest.mark.parametrize("name", ["MIPS_RHO1", "CIL_RHO1"])
+def test_rotation_equivariance(name):
+    """The update has the lattice's 90-degree symmetry (sigma = 0)."""
+    model, p = prm_of(name, sigma=0.0)
+    f = O.init(16, 16, 9, **W.INIT_CONFIG2, prm=p)
+    a = _rotate(O.run(f, model, p, 9, 0, 15))
+    b = O.run(_rotate(f), model, p, 9, 0, 15)
+    np.testing.assert_allclose(a, b, rtol=0, atol=1e-11)
+
+
+def test_reflection_equivariance():
+    """Mirror x -> -x swaps populations 1<->3, 5<->6, 7<->8."""
+    perm = np.array([0, 3, 2, 1, 4, 6, 5, 8, 7])
+    model, p = prm_of("CIL_RHO1", sigma=0.0)
+    f = O.init(10, 14, 4, **W.INIT_CONFIG2, prm=p)
+
+    def mirror(g):
+        h = np.empty_like(g)
+        for i in range(9):
+            h[perm[i]] = g[i][:, (-np.arange(g.shape[2])) % g.shape[2]]
+        return h
+    np.testing.assert_allclose(mirror(O.run(f, model, p, 4, 0, 15)),
+                               O.run(mirror(f), model, p, 4, 0, 15), rtol=0, atol=1e-12)
+
+
+# ---------------------------------------------------------------- P12 ------
+def test_phi_bounded_by_B():
+    """Eq. (phi): 0 <= phi <= B for the CIL model (sigma = 0, tau = 1)."""
+    model, p = prm_of("CIL_RHO1", sigma=0.0)
+    f = O.init(32, 32, 11, **W.INIT_CONFIG2, prm=p)
+    g = O.run(f, model, p, 11, 0, 100)
+    _, ux, uy = O.moments(g)
+    assert np.hypot(ux, uy).max() <= 0.3 * (1 + 1e-12)
+    obs = O.observables(g, B=0.3)
+    assert 0 <= obs["phi"] <= 0.3
+
+
+# -------------------------------------------------------- observables ------
+def test_observables_closed_forms():
+    """Eq. (phi), App. D on constructed states: a uniform flow, and a density
+    cosine along x (population std of a full-period cosine = amplitude/sqrt 2)."""
+    n = 32
+    f = O.from_moments(np.full((n, n), 1.2), np.full((n, n), 0.03), np.full((n, n), -0.04))
+    ob = O.observables(f, B=0.3)
+    assert abs(ob["phi"] - 0.05) < 1e-14 and abs(ob["zeta"] - 0.25) < 1e-14
+    assert ob["drho_y"] < 1e-12 and ob["drho_x"] < 1e-12 and ob["var_rho"] < 1e-24
+    assert abs(ob["mass"] - 1.2 * n * n) < 1e-13 * 1.2 * n * n
+    x = np.arange(n)[None, :] * np.ones((n, 1))
+    a = 0.07
+    f = O.from_moments(1 + a * np.cos(2 * np.pi * x / n), np.zeros((n, n)), np.zeros((n, n)))
+    ob = O.observables(f, B=0.3)
+    assert abs(ob["drho_y"] - a / math.sqrt(2)) < 1e-14
+    assert ob["drho_x"] < 1e-12
+    assert abs(ob["var_rho"] - a * a / 2) < 1e-14
+    assert ob["phi"] < 1e-15 and abs(ob["zeta"] - 0.3) < 1e-14
+
+
+# ---------------------------------------------------------------- P10 ------
+def test_noise_statistics():
+    """eta~ uniform on [-sigma, sigma] (Sec. 2): mean 0, variance sigma^2/3,
+    uncorrelated across the nine directions and across sites; with
+    eta = eta~ - mean, sum eta = 0 and <h_x^2> = sum_i e_ix^2 sigma^2/3 = 2 sigma^2
+    on D2Q9 (the paper's Sec. 7 moment h, D2Q7 value c^2 sigma^2)."""
+    n = 40000
+    s = np.array([O.noise_variates(W.seed(1), i % 200, i // 200, 17) for i in range(n)])
+    assert np.all(np.abs(s) < 1)
+    m = s.mean(0)
+    assert np.all(np.abs(m) < 5 * math.sqrt(1 / 3 / n))
+    v = s.var(0)
+    assert np.all(np.abs(v - 1 / 3) < 5 * math.sqrt(4 / 45 / n))
+    c = np.corrcoef(s.T)
+    assert np.abs(c - np.eye(9)).max() < 5 / math.sqrt(n)
+    eta = s - s.mean(1, keepdims=True)
+    assert np.abs(eta.sum(1)).max() < 1e-15
+    hx = (eta * EX).sum(1)
+    assert abs(hx.var() - 2.0) < 5 * 2.0 * math.sqrt(2 / n)  # sigma = 1
+    # 24-bit grid: every variate is an odd multiple of 2^-24
+    k = (s * 2 ** 24)
+    assert np.all(np.abs(k - np.round(k)) == 0) and np.all(np.round(k) % 2 == 1)
+    # different step, site or lattice id: different draws
+    assert not np.array_equal(O.noise_variates(1, 3, 4, 5, 0), O.noise_variates(1, 3, 4, 6, 0))
+    assert not np.array_equal(O.noise_variates(1, 3, 4, 5, 0), O.noise_variates(1, 3, 4, 5, 1))
+    assert not np.array_equal(O.noise_variates(1, 3, 4, 5, 0), O.noise_variates(2, 3, 4, 5, 0))
+
+
+def test_philox_bijection_and_avalanche():
+    """Philox4x32-10 is a bijection of the 128-bit counter for a fixed key
+    (Salmon et al. 2011), and one flipped input bit changes about half the
+    output bits."""
+    key = (0x12345678, 0x9ABCDEF0)
+    outs = {tuple(O.philox4x32_10((i, 0, 0, 0), key)) for i in range(20000)}
+    assert len(outs) == 20000
+    rng = np.random.default_rng(3)
+    flips = []
+    for _ in range(300):
+        c = rng.integers(0, 2 ** 32, 4, dtype=np.uint64)
+        b = int(rng.integers(0, 128))
+        c2 = c.copy(); c2[b // 32] ^= np.uint64(1 << (b % 32))
+        o1, o2 = O.philox4x32_10(c, key), O.philox4x32_10(c2, key)
+        flips.append(sum(bin(int(a) ^ int(d)).count("1") for a, d in zip(o1, o2)))
+    assert abs(np.mean(flips) - 64) < 2.0
+
+
+def test_init_uniforms_and_recipe():
+    """App. C.2 initialisation: rho within +-10 % of rho-bar, u magnitude as set."""
+    u = np.array([O.init_uniforms(5, i, 0) for i in range(20000)])
+    assert np.all((u > 0) & (u < 1))
+    assert np.all(np.abs(u.mean(0) - 0.5) < 5 * math.sqrt(1 / 12 / 20000))
+    d = W.preset("CIL_RHO1")
+    p = O.params(**{k: v for k, v in d.items() if k != "model"})
+    f = O.init(40, 30, 5, **W.INIT_PAPER_CIL, prm=p)
+    rho, ux, uy = O.moments(f)
+    assert rho.min() >= 0.9 and rho.max() <= 1.1
+    np.testing.assert_allclose(np.hypot(ux, uy), d["B"] - d["A"] * rho ** 2, rtol=1e-12)
+    f = O.init(40, 30, 5, **W.INIT_CONFIG2, prm=p)
+    rho, ux, uy = O.moments(f)
+    np.testing.assert_allclose(np.hypot(ux, uy), 0.01, rtol=1e-12)
+
+
+# --------------------------------------------------------- paper presets ---
+def test_presets_follow_paper_tables():
+    g = json.load(open(os.path.join(HERE, "golden", "paper_parameters.json")))
+    lit = W.PRESETS["MIPS_PAPER_LITERAL"]
+    assert lit["C"] == g["mips_table"]["C"] and lit["rho_star"] == g["mips_table"]["rho_star"]
+    assert lit["u_max"] == g["mips_table"]["U_max"]
+    assert abs(lit["sigma"] * math.sqrt(2) - g["mips_stills"]["b"]["sigma"]) < 1e-15
+    cil = W.PRESETS["CIL_PAPER_LITERAL"]
+    assert cil["B"] == g["cil_general"]["B"] and cil["A"] == g["cil_hysteresis"]["A"]
+    assert abs(cil["sigma"] * math.sqrt(2) - g["cil_general"]["sigma"]) < 1e-15
+    # rescaled presets are the P9 image with s = 1 / rho-bar
+    s = 1 / g["mips_sweep"]["rho_bar"]
+    r = W.PRESETS["MIPS_RHO1"]
+    assert abs(r["C"] - lit["C"] / s) < 1e-12 and abs(r["rho_star"] - lit["rho_star"] * s) < 1e-12
+    s = 1 / g["cil_hysteresis"]["rho_bar_HO"]
+    r = W.PRESETS["CIL_RHO1"]
+    assert abs(r["A"] - cil["A"] / s ** 2) < 1e-12 and abs(r["sigma"] - cil["sigma"] * s) < 1e-12
