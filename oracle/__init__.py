@@ -79,11 +79,12 @@ def _lib(bits: int = 64) -> ctypes.CDLL:
         prm = ctypes.POINTER(OrcParams)
         lib.orc_step.argtypes = [real_p, real_p, i32, i32, i32, prm, u64, u32, u32]
         lib.orc_step.restype = i32
-        lib.orc_run.argtypes = [real_p, i32, i32, i32, prm, u64, u32, i64, u32]
-        lib.orc_run.restype = i32
-        lib.orc_init.argtypes = [real_p, i32, i32, u64, u32, ctypes.c_double, ctypes.c_double,
-                                 i32, ctypes.c_double, ctypes.c_double, ctypes.c_double, prm]
-        lib.orc_init.restype = None
+        lib.orc_run_window.argtypes = [real_p, i32, i32, i32, prm, u64, u32, i64, u32, i32, i32, i32, i32]
+        lib.orc_run_window.restype = i32
+        lib.orc_init_window.argtypes = [real_p, i32, i32, u64, u32, ctypes.c_double, ctypes.c_double,
+                                        i32, ctypes.c_double, ctypes.c_double, ctypes.c_double, prm,
+                                        i32, i32, i32, i32]
+        lib.orc_init_window.restype = None
         lib.orc_from_moments.argtypes = [real_p, i32, i32, dbl_p, dbl_p, dbl_p]
         lib.orc_moments.argtypes = [real_p, i32, i32, dbl_p, dbl_p, dbl_p]
         lib.orc_observables.argtypes = [real_p, i32, i32, ctypes.c_double, dbl_p]
@@ -128,12 +129,16 @@ def _check_f(f: np.ndarray, bits: int) -> None:
 
 def init(nx: int, ny: int, seed: int, lattice_id: int = 0, rho_mean: float = 1.0,
          rho_amp: float = 0.0, u_kind: int = 0, u_amp: float = 0.0, ux0: float = 0.0,
-         uy0: float = 0.0, prm: OrcParams | None = None, bits: int = 64) -> np.ndarray:
-    """Seeded initial populations f = f^SS(rho, u) (App. C.2)."""
+         uy0: float = 0.0, prm: OrcParams | None = None, bits: int = 64, window=None) -> np.ndarray:
+    """Seeded initial populations f = f^SS(rho, u) (App. C.2).
+
+    window = (x_off, y_off, gnx, gny): the nx x ny window at that offset of a
+    gnx x gny lattice (the draws use the global site coordinates)."""
     lib = _lib(bits)
     f = np.empty((9, ny, nx), dtype=_dtype(bits))
-    lib.orc_init(_rp(f, bits), nx, ny, seed, lattice_id, rho_mean, rho_amp, u_kind, u_amp,
-                 ux0, uy0, ctypes.byref(prm if prm is not None else params()))
+    xo, yo, gx, gy = window if window is not None else (0, 0, nx, ny)
+    lib.orc_init_window(_rp(f, bits), nx, ny, seed, lattice_id, rho_mean, rho_amp, u_kind, u_amp,
+                        ux0, uy0, ctypes.byref(prm if prm is not None else params()), xo, yo, gx, gy)
     return f
 
 
@@ -164,13 +169,18 @@ def step(f: np.ndarray, model: str, prm: OrcParams, seed: int, t: int, lattice_i
 
 
 def run(f: np.ndarray, model: str, prm: OrcParams, seed: int, t0: int, nsteps: int,
-        lattice_id: int = 0, bits: int = 64) -> np.ndarray:
-    """nsteps steps from t0 (returns a new array; the input is untouched)."""
+        lattice_id: int = 0, bits: int = 64, window=None) -> np.ndarray:
+    """nsteps steps from t0 (returns a new array; the input is untouched).
+
+    window = (x_off, y_off, gnx, gny) keys the noise by global coordinates; the
+    window wraps on itself, so only sites at least nsteps (MIPS: 2 nsteps) from
+    its edge are exact."""
     g = np.array(f, dtype=_dtype(bits), order="C", copy=True)
     _check_f(g, bits)
     lib = _lib(bits)
-    rc = lib.orc_run(_rp(g, bits), g.shape[2], g.shape[1], MODELS[model], ctypes.byref(prm),
-                     seed, t0, nsteps, lattice_id)
+    xo, yo, gx, gy = window if window is not None else (0, 0, g.shape[2], g.shape[1])
+    rc = lib.orc_run_window(_rp(g, bits), g.shape[2], g.shape[1], MODELS[model], ctypes.byref(prm),
+                            seed, t0, nsteps, lattice_id, xo, yo, gx, gy)
     if rc != 0:
         raise MemoryError("oracle run failed")
     return g

@@ -242,9 +242,15 @@ void orc_ustar(int model, const orc_params *p, real rho, real ux, real uy, const
  *  2 rho, u from f*, 3 u* and f^SS, 4 BGK redistribution,
  *  5 zero-sum noise (Eq. (noiseDensityConservation)), 6 negative correction.
  * fin and fout are distinct [9][ny][nx] arrays.  Returns 0, or -1 on
- * allocation failure. */
-int orc_step(const real *fin, real *fout, int nx, int ny, int model, const orc_params *p,
-             uint64_t seed, uint32_t t, uint32_t id)
+ * allocation failure.
+ *
+ * Window form: the array is the nx x ny window at offset (x_off, y_off) of a
+ * larger gnx x gny periodic lattice; only the noise counter sees the global
+ * coordinates.  The window itself wraps periodically, so after k steps only
+ * sites farther than k (2k for MIPS, whose gradient reads one more ring) from
+ * the window edge equal the large lattice's values. */
+int orc_step_window(const real *fin, real *fout, int nx, int ny, int model, const orc_params *p,
+                    uint64_t seed, uint32_t t, uint32_t id, int x_off, int y_off, int gnx, int gny)
 {
     size_t n = (size_t)nx * (size_t)ny;
     real *fs = (real *)malloc(sizeof(real) * Q * n);
@@ -296,7 +302,8 @@ int orc_step(const real *fin, real *fout, int nx, int ny, int model, const orc_p
             /* 5. noise: eta_i = eta~_i - (1/Q) sum_j eta~_j */
             if (sigma > 0) {
                 double s[Q];
-                orc_noise_variates(seed, (uint32_t)x, (uint32_t)y, t, id, s);
+                orc_noise_variates(seed, (uint32_t)wrap(x + x_off, gnx), (uint32_t)wrap(y + y_off, gny),
+                                   t, id, s);
                 real et[Q], mean = 0;
                 for (int i = 0; i < Q; ++i) {
                     et[i] = sigma * (real)s[i];
@@ -313,16 +320,24 @@ int orc_step(const real *fin, real *fout, int nx, int ny, int model, const orc_p
     return 0;
 }
 
+/* The whole periodic lattice: a window with no offset. */
+int orc_step(const real *fin, real *fout, int nx, int ny, int model, const orc_params *p,
+             uint64_t seed, uint32_t t, uint32_t id)
+{
+    return orc_step_window(fin, fout, nx, ny, model, p, seed, t, id, 0, 0, nx, ny);
+}
+
 /* n steps from t0, ping-ponging between f and a scratch copy; the result is
  * left in f.  Returns 0, or -1 on allocation failure. */
-int orc_run(real *f, int nx, int ny, int model, const orc_params *p, uint64_t seed,
-            uint32_t t0, int64_t nsteps, uint32_t id)
+int orc_run_window(real *f, int nx, int ny, int model, const orc_params *p, uint64_t seed,
+                   uint32_t t0, int64_t nsteps, uint32_t id, int x_off, int y_off, int gnx, int gny)
 {
     size_t bytes = sizeof(real) * Q * (size_t)nx * (size_t)ny;
     real *tmp = (real *)malloc(bytes);
     if (!tmp) return -1;
     for (int64_t k = 0; k < nsteps; ++k) {
-        if (orc_step(f, tmp, nx, ny, model, p, seed, t0 + (uint32_t)k, id) != 0) {
+        if (orc_step_window(f, tmp, nx, ny, model, p, seed, t0 + (uint32_t)k, id, x_off, y_off, gnx,
+                            gny) != 0) {
             free(tmp);
             return -1;
         }
@@ -332,21 +347,28 @@ int orc_run(real *f, int nx, int ny, int model, const orc_params *p, uint64_t se
     return 0;
 }
 
+int orc_run(real *f, int nx, int ny, int model, const orc_params *p, uint64_t seed,
+            uint32_t t0, int64_t nsteps, uint32_t id)
+{
+    return orc_run_window(f, nx, ny, model, p, seed, t0, nsteps, id, 0, 0, nx, ny);
+}
+
 /* Initial state (App. C.2): per site draw uniforms, form rho and u, and set
  * f_i = xi_i(rho, u) = f^SS.  u_kind:
  *   0  u = (ux0, uy0) + u_amp (2U1 - 1, 2U2 - 1)       (componentwise noise)
  *   1  u = (ux0, uy0) + u_amp (cos 2 pi U1, sin 2 pi U1)  (random direction)
  *   2  u = U0(rho) (cos 2 pi U1, sin 2 pi U1)          (paper CIL init)
  * rho = rho_mean (1 + rho_amp (2U0 - 1)). */
-void orc_init(real *f, int nx, int ny, uint64_t seed, uint32_t id, double rho_mean,
-              double rho_amp, int u_kind, double u_amp, double ux0, double uy0,
-              const orc_params *p)
+void orc_init_window(real *f, int nx, int ny, uint64_t seed, uint32_t id, double rho_mean,
+                     double rho_amp, int u_kind, double u_amp, double ux0, double uy0,
+                     const orc_params *p, int x_off, int y_off, int gnx, int gny)
 {
     const double two_pi = 6.283185307179586476925286766559;
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             double U[4];
-            orc_init_uniforms(seed, (uint32_t)x, (uint32_t)y, id, U);
+            orc_init_uniforms(seed, (uint32_t)wrap(x + x_off, gnx), (uint32_t)wrap(y + y_off, gny), id,
+                              U);
             double r = rho_mean * (1.0 + rho_amp * (2.0 * U[0] - 1.0));
             double vx, vy;
             if (u_kind == 0) {
@@ -368,6 +390,14 @@ void orc_init(real *f, int nx, int ny, uint64_t seed, uint32_t id, double rho_me
                 AT(f, i, y, x) = (real)(w * r * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * usq));
             }
         }
+}
+
+void orc_init(real *f, int nx, int ny, uint64_t seed, uint32_t id, double rho_mean,
+              double rho_amp, int u_kind, double u_amp, double ux0, double uy0,
+              const orc_params *p)
+{
+    orc_init_window(f, nx, ny, seed, id, rho_mean, rho_amp, u_kind, u_amp, ux0, uy0, p, 0, 0, nx,
+                    ny);
 }
 
 /* Populations from given moment fields: f_i = xi_i(rho, u) per site. */
