@@ -1,0 +1,399 @@
+"""Throughput of the fused active-LBM step on GB300.
+
+Default workload: the 8192 x 8192 periodic D2Q9 lattice with the rescaled MIPS
+closure (grad-rho gradient, noise, negative correction), FP32 populations,
+observables sampled every 100 steps -- the precision/throughput configuration
+whose roofline target is stated for an 8192^2 lattice.  One "step" is one
+update of every site (all steps of the method).  Inputs (4.8 GB of populations)
+exceed the 129 MB L2, so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank advances its own
+independent lattice (replicas: the method has no exchange between lattices).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GLUPS & % HBM roofline; batched/16-bit-storage vs plain FP32 at stated error"
+UNIT = "GLUPS"
+BYTES_PER_UPDATE = {"f32": 72, "f16s": 36, "bf16s": 36}   # 9 reads + 9 writes per site
+KERNEL_SOURCES = ["paper_1902_00530_gb300/csrc/lbm_step.cuh", "paper_1902_00530_gb300/csrc/lbm_device.cuh"]
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def ncu_traffic(workload: str):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary,
+    if it was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except Exception:
+        return None
+    entry = rec.get(workload)
+    if not entry or entry.get("kernel_hash") != kernel_hash():
+        return None
+    return entry.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, local_rank: int):
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        ids = [v.strip() for v in vis.split(",") if v.strip()]
+        self.gpu = ids[local_rank] if local_rank < len(ids) else str(local_rank)
+        self.proc = None
+        self.t_begin = self.t_end = None
+        self.out = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def mark_begin(self):
+        self.t_begin = time.time()
+
+    def mark_end(self):
+        self.t_end = time.time()
+
+    def stop(self) -> dict:
+        import datetime
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.flush()
+        self.out.seek(0)
+        rows = [r.strip().split(", ") for r in self.out.read().strip().splitlines() if r.strip()]
+        os.unlink(self.out.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                ts = datetime.datetime.strptime(r[0].strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except ValueError:
+                ts = None
+            if ts is not None and self.t_begin is not None and not (self.t_begin - 0.05 <= ts <= self.t_end + 0.05):
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def workload_spec(name: str):
+    import workloads as W
+    if name == "mips8192":
+        d = W.preset("MIPS_RHO1")
+        return dict(nx=8192, ny=8192, model=d.pop("model"), params=d, init=W.INIT_CONFIG1, sample_every=100,
+                    seed=W.seed(3), label="mips_rho1_8192x8192")
+    if name == "cil1024":
+        d = W.preset("CIL_RHO1")
+        return dict(nx=1024, ny=1024, model=d.pop("model"), params=d, init=W.INIT_CONFIG2, sample_every=100,
+                    seed=W.seed(2), label="cil_rho1_1024x1024")
+    raise SystemExit(f"unknown workload {name}")
+
+
+def run_gpu(args, world, rank, local):
+    import torch
+    import torch.distributed as dist
+    from paper_1902_00530_gb300 import Lattice, Simulation
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    wl = workload_spec(args.workload)
+    storage = args.storage
+    sim = Simulation([Lattice(wl["nx"], wl["ny"], storage, rank)], [wl["model"]], [wl["params"]],
+                     sample_every=wl["sample_every"], ring_capacity=max(16, args.steps // wl["sample_every"] + 4))
+    sim.init(wl["seed"], [wl["init"]])
+    sim.tune()
+    sim.step(args.warmup)
+    sim.synchronize()
+    cells = wl["nx"] * wl["ny"]
+
+    # ---------------- timed region: K steps, events on the library's stream --
+    sim.set_profiling(True)
+    sim.profile_read()
+    sampler = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)  # let the sampler start before the work
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler.mark_begin()
+    e0.record(sim.stream)
+    sim.step(args.steps)
+    launches = sim.last_launch_count()
+    e1.record(sim.stream)
+    e1.synchronize()
+    torch.cuda.synchronize()
+    sampler.mark_end()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    prof = sim.profile_read()
+    sim.set_profiling(False)
+    ms = e0.elapsed_time(e1)
+    ms_max = ms
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    value = world * cells * args.steps / (ms_max * 1e-3) / 1e9
+
+    # ---------------- roofline of the dominant kernel (the fused step) -------
+    peak, peak_kind = measured_peak()
+    step_avg_ms = prof["step_ms"] / max(prof["step_launches"], 1)
+    achieved = BYTES_PER_UPDATE[storage] * cells / (step_avg_ms * 1e-3) / 1e9
+    traffic = ncu_traffic(f"{wl['label']}_{storage}")
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic, "peak_source": peak_kind,
+                "algorithmic_bytes_per_launch": BYTES_PER_UPDATE[storage] * cells,
+                "kernel": "lbm::step_kernel", "avg_launch_ms": round(step_avg_ms, 5),
+                "step_kernel_share": round(prof["step_ms"] / max(prof["step_ms"] + prof["other_ms"], 1e-9), 4),
+                "frac_of_8TBps": round(achieved / 8000.0, 4)}
+
+    # ---------------- end to end through the C ABI with host buffers ---------
+    host_state = sim.get_state(host=True)  # pinned input prepared outside the timed region
+    out_state = torch.empty_like(host_state).pin_memory()
+    state_bytes = host_state.numel() * 4
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim.set_state(host_state)              # H2D of the populations
+    sim.step(args.steps)
+    sim.get_state(host=True, out=out_state)  # D2H of the result
+    obs = sim.observables()                # D2H of the observables (syncs)
+    t1 = time.perf_counter()
+    e2e_s = t1 - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": round(world * cells * args.steps / e2e_s / 1e9, 3), "unit": UNIT,
+           "h2d_bytes_per_step": round(state_bytes / args.steps, 1),
+           "d2h_bytes_per_step": round((out_state.numel() * 4 + 56) / args.steps, 1)}
+    del out_state, host_state
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+
+    extra = {}
+    if rank == 0 and not args.quick:
+        extra = secondary_lines(args, wl)
+    return dict(value=value, ms=ms_max, clocks=clocks, roofline=roofline, e2e=e2e, launches=launches,
+                obs=obs, extra=extra, wl=wl)
+
+
+def secondary_lines(args, wl):
+    """The metric's comparison forms on the same GPU: 16-bit shifted storage of
+    the same workload, and the batched forms (256 lattices of 256^2 CIL on a
+    density x activity grid; a ragged mixed-model batch)."""
+    import torch
+    import workloads as W
+    from paper_1902_00530_gb300 import Lattice, Simulation
+    out = {}
+    steps = max(50, min(args.steps, 300))
+
+    def time_sim(sim, cells, steps):
+        sim.tune()
+        sim.step(5)
+        sim.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(sim.stream)
+        sim.step(steps)
+        e1.record(sim.stream)
+        e1.synchronize()
+        return cells * steps / (e0.elapsed_time(e1) * 1e-3) / 1e9
+
+    for st in ("f16s", "bf16s"):
+        sim = Simulation([Lattice(wl["nx"], wl["ny"], st)], [wl["model"]], [wl["params"]],
+                         sample_every=wl["sample_every"], ring_capacity=16)
+        sim.init(wl["seed"], [wl["init"]])
+        out[f"{st}_glups"] = round(time_sim(sim, wl["nx"] * wl["ny"], steps), 2)
+        sim.close()
+        del sim
+        torch.cuda.empty_cache()
+    # uniform batch: 256 CIL lattices of 256^2, rho-bar x activity (B) grid
+    c4 = W.CONFIG4
+    d = W.preset(c4["preset"])
+    model = d.pop("model")
+    lats, prms, specs = [], [], []
+    for i, rm in enumerate(c4["rho_means"]):
+        for j, act in enumerate(c4["activities"]):
+            lats.append(Lattice(c4["side"], c4["side"], "f32", i * 16 + j))
+            prms.append(dict(d, B=act))
+            specs.append(dict(c4["init"], rho_mean=rm))
+    sim = Simulation(lats, [model] * len(lats), prms, sample_every=100, ring_capacity=16)
+    sim.init(W.seed(4), specs)
+    out["batch256_cil_f32_glups"] = round(time_sim(sim, len(lats) * c4["side"] ** 2, steps), 2)
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+    # ragged batch: 64 lattices, sides from {128..2048}, mixed MIPS/CIL, 16-bit storage
+    rag = W.ragged_batch()
+    lats, mods, prms, specs = [], [], [], []
+    for k, (side, pname) in enumerate(rag):
+        dd = W.preset(pname)
+        mods.append(dd.pop("model"))
+        prms.append(dd)
+        lats.append(Lattice(side, side, "bf16s", k))
+        specs.append(W.INIT_CONFIG1 if mods[-1] == "mips" else W.INIT_CONFIG2)
+    sim = Simulation(lats, mods, prms, sample_every=100, ring_capacity=16)
+    sim.init(W.seed(5), specs)
+    out["ragged64_bf16s_glups"] = round(time_sim(sim, sum(s * s for s, _ in rag), steps), 2)
+    sim.close()
+    return out
+
+
+def cpu_baseline(wl, budget_s: float = 15.0):
+    """The FP64 oracle, as it stands, single-threaded on the host: a 512^2
+    window of the same workload (same seed, parameters and global
+    coordinates), stepped until about budget_s seconds have passed."""
+    import oracle as O
+    n = 512
+    p = O.params(**wl["params"])
+    win = (0, 0, wl["nx"], wl["ny"])
+    f = O.init(n, n, wl["seed"], **wl["init"], prm=p, window=win)
+    steps, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < budget_s:
+        f = O.run(f, wl["model"], p, wl["seed"], steps, 5, window=win)
+        steps += 5
+    dt = time.perf_counter() - t0
+    return {"value": round(n * n * steps / dt / 1e9, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n}x{n} window of the {wl['label']} workload, {steps} steps, FP64, 1 thread, {dt:.1f} s"}
+
+
+def run_reference(args, world, rank):
+    """The oracle as the reference arm: each step advances an n x n window of
+    the workload by one step on one host core (n = 512, smaller for long runs
+    so the whole run stays within a few minutes)."""
+    if rank != 0:
+        return
+    import oracle as O
+    wl = workload_spec(args.workload)
+    n = 512
+    while n > 64 and n * n * (args.steps + args.warmup) > 3.0e8:
+        n //= 2
+    p = O.params(**wl["params"])
+    win = (0, 0, wl["nx"], wl["ny"])
+    f = O.init(n, n, wl["seed"], **wl["init"], prm=p, window=win)
+    f = O.run(f, wl["model"], p, wl["seed"], 0, args.warmup, window=win)
+    t0 = time.perf_counter()
+    f = O.run(f, wl["model"], p, wl["seed"], args.warmup, args.steps, window=win)
+    dt = time.perf_counter() - t0
+    value = n * n * args.steps / dt / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded)",
+            "config": {"workload": wl["label"], "sample": f"{n}x{n} window per step, FP64 oracle, 1 thread"},
+            "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{n}x{n} window of {wl['label']}, {args.steps} steps"},
+            "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="mips8192")
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16s", "bf16s"])
+    ap.add_argument("--quick", action="store_true", help="skip the secondary (16-bit, batched) lines")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    r = run_gpu(args, world, rank, local)
+    if rank != 0:
+        return
+    base = None if args.no_cpu_baseline or world > 1 else cpu_baseline(r["wl"])
+    clocks = r["clocks"]
+    wl = r["wl"]
+    line = {
+        "metric": METRIC, "value": round(r["value"], 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(r["ms"] / args.steps, 5), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.storage == "f32" else args.storage,
+        "data": "synthetic (seeded lattice, paper-shaped parameters)",
+        "config": {"workload": wl["label"] + "_" + args.storage, "nx": wl["nx"], "ny": wl["ny"],
+                   "closure": wl["model"], "storage": args.storage, "sample_every": wl["sample_every"],
+                   "replicas": world, "l2": "inputs larger than L2 (populations 4.8 GB FP32); no flush",
+                   "timing": "CUDA events on the library stream around lbm_step(K); per-kernel event pairs"},
+        "gpu_launches": r["launches"],
+        "clocks": clocks,
+        "roofline": r["roofline"],
+        "e2e": r["e2e"],
+        "cpu_baseline": base,
+        "secondary": r["extra"],
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

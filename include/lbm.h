@@ -1,0 +1,223 @@
+/*
+ * lbm.h -- C ABI of the GB300 active lattice Boltzmann library (liblbm.so).
+ *
+ * The library advances the active lattice Boltzmann model of Nesbitt,
+ * Pruessner & Lee (arXiv:1902.00530) on periodic D2Q9 lattices:
+ *   f_i(t+1, r + e_i) - f_i(t, r) = -(f_i - f^SS_i)/tau + eta_i
+ * (Sec. 2, Eq. (fevolution2)) with f^SS_i = xi_i(rho, u*) (Eq. (fssD2Q7),
+ * lifted to D2Q9 with c_s^2 = 1/3), u* given by the MIPS closure (Sec. 3,
+ * Eq. (bu_mips) with the U_max clamp), the CIL closure (Sec. 4, Eqs. (bu_CIL),
+ * (U0)) or the passive limit u* = u (App. A.1), zero-sum uniform noise
+ * (Eq. (noiseDensityConservation)) and the negative correction of App. A.3,
+ * in the step order of App. A.2.
+ *
+ * Conventions for every call:
+ *  - Ownership.  The caller owns all device memory and the CUDA stream: it
+ *    allocates the state and scratch buffers whose sizes lbm_buffer_bytes
+ *    reports and hands them over with lbm_bind.  The context owns only host
+ *    descriptors, tuning results and cached CUDA graphs.  Every call that
+ *    launches device work enqueues it on the bound stream; calls documented as
+ *    "syncs" wait for that stream before returning.
+ *  - Errors.  Every call returns an lbm_status.  Nothing throws across the ABI
+ *    and nothing exits.  lbm_last_error(ctx) describes the last failure.
+ *    Device-side conditions (non-finite observables, a barrier that timed out)
+ *    are latched in a device flag and reported by the next syncing call.
+ *  - Populations.  Device storage is structure-of-arrays per lattice:
+ *    f[i][y][pitch] for i = 0..8, x fastest, with the D2Q9 velocities
+ *    e = (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1) (-1,-1) (1,-1).
+ *    Calls that exchange populations with the caller use dense FP32
+ *    [9][ny][nx] arrays regardless of the storage type.
+ *  - Threads.  One context per host thread; contexts are independent.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_INVALID_ARG = 1, /* a bad argument; nothing was changed            */
+    LBM_ERR_UNBOUND = 2,     /* buffers not bound (lbm_bind) or not initialised */
+    LBM_ERR_CUDA = 3,        /* a CUDA runtime call failed                      */
+    LBM_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up              */
+    LBM_ERR_NUMERIC = 5,     /* non-finite observables were detected            */
+    LBM_ERR_UNSUPPORTED = 6  /* valid request this build does not provide       */
+} lbm_status;
+
+typedef enum {
+    LBM_PASSIVE = 0, /* u* = u: standard BGK lattice Boltzmann (App. A.1)          */
+    LBM_MIPS = 1,    /* u* = C (1 - rho/rho*) grad rho, clamped to U_max (Sec. 3)  */
+    LBM_CIL = 2      /* u* = U0(rho) u/|u|, U0 = max(B - A rho^2, 0) (Sec. 4)      */
+} lbm_model;
+
+typedef enum {
+    LBM_F32 = 0,          /* populations stored as FP32                              */
+    LBM_F16_SHIFTED = 1,  /* stored as FP16 of f_i - w_i rho0, collided in FP32      */
+    LBM_BF16_SHIFTED = 2  /* stored as BF16 of f_i - w_i rho0, collided in FP32      */
+} lbm_storage;
+
+/* One periodic rectangular lattice (Sec. 4: "rectangular geometry with
+ * periodic boundary conditions").  id keys the lattice's random streams: two
+ * lattices with the same seed, id and state evolve identically. */
+typedef struct {
+    int32_t nx, ny;   /* sites along x and y, each in [1, 65536]        */
+    int32_t storage;  /* an lbm_storage value                           */
+    int32_t id;       /* random-stream id, in [0, 2^24)                 */
+} lbm_lattice;
+
+/* Model parameters (App. C tables), all in lattice units dx = dt = c = 1. */
+typedef struct {
+    double tau;      /* relaxation time, > 1/2; the paper uses tau >= 1 (App. A.3) */
+    double sigma;    /* noise: eta~_i uniform on [-sigma, sigma] (Sec. 2); >= 0    */
+    double C;        /* MIPS gradient sensitivity (Eq. (bu_mips))                  */
+    double rho_star; /* MIPS density ceiling rho* > 0                              */
+    double u_max;    /* MIPS speed clamp U_max >= 0                                */
+    double A, B;     /* CIL U0(rho) = max(B - A rho^2, 0) (Eq. (U0))               */
+    double rho0;     /* 16-bit storage shift; 0 = the mean density set by lbm_init */
+} lbm_params;
+
+/* Seeded initial state (App. C.2): per site, rho = rho_mean (1 + rho_amp (2U-1))
+ * and u by u_kind; populations are set to f^SS(rho, u) computed in FP64.
+ *   u_kind 0: u = (ux0, uy0) + u_amp (2U1 - 1, 2U2 - 1)
+ *   u_kind 1: u = (ux0, uy0) + u_amp (cos 2 pi U1, sin 2 pi U1)
+ *   u_kind 2: u = U0(rho) (cos 2 pi U1, sin 2 pi U1)   (the paper's CIL start) */
+typedef struct {
+    double rho_mean, rho_amp;
+    int32_t u_kind;
+    double u_amp, ux0, uy0;
+} lbm_init_spec;
+
+/* One observable record of a stored state (after the step's correction):
+ * mass = sum rho; phi = |sum rho u| / sum rho (Eq. (phi));
+ * drho_y = population std over x of rho_y(x) = mean over y of rho (App. D);
+ * drho_x = the same with axes swapped; var_rho = population variance of rho;
+ * zeta = sum rho (B - |u|) / sum rho (App. D).  t is the time of the state. */
+typedef struct {
+    int64_t t;
+    double mass, phi, drho_y, drho_x, var_rho, zeta;
+} lbm_obs;
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* Create a context for one lattice.  Validates the parameters: tau <= 1/2,
+ * sigma < 0, a NaN parameter, nx or ny outside [1, 65536], an unknown model or
+ * storage, or a non-positive rho_star (MIPS) returns LBM_ERR_INVALID_ARG and
+ * sets *out = NULL.  Host only; no CUDA call. */
+lbm_status lbm_create(const lbm_lattice *lattice, lbm_model model, const lbm_params *params,
+                      lbm_ctx **out);
+
+/* Create a context for n independent lattices advanced together (a batch, as
+ * in the paper's sweeps over density and activity, App. C.3-C.4).  Arrays
+ * hold n entries.  Lattice k of the batch is addressed by index k below.
+ * Same validation as lbm_create.  Host only. */
+lbm_status lbm_create_batch(int32_t n, const lbm_lattice *lattices, const lbm_model *models,
+                            const lbm_params *params, lbm_ctx **out);
+
+/* Observable sampling: every sample_every steps (0 = never) the step's
+ * stored state is reduced to one lbm_obs record per lattice into a device
+ * ring of ring_capacity records per lattice (App. C: samples every t_sample
+ * steps).  Must be called before lbm_buffer_bytes/lbm_bind.  Host only. */
+lbm_status lbm_set_sampling(lbm_ctx *ctx, int32_t sample_every, int32_t ring_capacity);
+
+/* Device bytes the caller must allocate: state (two population buffers per
+ * lattice) and scratch (reduction partials, observable ring, step counter,
+ * descriptors, error flag).  Host only. */
+lbm_status lbm_buffer_bytes(const lbm_ctx *ctx, size_t *state_bytes, size_t *scratch_bytes);
+
+/* Hand over device buffers (256-byte aligned, at least the sizes above) and
+ * the stream (a cudaStream_t; NULL = legacy default stream).  The caller keeps
+ * ownership and must keep them alive until lbm_destroy or the next lbm_bind.
+ * Uploads descriptors; syncs. */
+lbm_status lbm_bind(lbm_ctx *ctx, void *state_dev, void *scratch_dev, void *cuda_stream);
+
+/* Seeded initial state of every lattice (App. C.2); specs holds one entry per
+ * lattice.  Sets t = 0, clears the observable ring.  Enqueued; syncs. */
+lbm_status lbm_init(lbm_ctx *ctx, uint64_t seed, const lbm_init_spec *specs);
+
+/* Advance every lattice n >= 0 steps (App. A.2 steps 1-6 per step), t += n.
+ * Enqueued on the bound stream; returns without waiting.  The first call
+ * tunes the launch shape unless lbm_set_tuning disabled it.  Requires
+ * t + n < 2^32 (the step index is one 32-bit word of the noise counter). */
+lbm_status lbm_step(lbm_ctx *ctx, int64_t n);
+
+/* Density and velocity of every site of lattice `lattice` in its stored
+ * state (Eq. (D2Q7macroscopic) on D2Q9): rho, ux, uy are DEVICE pointers to
+ * dense FP32 [ny][nx] arrays, written asynchronously on the bound stream. */
+lbm_status lbm_moments(lbm_ctx *ctx, int32_t lattice, float *rho, float *ux, float *uy);
+
+/* Observables of lattice `lattice` in its current stored state, computed now
+ * by the same fused reduction the sample steps use.  Syncs; returns
+ * LBM_ERR_NUMERIC if a sum is not finite. */
+lbm_status lbm_observables(lbm_ctx *ctx, int32_t lattice, lbm_obs *out);
+
+/* Copy the sampled records of lattice `lattice` (oldest first, at most cap)
+ * to host memory and report how many were written; the ring is then empty
+ * for that lattice.  Records beyond the ring capacity overwrite the oldest.
+ * Syncs. */
+lbm_status lbm_observable_series(lbm_ctx *ctx, int32_t lattice, lbm_obs *out, int32_t cap,
+                                 int32_t *n_out);
+
+/* Copy lattice `lattice`'s populations out as dense FP32 [9][ny][nx]; dst is a
+ * host pointer if dst_is_host, else a device pointer.  16-bit storage is
+ * expanded to f_i = w_i rho0 + s_i.  Syncs. */
+lbm_status lbm_get_state(lbm_ctx *ctx, int32_t lattice, float *dst, int32_t dst_is_host);
+
+/* Replace lattice `lattice`'s populations by dense FP32 [9][ny][nx] from src
+ * (host if src_is_host, else device).  16-bit storage stores s_i = f_i -
+ * w_i rho0 rounded to nearest.  Does not change t.  Syncs. */
+lbm_status lbm_set_state(lbm_ctx *ctx, int32_t lattice, const float *src, int32_t src_is_host);
+
+/* Current time step t (steps taken since lbm_init or loaded with lbm_load). */
+lbm_status lbm_get_time(const lbm_ctx *ctx, int64_t *t);
+
+/* Serialise all lattices (raw storage, t, seed) to a file / restore them.
+ * The context must have the same lattices, models and storage.  Because the
+ * noise is counter-based (keyed by seed, site, t and id), a run resumed from a
+ * file continues bit-identically.  Syncs. */
+lbm_status lbm_save(lbm_ctx *ctx, const char *path);
+lbm_status lbm_load(lbm_ctx *ctx, const char *path);
+
+/* Launch-shape tuning.  mode 0: automatic on the first lbm_step (default);
+ * mode 1: off, use the fixed shape (vec, rows) given; vec = sites per thread
+ * along x (1, 2, 4 or 8, dividing nx) and rows = rows per warp strip. */
+lbm_status lbm_set_tuning(lbm_ctx *ctx, int32_t mode, int32_t vec, int32_t rows);
+
+/* Run the tuner now (times candidate shapes on the bound buffers without
+ * changing the state).  Syncs. */
+lbm_status lbm_tune(lbm_ctx *ctx);
+
+/* The launch shape in use for lattice `lattice`: vec, rows, warps per block. */
+lbm_status lbm_get_tuning(const lbm_ctx *ctx, int32_t lattice, int32_t *vec, int32_t *rows,
+                          int32_t *warps);
+
+/* CUDA-graph replay of lbm_step: 1 = capture each distinct step sequence once
+ * and replay it (default), 0 = launch kernels directly. */
+lbm_status lbm_set_graphs(lbm_ctx *ctx, int32_t enabled);
+
+/* Number of kernels the last lbm_step call enqueued (graph nodes included). */
+lbm_status lbm_last_launch_count(const lbm_ctx *ctx, int64_t *count);
+
+/* Kernel timing on the bound stream.  While enabled, lbm_step launches its
+ * kernels directly (no graph replay) with a CUDA event pair around each one;
+ * lbm_profile_read syncs and reports the summed device time of the fused step
+ * kernels and of all other kernels since profiling was enabled (or last
+ * read), and the number of step-kernel launches; reading resets the sums. */
+lbm_status lbm_set_profiling(lbm_ctx *ctx, int32_t enabled);
+lbm_status lbm_profile_read(lbm_ctx *ctx, double *step_ms, int64_t *step_launches, double *other_ms);
+
+/* Text of the last error on this context (never NULL; "" if none). */
+const char *lbm_last_error(const lbm_ctx *ctx);
+
+/* Release host resources.  NULL is a no-op.  Does not free caller buffers. */
+void lbm_destroy(lbm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

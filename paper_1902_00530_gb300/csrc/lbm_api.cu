@@ -1,0 +1,1021 @@
+// lbm_api.cu -- host side of the C ABI declared in include/lbm.h.
+//
+// The context holds host descriptors only; all device memory (population
+// buffers and scratch) belongs to the caller.  Scratch layout (256-byte
+// aligned regions): control words (step counter t, error flag), per-lattice
+// counters, descriptor tables (all lattices, then one table per launch group),
+// initial-state specs, and per lattice the reduction partials, the finaliser
+// partials, the observable ring and the on-demand record.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "lbm_internal.h"
+
+using namespace lbm;
+
+namespace {
+
+constexpr int ROWS_MIN = 16;       // smallest strip height; scratch is sized for it
+constexpr int CHUNK_COLS = 256;    // columns / rows / strips per finaliser block
+constexpr int NCHUNK_MAX = 1024;
+constexpr int GRAPH_CHUNK_MAX = 256;
+
+size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+size_t elem_bytes(int storage) { return storage == LBM_F32 ? 4 : 2; }
+
+struct LatHost {
+    lbm_lattice lat;
+    int model;
+    lbm_params p;
+    float rho0 = 1.f;
+    size_t pitch = 0, buf_bytes = 0, state_off = 0;
+    size_t scal_off = 0, colp_off = 0, rowp_off = 0, finp_off = 0, ring_off = 0, now_off = 0, ctr_off = 0;
+    int nsx = 0, nsy = 0, nchunk = 1, nchunk_max = 1;
+    int group = 0, block_begin = 0;
+    int64_t consumed = 0;
+};
+
+struct GroupHost {
+    int model = 0, storage = 0;
+    std::vector<int> members;
+    int vec = 1, rows = 32, warps = 4, blocks = 0;
+    size_t desc_off = 0;
+};
+
+struct GraphKey {
+    int64_t n, phase;
+    int parity;
+    bool operator<(const GraphKey &o) const
+    {
+        return std::tie(n, phase, parity) < std::tie(o.n, o.phase, o.parity);
+    }
+};
+
+}  // namespace
+
+struct lbm_ctx {
+    std::vector<LatHost> lats;
+    std::vector<GroupHost> groups;
+    int32_t sample_every = 0, ring_cap = 0;
+    char *state = nullptr, *scratch = nullptr;
+    cudaStream_t stream = nullptr;
+    bool bound = false, initialized = false;
+    uint64_t seed = 0;
+    int64_t t = 0;
+    int parity = 0;
+    std::string err;
+    size_t state_bytes = 0, scratch_bytes = 0;
+    size_t all_desc_off = 0, spec_off = 0;
+    int max_chunk = 1;
+    int tune_mode = 0, fixed_vec = 0, fixed_rows = 0;
+    bool tuned = false, use_graphs = true;
+    std::map<GraphKey, cudaGraphExec_t> graphs;
+    int64_t last_launches = 0;
+    // kernel timing (lbm_set_profiling)
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, bool>> ev_marks;  // (first event index, is step kernel)
+    size_t ev_used = 0;
+};
+
+namespace {
+
+lbm_status fail(lbm_ctx *c, lbm_status s, const std::string &msg)
+{
+    if (c) c->err = msg;
+    return s;
+}
+
+lbm_status cuda_fail(lbm_ctx *c, cudaError_t e, const char *what)
+{
+    return fail(c, LBM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                    \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
+    } while (0)
+
+bool finite_all(const lbm_params &p)
+{
+    const double v[] = {p.tau, p.sigma, p.C, p.rho_star, p.u_max, p.A, p.B, p.rho0};
+    for (double x : v)
+        if (!std::isfinite(x)) return false;
+    return true;
+}
+
+std::string validate(const lbm_lattice &l, int model, const lbm_params &p)
+{
+    if (l.nx < 1 || l.ny < 1 || l.nx > 65536 || l.ny > 65536) return "nx, ny must be in [1, 65536]";
+    if (l.storage < LBM_F32 || l.storage > LBM_BF16_SHIFTED) return "unknown storage type";
+    if (l.id < 0 || l.id >= (1 << 24)) return "lattice id must be in [0, 2^24)";
+    if (model < LBM_PASSIVE || model > LBM_CIL) return "unknown model";
+    if (!finite_all(p)) return "parameters must be finite";
+    if (!(p.tau > 0.5)) return "tau must exceed 1/2";
+    if (p.sigma < 0) return "sigma must be >= 0";
+    if (p.rho0 < 0) return "rho0 must be >= 0";
+    if (model == LBM_MIPS && !(p.rho_star > 0)) return "MIPS needs rho_star > 0";
+    if (model == LBM_MIPS && p.u_max < 0) return "MIPS needs u_max >= 0";
+    return "";
+}
+
+int allowed_vec(int storage, int v)
+{
+    if (storage == LBM_F32) return v == 1 || v == 2 || v == 4;
+    return v == 1 || v == 2 || v == 4 || v == 8;
+}
+
+int default_vec(const lbm_ctx *c, const GroupHost &g)
+{
+    const int cands_f32[] = {4, 2, 1};
+    const int cands_16[] = {8, 4, 2, 1};
+    const int *cands = g.storage == LBM_F32 ? cands_f32 : cands_16;
+    const int nc = g.storage == LBM_F32 ? 3 : 4;
+    for (int k = 0; k < nc; ++k) {
+        bool ok = true;
+        for (int m : g.members) ok = ok && (c->lats[m].lat.nx % cands[k] == 0);
+        if (ok) return cands[k];
+    }
+    return 1;
+}
+
+// Scratch / state layout; depends only on the lattices and sampling settings.
+void layout(lbm_ctx *c)
+{
+    size_t so = 0;
+    for (auto &L : c->lats) {
+        const size_t eb = elem_bytes(L.lat.storage);
+        const size_t align_elems = 128 / eb;
+        L.pitch = ((size_t)L.lat.nx + align_elems - 1) / align_elems * align_elems;
+        L.buf_bytes = align256(9 * (size_t)L.lat.ny * L.pitch * eb);
+        L.state_off = so;
+        so += 2 * L.buf_bytes;
+    }
+    c->state_bytes = so;
+    const int nl = (int)c->lats.size();
+    size_t o = 256;  // [0]: t (uint32), [4]: error flag (uint32)
+    for (auto &L : c->lats) {
+        L.ctr_off = o;
+        o += 16;
+    }
+    o = align256(o);
+    c->all_desc_off = o;
+    o = align256(o + nl * sizeof(LatDesc));
+    for (auto &g : c->groups) {
+        g.desc_off = o;
+        o = align256(o + g.members.size() * sizeof(LatDesc));
+    }
+    c->spec_off = o;
+    o = align256(o + nl * init_spec_bytes());
+    for (auto &L : c->lats) {
+        const int nsx_max = ceil_div(L.lat.nx, 32);
+        const int nsy_max = ceil_div(L.lat.ny, ROWS_MIN);
+        const long long nstrip_max = (long long)nsx_max * nsy_max;
+        L.nchunk_max = std::min(NCHUNK_MAX,
+                                std::max(1, ceil_div(std::max<long long>({L.lat.nx, L.lat.ny, nstrip_max}), CHUNK_COLS)));
+        L.scal_off = o;
+        o = align256(o + nstrip_max * 5 * sizeof(double));
+        L.colp_off = o;
+        o = align256(o + (size_t)nsy_max * L.lat.nx * sizeof(double));
+        L.rowp_off = o;
+        o = align256(o + (size_t)nsx_max * L.lat.ny * sizeof(double));
+        L.finp_off = o;
+        o = align256(o + (size_t)L.nchunk_max * 9 * sizeof(double));
+        L.ring_off = o;
+        o = align256(o + (size_t)std::max(c->ring_cap, 1) * 8 * sizeof(double));
+        L.now_off = o;
+        o = align256(o + 8 * sizeof(double));
+    }
+    c->scratch_bytes = o;
+}
+
+LatDesc make_desc(const lbm_ctx *c, const LatHost &L, int block_begin, const GroupHost &g)
+{
+    LatDesc d;
+    std::memset(&d, 0, sizeof(d));
+    char *sb = c->state + L.state_off;
+    d.f[0] = sb;
+    d.f[1] = sb + L.buf_bytes;
+    d.scal = reinterpret_cast<double *>(c->scratch + L.scal_off);
+    d.colp = reinterpret_cast<double *>(c->scratch + L.colp_off);
+    d.rowp = reinterpret_cast<double *>(c->scratch + L.rowp_off);
+    d.finp = reinterpret_cast<double *>(c->scratch + L.finp_off);
+    d.ring = reinterpret_cast<double *>(c->scratch + L.ring_off);
+    d.now = reinterpret_cast<double *>(c->scratch + L.now_off);
+    d.counters = reinterpret_cast<unsigned *>(c->scratch + L.ctr_off);
+    d.nx = L.lat.nx;
+    d.ny = L.lat.ny;
+    d.pitch = (int)L.pitch;
+    d.id = L.lat.id;
+    d.nsx = ceil_div(L.lat.nx, 32 * g.vec);
+    d.nsy = ceil_div(L.lat.ny, g.rows);
+    d.rows = g.rows;
+    d.block_begin = block_begin;
+    d.ring_cap = std::max(c->ring_cap, 1);
+    const long long nstrip = (long long)d.nsx * d.nsy;
+    d.nchunk = std::min(L.nchunk_max, std::max(1, ceil_div(std::max<long long>({L.lat.nx, L.lat.ny, nstrip}), CHUNK_COLS)));
+    d.omega = (float)(1.0 / L.p.tau);
+    d.sigma_q = (float)(L.p.sigma / 16777216.0);
+    d.C = (float)L.p.C;
+    d.rho_star = (float)L.p.rho_star;
+    d.inv_rho_star = L.p.rho_star > 0 ? (float)(1.0 / L.p.rho_star) : 0.f;
+    d.u_max = (float)L.p.u_max;
+    d.u_max2 = (float)(L.p.u_max * L.p.u_max);
+    d.A = (float)L.p.A;
+    d.B = (float)L.p.B;
+    d.rho0 = L.rho0;
+    return d;
+}
+
+// Recompute strip geometry from the group shapes and upload all descriptor
+// tables.  Syncs.
+lbm_status upload_descs(lbm_ctx *c)
+{
+    std::vector<LatDesc> all(c->lats.size());
+    c->max_chunk = 1;
+    for (size_t gi = 0; gi < c->groups.size(); ++gi) {
+        GroupHost &g = c->groups[gi];
+        std::vector<LatDesc> gd;
+        int blocks = 0;
+        for (int m : g.members) {
+            LatHost &L = c->lats[m];
+            LatDesc d = make_desc(c, L, blocks, g);
+            L.nsx = d.nsx;
+            L.nsy = d.nsy;
+            L.nchunk = d.nchunk;
+            L.block_begin = blocks;
+            blocks += ceil_div((long long)d.nsx * d.nsy, g.warps);
+            gd.push_back(d);
+            all[m] = d;
+            c->max_chunk = std::max(c->max_chunk, d.nchunk);
+        }
+        g.blocks = blocks;
+        CK(cudaMemcpyAsync(c->scratch + g.desc_off, gd.data(), gd.size() * sizeof(LatDesc),
+                           cudaMemcpyHostToDevice, c->stream),
+           "upload group descriptors");
+    }
+    CK(cudaMemcpyAsync(c->scratch + c->all_desc_off, all.data(), all.size() * sizeof(LatDesc),
+                       cudaMemcpyHostToDevice, c->stream),
+       "upload descriptors");
+    CK(cudaStreamSynchronize(c->stream), "synchronise after descriptor upload");
+    return LBM_OK;
+}
+
+const LatDesc *all_desc(const lbm_ctx *c)
+{
+    return reinterpret_cast<const LatDesc *>(c->scratch + c->all_desc_off);
+}
+uint32_t *t_dev(const lbm_ctx *c) { return reinterpret_cast<uint32_t *>(c->scratch); }
+unsigned *err_dev(const lbm_ctx *c) { return reinterpret_cast<unsigned *>(c->scratch + 4); }
+
+cudaError_t launch_group_step(const lbm_ctx *c, const GroupHost &g, int src, uint32_t k, bool sample)
+{
+    StepArgs a;
+    a.desc = reinterpret_cast<const LatDesc *>(c->scratch + g.desc_off);
+    a.nlat = (int)g.members.size();
+    a.src = src;
+    a.t_ptr = t_dev(c);
+    a.k = k;
+    a.key0 = (uint32_t)c->seed;
+    a.key1 = (uint32_t)(c->seed >> 32);
+    if (g.storage == LBM_F32) return launch_step_f32(g.model, g.vec, sample, a, g.blocks, g.warps, c->stream);
+    if (g.storage == LBM_F16_SHIFTED) return launch_step_f16(g.model, g.vec, sample, a, g.blocks, g.warps, c->stream);
+    return launch_step_bf16(g.model, g.vec, sample, a, g.blocks, g.warps, c->stream);
+}
+
+cudaError_t launch_group_observe(const lbm_ctx *c, const GroupHost &g, int src)
+{
+    StepArgs a;
+    a.desc = reinterpret_cast<const LatDesc *>(c->scratch + g.desc_off);
+    a.nlat = (int)g.members.size();
+    a.src = src;
+    a.t_ptr = t_dev(c);
+    a.k = 0;
+    a.key0 = a.key1 = 0;
+    if (g.storage == LBM_F32) return launch_observe_f32(g.vec, a, g.blocks, g.warps, c->stream);
+    if (g.storage == LBM_F16_SHIFTED) return launch_observe_f16(g.vec, a, g.blocks, g.warps, c->stream);
+    return launch_observe_bf16(g.vec, a, g.blocks, g.warps, c->stream);
+}
+
+// Kernel timing: an event pair around a launch when profiling is on.
+cudaError_t prof_begin(lbm_ctx *c, bool is_step)
+{
+    if (!c->profiling) return cudaSuccess;
+    while (c->ev_pool.size() < c->ev_used + 2) {
+        cudaEvent_t e;
+        cudaError_t err = cudaEventCreate(&e);
+        if (err != cudaSuccess) return err;
+        c->ev_pool.push_back(e);
+    }
+    c->ev_marks.push_back({(int)c->ev_used, is_step});
+    cudaError_t err = cudaEventRecord(c->ev_pool[c->ev_used], c->stream);
+    c->ev_used += 2;
+    return err;
+}
+
+cudaError_t prof_end(lbm_ctx *c)
+{
+    if (!c->profiling) return cudaSuccess;
+    return cudaEventRecord(c->ev_pool[c->ev_marks.back().first + 1], c->stream);
+}
+
+// Enqueue n steps starting at host time t0 from buffer parity p0.
+lbm_status enqueue_steps(lbm_ctx *c, int64_t n, int64_t t0, int p0, int64_t *launches)
+{
+    for (int64_t k = 0; k < n; ++k) {
+        const bool sample = c->sample_every > 0 && ((t0 + k + 1) % c->sample_every == 0);
+        for (const GroupHost &g : c->groups) {
+            CK(prof_begin(c, true), "record event");
+            CK(launch_group_step(c, g, (int)((p0 + k) & 1), (uint32_t)k, sample), "launch step kernel");
+            CK(prof_end(c), "record event");
+            ++*launches;
+        }
+        if (sample) {
+            CK(prof_begin(c, false), "record event");
+            CK(launch_finalize(all_desc(c), (int)c->lats.size(), c->max_chunk, t_dev(c), (uint32_t)k, 1,
+                               err_dev(c), c->stream),
+               "launch finaliser");
+            CK(prof_end(c), "record event");
+            ++*launches;
+        }
+    }
+    CK(prof_begin(c, false), "record event");
+    CK(launch_advance_time(t_dev(c), (uint32_t)n, c->stream), "launch time advance");
+    CK(prof_end(c), "record event");
+    ++*launches;
+    return LBM_OK;
+}
+
+void drop_graphs(lbm_ctx *c)
+{
+    for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    c->graphs.clear();
+}
+
+lbm_status read_error_flag(lbm_ctx *c)
+{
+    unsigned flag = 0;
+    CK(cudaMemcpyAsync(&flag, err_dev(c), sizeof(flag), cudaMemcpyDeviceToHost, c->stream), "read error flag");
+    CK(cudaStreamSynchronize(c->stream), "synchronise");
+    if (flag) {
+        const unsigned zero = 0;
+        CK(cudaMemcpyAsync(err_dev(c), &zero, sizeof(zero), cudaMemcpyHostToDevice, c->stream), "clear error flag");
+        CK(cudaStreamSynchronize(c->stream), "synchronise");
+        if (flag & DEVERR_TIMEOUT) return fail(c, LBM_ERR_TIMEOUT, "a device-side wait timed out");
+        return fail(c, LBM_ERR_NUMERIC, "non-finite observable sums");
+    }
+    return LBM_OK;
+}
+
+lbm_status require_ready(lbm_ctx *c, bool need_init)
+{
+    if (!c) return LBM_ERR_INVALID_ARG;
+    if (!c->bound) return fail(c, LBM_ERR_UNBOUND, "buffers are not bound (lbm_bind)");
+    if (need_init && !c->initialized) return fail(c, LBM_ERR_UNBOUND, "state is not initialised (lbm_init)");
+    return LBM_OK;
+}
+
+lbm_status tune_group(lbm_ctx *c, GroupHost &g)
+{
+    std::vector<int> vecs;
+    const int all_v[] = {1, 2, 4, 8};
+    for (int v : all_v) {
+        if (!allowed_vec(g.storage, v)) continue;
+        bool ok = true;
+        for (int m : g.members) ok = ok && (c->lats[m].lat.nx % v == 0);
+        if (ok) vecs.push_back(v);
+    }
+    const int rows_c[] = {16, 32, 64, 128};
+    const int warps_c[] = {4, 8};
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0), "create event");
+    CK(cudaEventCreate(&e1), "create event");
+    float best = 1e30f;
+    int bv = g.vec, br = g.rows, bw = g.warps;
+    long long max_ny = 1;
+    for (int m : g.members) max_ny = std::max<long long>(max_ny, c->lats[m].lat.ny);
+    for (int v : vecs)
+        for (int r : rows_c) {
+            if (r > 16 && r > 2 * max_ny) continue;
+            for (int w : warps_c) {
+                g.vec = v;
+                g.rows = r;
+                g.warps = w;
+                lbm_status st = upload_descs(c);
+                if (st != LBM_OK) return st;
+                CK(launch_group_step(c, g, c->parity, 0, false), "tuning launch");
+                CK(cudaEventRecord(e0, c->stream), "record event");
+                const int reps = 3;
+                for (int q = 0; q < reps; ++q) CK(launch_group_step(c, g, c->parity, 0, false), "tuning launch");
+                CK(cudaEventRecord(e1, c->stream), "record event");
+                CK(cudaEventSynchronize(e1), "synchronise event");
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, e0, e1), "event time");
+                if (ms < best) {
+                    best = ms;
+                    bv = v;
+                    br = r;
+                    bw = w;
+                }
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    g.vec = bv;
+    g.rows = br;
+    g.warps = bw;
+    return upload_descs(c);
+}
+
+lbm_status do_tune(lbm_ctx *c)
+{
+    for (auto &g : c->groups) {
+        lbm_status st = tune_group(c, g);
+        if (st != LBM_OK) return st;
+    }
+    drop_graphs(c);
+    c->tuned = true;
+    return LBM_OK;
+}
+
+lbm_status create_common(int32_t n, const lbm_lattice *lats, const lbm_model *models, const lbm_params *ps,
+                         lbm_ctx **out)
+{
+    if (!out) return LBM_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (n < 1 || !lats || !models || !ps) return LBM_ERR_INVALID_ARG;
+    lbm_ctx *c = new (std::nothrow) lbm_ctx();
+    if (!c) return LBM_ERR_INVALID_ARG;
+    for (int32_t k = 0; k < n; ++k) {
+        const std::string why = validate(lats[k], (int)models[k], ps[k]);
+        if (!why.empty()) {
+            delete c;
+            return LBM_ERR_INVALID_ARG;
+        }
+        LatHost L;
+        L.lat = lats[k];
+        L.model = (int)models[k];
+        L.p = ps[k];
+        L.rho0 = ps[k].rho0 > 0 ? (float)ps[k].rho0 : 1.f;
+        c->lats.push_back(L);
+    }
+    // launch groups: one per (model, storage)
+    for (int32_t k = 0; k < n; ++k) {
+        LatHost &L = c->lats[k];
+        int gi = -1;
+        for (size_t q = 0; q < c->groups.size(); ++q)
+            if (c->groups[q].model == L.model && c->groups[q].storage == L.lat.storage) gi = (int)q;
+        if (gi < 0) {
+            GroupHost g;
+            g.model = L.model;
+            g.storage = L.lat.storage;
+            c->groups.push_back(g);
+            gi = (int)c->groups.size() - 1;
+        }
+        c->groups[gi].members.push_back(k);
+        L.group = gi;
+    }
+    for (auto &g : c->groups) {
+        g.vec = default_vec(c, g);
+        g.rows = 32;
+        g.warps = 4;
+    }
+    layout(c);
+    *out = c;
+    return LBM_OK;
+}
+
+}  // namespace
+
+// ============================================================================
+// C ABI
+// ============================================================================
+extern "C" {
+
+lbm_status lbm_create(const lbm_lattice *lattice, lbm_model model, const lbm_params *params, lbm_ctx **out)
+{
+    return create_common(1, lattice, &model, params, out);
+}
+
+lbm_status lbm_create_batch(int32_t n, const lbm_lattice *lattices, const lbm_model *models,
+                            const lbm_params *params, lbm_ctx **out)
+{
+    return create_common(n, lattices, models, params, out);
+}
+
+lbm_status lbm_set_sampling(lbm_ctx *c, int32_t sample_every, int32_t ring_capacity)
+{
+    if (!c) return LBM_ERR_INVALID_ARG;
+    if (c->bound) return fail(c, LBM_ERR_INVALID_ARG, "set sampling before lbm_bind");
+    if (sample_every < 0 || ring_capacity < 0 || ring_capacity > (1 << 24))
+        return fail(c, LBM_ERR_INVALID_ARG, "sample_every >= 0 and 0 <= ring_capacity <= 2^24");
+    if (sample_every > 0 && ring_capacity < 1)
+        return fail(c, LBM_ERR_INVALID_ARG, "sampling needs ring_capacity >= 1");
+    c->sample_every = sample_every;
+    c->ring_cap = ring_capacity;
+    layout(c);
+    return LBM_OK;
+}
+
+lbm_status lbm_buffer_bytes(const lbm_ctx *c, size_t *state_bytes, size_t *scratch_bytes)
+{
+    if (!c || !state_bytes || !scratch_bytes) return LBM_ERR_INVALID_ARG;
+    *state_bytes = c->state_bytes;
+    *scratch_bytes = c->scratch_bytes;
+    return LBM_OK;
+}
+
+lbm_status lbm_bind(lbm_ctx *c, void *state_dev, void *scratch_dev, void *cuda_stream)
+{
+    if (!c) return LBM_ERR_INVALID_ARG;
+    if (!state_dev || !scratch_dev) return fail(c, LBM_ERR_INVALID_ARG, "null buffer");
+    if (((uintptr_t)state_dev & 255) || ((uintptr_t)scratch_dev & 255))
+        return fail(c, LBM_ERR_INVALID_ARG, "buffers must be 256-byte aligned");
+    drop_graphs(c);
+    c->state = static_cast<char *>(state_dev);
+    c->scratch = static_cast<char *>(scratch_dev);
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    c->bound = true;
+    c->initialized = false;
+    CK(cudaMemsetAsync(c->scratch, 0, c->all_desc_off, c->stream), "clear control words");
+    return upload_descs(c);
+}
+
+lbm_status lbm_init(lbm_ctx *c, uint64_t seed, const lbm_init_spec *specs)
+{
+    lbm_status st = require_ready(c, false);
+    if (st != LBM_OK) return st;
+    if (!specs) return fail(c, LBM_ERR_INVALID_ARG, "null init spec");
+    const size_t nl = c->lats.size();
+    std::vector<char> packed(nl * init_spec_bytes());
+    for (size_t k = 0; k < nl; ++k) {
+        const lbm_init_spec &s = specs[k];
+        const double v[] = {s.rho_mean, s.rho_amp, s.u_amp, s.ux0, s.uy0};
+        for (double x : v)
+            if (!std::isfinite(x)) return fail(c, LBM_ERR_INVALID_ARG, "init spec must be finite");
+        if (s.u_kind < 0 || s.u_kind > 2) return fail(c, LBM_ERR_INVALID_ARG, "u_kind must be 0, 1 or 2");
+        if (!(s.rho_mean > 0)) return fail(c, LBM_ERR_INVALID_ARG, "rho_mean must be > 0");
+        LatHost &L = c->lats[k];
+        L.rho0 = L.p.rho0 > 0 ? (float)L.p.rho0 : (float)s.rho_mean;
+        pack_init_spec(packed.data() + k * init_spec_bytes(), s.rho_mean, s.rho_amp, s.u_kind, s.u_amp, s.ux0,
+                       s.uy0, L.p.A, L.p.B);
+    }
+    st = upload_descs(c);
+    if (st != LBM_OK) return st;
+    CK(cudaMemcpyAsync(c->scratch + c->spec_off, packed.data(), packed.size(), cudaMemcpyHostToDevice, c->stream),
+       "upload init specs");
+    c->seed = seed;
+    for (size_t k = 0; k < nl; ++k) {
+        const LatHost &L = c->lats[k];
+        CK(launch_init(L.lat.storage, all_desc(c) + k, c->scratch + c->spec_off + k * init_spec_bytes(), 1,
+                       (long long)L.lat.nx * L.lat.ny, 0, seed, c->stream),
+           "launch init kernel");
+        c->lats[k].consumed = 0;
+    }
+    CK(cudaMemsetAsync(c->scratch, 0, c->all_desc_off, c->stream), "clear control words");
+    CK(cudaStreamSynchronize(c->stream), "synchronise after init");
+    c->t = 0;
+    c->parity = 0;
+    c->initialized = true;
+    drop_graphs(c);
+    return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_ctx *c, int64_t n)
+{
+    lbm_status st = require_ready(c, true);
+    if (st != LBM_OK) return st;
+    if (n < 0) return fail(c, LBM_ERR_INVALID_ARG, "n must be >= 0");
+    if (c->t + n >= (int64_t(1) << 32)) return fail(c, LBM_ERR_INVALID_ARG, "t + n must stay below 2^32");
+    c->last_launches = 0;
+    if (n == 0) return LBM_OK;
+    if (!c->tuned && c->tune_mode == 0) {
+        st = do_tune(c);
+        if (st != LBM_OK) return st;
+    }
+    const bool graphs = c->use_graphs && c->stream != nullptr && !c->profiling;
+    int64_t done = 0;
+    while (done < n) {
+        int64_t chunk = n - done;
+        if (graphs) {
+            int64_t cap = GRAPH_CHUNK_MAX;
+            if (c->sample_every > 0 && c->sample_every <= GRAPH_CHUNK_MAX)
+                cap = (GRAPH_CHUNK_MAX / c->sample_every) * c->sample_every;
+            chunk = std::min(chunk, cap);
+            const GraphKey key{chunk, c->sample_every > 0 ? c->t % c->sample_every : 0, c->parity};
+            auto it = c->graphs.find(key);
+            if (it == c->graphs.end()) {
+                CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+                int64_t dummy = 0;
+                st = enqueue_steps(c, chunk, c->t, c->parity, &dummy);
+                cudaGraph_t graph = nullptr;
+                cudaError_t ec = cudaStreamEndCapture(c->stream, &graph);
+                if (st != LBM_OK) {
+                    if (graph) cudaGraphDestroy(graph);
+                    return st;
+                }
+                if (ec != cudaSuccess) return cuda_fail(c, ec, "end capture");
+                cudaGraphExec_t exec = nullptr;
+                ec = cudaGraphInstantiate(&exec, graph, 0);
+                cudaGraphDestroy(graph);
+                if (ec != cudaSuccess) return cuda_fail(c, ec, "instantiate graph");
+                it = c->graphs.emplace(key, exec).first;
+            }
+            CK(cudaGraphLaunch(it->second, c->stream), "launch graph");
+            c->last_launches += chunk * (int64_t)c->groups.size() + 1;
+            if (c->sample_every > 0) {
+                for (int64_t k = 0; k < chunk; ++k)
+                    if ((c->t + k + 1) % c->sample_every == 0) ++c->last_launches;
+            }
+        } else {
+            st = enqueue_steps(c, chunk, c->t, c->parity, &c->last_launches);
+            if (st != LBM_OK) return st;
+        }
+        c->t += chunk;
+        c->parity = (int)((c->parity + chunk) & 1);
+        done += chunk;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_moments(lbm_ctx *c, int32_t lattice, float *rho, float *ux, float *uy)
+{
+    lbm_status st = require_ready(c, true);
+    if (st != LBM_OK) return st;
+    if (lattice < 0 || lattice >= (int32_t)c->lats.size()) return fail(c, LBM_ERR_INVALID_ARG, "bad lattice index");
+    if (!rho || !ux || !uy) return fail(c, LBM_ERR_INVALID_ARG, "null output pointer");
+    const LatHost &L = c->lats[lattice];
+    CK(launch_moments(L.lat.storage, all_desc(c), lattice, (long long)L.lat.nx * L.lat.ny, c->parity, rho, ux,
+                      uy, c->stream),
+       "launch moments kernel");
+    return LBM_OK;
+}
+
+lbm_status lbm_observables(lbm_ctx *c, int32_t lattice, lbm_obs *out)
+{
+    lbm_status st = require_ready(c, true);
+    if (st != LBM_OK) return st;
+    if (lattice < 0 || lattice >= (int32_t)c->lats.size() || !out)
+        return fail(c, LBM_ERR_INVALID_ARG, "bad lattice index or null output");
+    for (const GroupHost &g : c->groups) CK(launch_group_observe(c, g, c->parity), "launch observe kernel");
+    CK(launch_finalize(all_desc(c), (int)c->lats.size(), c->max_chunk, t_dev(c), 0, 0, err_dev(c), c->stream),
+       "launch finaliser");
+    double rec[8];
+    CK(cudaMemcpyAsync(rec, c->scratch + c->lats[lattice].now_off, sizeof(rec), cudaMemcpyDeviceToHost, c->stream),
+       "read observables");
+    CK(cudaStreamSynchronize(c->stream), "synchronise");
+    long long tt;
+    std::memcpy(&tt, &rec[0], sizeof(tt));
+    out->t = c->t;
+    out->mass = rec[1];
+    out->phi = rec[2];
+    out->drho_y = rec[3];
+    out->drho_x = rec[4];
+    out->var_rho = rec[5];
+    out->zeta = rec[6];
+    return read_error_flag(c);
+}
+
+lbm_status lbm_observable_series(lbm_ctx *c, int32_t lattice, lbm_obs *out, int32_t cap, int32_t *n_out)
+{
+    lbm_status st = require_ready(c, true);
+    if (st != LBM_OK) return st;
+    if (lattice < 0 || lattice >= (int32_t)c->lats.size() || !n_out || cap < 0 || (cap > 0 && !out))
+        return fail(c, LBM_ERR_INVALID_ARG, "bad arguments");
+    *n_out = 0;
+    LatHost &L = c->lats[lattice];
+    unsigned count = 0;
+    CK(cudaMemcpyAsync(&count, c->scratch + L.ctr_off, sizeof(count), cudaMemcpyDeviceToHost, c->stream),
+       "read sample count");
+    CK(cudaStreamSynchronize(c->stream), "synchronise");
+    const int64_t rc = std::max(c->ring_cap, 1);
+    int64_t first = std::max<int64_t>(L.consumed, (int64_t)count - rc);
+    const int64_t avail = (int64_t)count - first;
+    const int64_t take = std::min<int64_t>(avail, cap);
+    if (take > 0) {
+        std::vector<double> ring((size_t)rc * 8);
+        CK(cudaMemcpyAsync(ring.data(), c->scratch + L.ring_off, ring.size() * sizeof(double),
+                           cudaMemcpyDeviceToHost, c->stream),
+           "read observable ring");
+        CK(cudaStreamSynchronize(c->stream), "synchronise");
+        for (int64_t q = 0; q < take; ++q) {
+            const double *r = &ring[(size_t)((first + q) % rc) * 8];
+            long long tt;
+            std::memcpy(&tt, &r[0], sizeof(tt));
+            out[q].t = tt;
+            out[q].mass = r[1];
+            out[q].phi = r[2];
+            out[q].drho_y = r[3];
+            out[q].drho_x = r[4];
+            out[q].var_rho = r[5];
+            out[q].zeta = r[6];
+        }
+    }
+    L.consumed = first + take;
+    *n_out = (int32_t)take;
+    return read_error_flag(c);
+}
+
+lbm_status lbm_get_state(lbm_ctx *c, int32_t lattice, float *dst, int32_t dst_is_host)
+{
+    lbm_status st = require_ready(c, true);
+    if (st != LBM_OK) return st;
+    if (lattice < 0 || lattice >= (int32_t)c->lats.size() || !dst)
+        return fail(c, LBM_ERR_INVALID_ARG, "bad lattice index or null output");
+    const LatHost &L = c->lats[lattice];
+    const char *src = c->state + L.state_off + (c->parity ? L.buf_bytes : 0);
+    const size_t eb = elem_bytes(L.lat.storage);
+    const long long cells = (long long)L.lat.nx * L.lat.ny;
+    if (L.lat.storage == LBM_F32) {
+        CK(cudaMemcpy2DAsync(dst, L.lat.nx * 4, src, L.pitch * 4, L.lat.nx * 4, 9 * (size_t)L.lat.ny,
+                             dst_is_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c->stream),
+           "copy populations");
+    } else if (!dst_is_host) {
+        CK(launch_export(L.lat.storage, all_desc(c), lattice, cells, c->parity, dst, c->stream), "launch export");
+    } else {
+        std::vector<uint16_t> raw((size_t)9 * cells);
+        CK(cudaMemcpy2DAsync(raw.data(), L.lat.nx * eb, src, L.pitch * eb, L.lat.nx * eb, 9 * (size_t)L.lat.ny,
+                             cudaMemcpyDeviceToHost, c->stream),
+           "copy populations");
+        CK(cudaStreamSynchronize(c->stream), "synchronise");
+        for (int i = 0; i < 9; ++i) {
+            const float shift = wq(i) * L.rho0;
+            for (long long q = 0; q < cells; ++q) {
+                const uint16_t bits = raw[(size_t)i * cells + q];
+                float v;
+                if (L.lat.storage == LBM_F16_SHIFTED) {
+                    __half h;
+                    std::memcpy(&h, &bits, 2);
+                    v = __half2float(h);
+                } else {
+                    const uint32_t w = (uint32_t)bits << 16;
+                    std::memcpy(&v, &w, 4);
+                }
+                dst[(size_t)i * cells + q] = v + shift;
+            }
+        }
+    }
+    CK(cudaStreamSynchronize(c->stream), "synchronise");
+    return LBM_OK;
+}
+
+lbm_status lbm_set_state(lbm_ctx *c, int32_t lattice, const float *src, int32_t src_is_host)
+{
+    lbm_status st = require_ready(c, false);
+    if (st != LBM_OK) return st;
+    if (lattice < 0 || lattice >= (int32_t)c->lats.size() || !src)
+        return fail(c, LBM_ERR_INVALID_ARG, "bad lattice index or null input");
+    if (!c->initialized) {  // state set directly: start the clock at 0
+        CK(cudaMemsetAsync(c->scratch, 0, c->all_desc_off, c->stream), "clear control words");
+        c->t = 0;
+        c->parity = 0;
+        c->initialized = true;
+    }
+    const LatHost &L = c->lats[lattice];
+    char *dstp = c->state + L.state_off + (c->parity ? L.buf_bytes : 0);
+    const size_t eb = elem_bytes(L.lat.storage);
+    const long long cells = (long long)L.lat.nx * L.lat.ny;
+    if (L.lat.storage == LBM_F32) {
+        CK(cudaMemcpy2DAsync(dstp, L.pitch * 4, src, L.lat.nx * 4, L.lat.nx * 4, 9 * (size_t)L.lat.ny,
+                             src_is_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, c->stream),
+           "copy populations");
+    } else if (!src_is_host) {
+        CK(launch_import(L.lat.storage, all_desc(c), lattice, cells, c->parity, src, c->stream), "launch import");
+    } else {
+        std::vector<uint16_t> raw((size_t)9 * cells);
+        for (int i = 0; i < 9; ++i) {
+            const float shift = wq(i) * L.rho0;
+            for (long long q = 0; q < cells; ++q) {
+                const float v = src[(size_t)i * cells + q] - shift;
+                uint16_t bits;
+                if (L.lat.storage == LBM_F16_SHIFTED) {
+                    const __half h = __float2half_rn(v);
+                    std::memcpy(&bits, &h, 2);
+                } else {
+                    const __nv_bfloat16 b = __float2bfloat16_rn(v);
+                    std::memcpy(&bits, &b, 2);
+                }
+                raw[(size_t)i * cells + q] = bits;
+            }
+        }
+        CK(cudaMemcpy2DAsync(dstp, L.pitch * eb, raw.data(), L.lat.nx * eb, L.lat.nx * eb, 9 * (size_t)L.lat.ny,
+                             cudaMemcpyHostToDevice, c->stream),
+           "copy populations");
+    }
+    CK(cudaStreamSynchronize(c->stream), "synchronise");
+    return LBM_OK;
+}
+
+lbm_status lbm_get_time(const lbm_ctx *c, int64_t *t)
+{
+    if (!c || !t) return LBM_ERR_INVALID_ARG;
+    *t = c->t;
+    return LBM_OK;
+}
+
+static const char kMagic[8] = {'L', 'B', 'M', 'S', 'T', 'A', 'T', '1'};
+
+lbm_status lbm_save(lbm_ctx *c, const char *path)
+{
+    lbm_status st = require_ready(c, true);
+    if (st != LBM_OK) return st;
+    if (!path) return fail(c, LBM_ERR_INVALID_ARG, "null path");
+    FILE *f = std::fopen(path, "wb");
+    if (!f) return fail(c, LBM_ERR_INVALID_ARG, std::string("cannot open ") + path);
+    bool ok = std::fwrite(kMagic, 1, 8, f) == 8;
+    const int64_t hdr[3] = {(int64_t)c->lats.size(), c->t, (int64_t)c->seed};
+    ok = ok && std::fwrite(hdr, sizeof(hdr), 1, f) == 1;
+    for (size_t k = 0; ok && k < c->lats.size(); ++k) {
+        const LatHost &L = c->lats[k];
+        const int32_t meta[5] = {L.lat.nx, L.lat.ny, L.lat.storage, L.model, L.lat.id};
+        ok = ok && std::fwrite(meta, sizeof(meta), 1, f) == 1;
+        ok = ok && std::fwrite(&L.rho0, sizeof(float), 1, f) == 1;
+        const size_t eb = elem_bytes(L.lat.storage);
+        std::vector<char> raw((size_t)9 * L.lat.ny * L.lat.nx * eb);
+        const char *src = c->state + L.state_off + (c->parity ? L.buf_bytes : 0);
+        cudaError_t e = cudaMemcpy2DAsync(raw.data(), L.lat.nx * eb, src, L.pitch * eb, L.lat.nx * eb,
+                                          9 * (size_t)L.lat.ny, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) {
+            std::fclose(f);
+            return cuda_fail(c, e, "read populations for save");
+        }
+        ok = ok && std::fwrite(raw.data(), 1, raw.size(), f) == raw.size();
+    }
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok) return fail(c, LBM_ERR_INVALID_ARG, std::string("write failed: ") + path);
+    return LBM_OK;
+}
+
+lbm_status lbm_load(lbm_ctx *c, const char *path)
+{
+    lbm_status st = require_ready(c, false);
+    if (st != LBM_OK) return st;
+    if (!path) return fail(c, LBM_ERR_INVALID_ARG, "null path");
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return fail(c, LBM_ERR_INVALID_ARG, std::string("cannot open ") + path);
+    char magic[8];
+    int64_t hdr[3];
+    bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kMagic, 8) == 0;
+    ok = ok && std::fread(hdr, sizeof(hdr), 1, f) == 1 && hdr[0] == (int64_t)c->lats.size();
+    ok = ok && hdr[1] >= 0 && hdr[1] < (int64_t(1) << 32);
+    std::vector<std::vector<char>> raws;
+    std::vector<float> rho0s;
+    for (size_t k = 0; ok && k < c->lats.size(); ++k) {
+        const LatHost &L = c->lats[k];
+        int32_t meta[5];
+        float r0 = 0.f;
+        ok = ok && std::fread(meta, sizeof(meta), 1, f) == 1 && std::fread(&r0, sizeof(float), 1, f) == 1;
+        ok = ok && meta[0] == L.lat.nx && meta[1] == L.lat.ny && meta[2] == L.lat.storage && meta[3] == L.model &&
+             meta[4] == L.lat.id;
+        if (!ok) break;
+        const size_t eb = elem_bytes(L.lat.storage);
+        std::vector<char> raw((size_t)9 * L.lat.ny * L.lat.nx * eb);
+        ok = std::fread(raw.data(), 1, raw.size(), f) == raw.size();
+        raws.push_back(std::move(raw));
+        rho0s.push_back(r0);
+    }
+    std::fclose(f);
+    if (!ok) return fail(c, LBM_ERR_INVALID_ARG, "state file does not match this context");
+    for (size_t k = 0; k < c->lats.size(); ++k) c->lats[k].rho0 = rho0s[k];
+    st = upload_descs(c);
+    if (st != LBM_OK) return st;
+    for (size_t k = 0; k < c->lats.size(); ++k) {
+        const LatHost &L = c->lats[k];
+        const size_t eb = elem_bytes(L.lat.storage);
+        CK(cudaMemcpy2DAsync(c->state + L.state_off, L.pitch * eb, raws[k].data(), L.lat.nx * eb, L.lat.nx * eb,
+                             9 * (size_t)L.lat.ny, cudaMemcpyHostToDevice, c->stream),
+           "upload populations");
+        c->lats[k].consumed = 0;
+    }
+    CK(cudaMemsetAsync(c->scratch, 0, c->all_desc_off, c->stream), "clear control words");
+    CK(launch_set_time(t_dev(c), (uint32_t)hdr[1], c->stream), "set time");
+    CK(cudaStreamSynchronize(c->stream), "synchronise");
+    c->t = hdr[1];
+    c->seed = (uint64_t)hdr[2];
+    c->parity = 0;
+    c->initialized = true;
+    drop_graphs(c);
+    return LBM_OK;
+}
+
+lbm_status lbm_set_tuning(lbm_ctx *c, int32_t mode, int32_t vec, int32_t rows)
+{
+    if (!c) return LBM_ERR_INVALID_ARG;
+    if (mode == 0) {
+        c->tune_mode = 0;
+        c->tuned = false;
+        return LBM_OK;
+    }
+    if (mode != 1) return fail(c, LBM_ERR_INVALID_ARG, "mode must be 0 or 1");
+    if (rows < ROWS_MIN || rows > 4096) return fail(c, LBM_ERR_INVALID_ARG, "rows must be in [16, 4096]");
+    for (auto &g : c->groups) {
+        if (!allowed_vec(g.storage, vec)) return fail(c, LBM_ERR_INVALID_ARG, "vec not available for this storage");
+        for (int m : g.members)
+            if (c->lats[m].lat.nx % vec) return fail(c, LBM_ERR_INVALID_ARG, "vec must divide nx");
+    }
+    for (auto &g : c->groups) {
+        g.vec = vec;
+        g.rows = rows;
+        g.warps = 4;
+    }
+    c->tune_mode = 1;
+    c->tuned = true;
+    drop_graphs(c);
+    if (c->bound) return upload_descs(c);
+    return LBM_OK;
+}
+
+lbm_status lbm_tune(lbm_ctx *c)
+{
+    lbm_status st = require_ready(c, true);
+    if (st != LBM_OK) return st;
+    return do_tune(c);
+}
+
+lbm_status lbm_get_tuning(const lbm_ctx *c, int32_t lattice, int32_t *vec, int32_t *rows, int32_t *warps)
+{
+    if (!c || !vec || !rows || !warps || lattice < 0 || lattice >= (int32_t)c->lats.size())
+        return LBM_ERR_INVALID_ARG;
+    const GroupHost &g = c->groups[c->lats[lattice].group];
+    *vec = g.vec;
+    *rows = g.rows;
+    *warps = g.warps;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_graphs(lbm_ctx *c, int32_t enabled)
+{
+    if (!c) return LBM_ERR_INVALID_ARG;
+    c->use_graphs = enabled != 0;
+    if (!c->use_graphs) drop_graphs(c);
+    return LBM_OK;
+}
+
+lbm_status lbm_last_launch_count(const lbm_ctx *c, int64_t *count)
+{
+    if (!c || !count) return LBM_ERR_INVALID_ARG;
+    *count = c->last_launches;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_profiling(lbm_ctx *c, int32_t enabled)
+{
+    if (!c) return LBM_ERR_INVALID_ARG;
+    c->profiling = enabled != 0;
+    c->ev_marks.clear();
+    c->ev_used = 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_profile_read(lbm_ctx *c, double *step_ms, int64_t *step_launches, double *other_ms)
+{
+    if (!c || !step_ms || !step_launches || !other_ms) return LBM_ERR_INVALID_ARG;
+    *step_ms = 0.0;
+    *other_ms = 0.0;
+    *step_launches = 0;
+    if (!c->ev_marks.empty()) {
+        CK(cudaEventSynchronize(c->ev_pool[c->ev_marks.back().first + 1]), "synchronise event");
+        for (const auto &m : c->ev_marks) {
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, c->ev_pool[m.first], c->ev_pool[m.first + 1]), "event time");
+            if (m.second) {
+                *step_ms += ms;
+                ++*step_launches;
+            } else {
+                *other_ms += ms;
+            }
+        }
+    }
+    c->ev_marks.clear();
+    c->ev_used = 0;
+    return LBM_OK;
+}
+
+const char *lbm_last_error(const lbm_ctx *c)
+{
+    if (!c) return "null context";
+    return c->err.c_str();
+}
+
+void lbm_destroy(lbm_ctx *c)
+{
+    if (!c) return;
+    drop_graphs(c);
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    delete c;
+}
+
+}  // extern "C"

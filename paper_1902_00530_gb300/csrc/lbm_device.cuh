@@ -1,0 +1,211 @@
+// lbm_device.cuh -- device-side pieces of the fused active-LBM step for sm_103a.
+//
+// The step (App. A.2 of arXiv:1902.00530) per site: pull-stream the nine
+// populations, form rho and u, the steady-state velocity u* of the model,
+// f^SS = xi(rho, u*) (Eq. (fssD2Q7) in D2Q9 form), BGK relaxation, zero-sum
+// uniform noise (Eq. (noiseDensityConservation)) and the negative correction
+// (App. A.3), all in registers, in one pass over HBM.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbm {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// D2Q9 velocity set: 0 rest, 1 +x, 2 +y, 3 -x, 4 -y, 5 (+x,+y), 6 (-x,+y),
+// 7 (-x,-y), 8 (+x,-y).
+__host__ __device__ constexpr int vx(int i)
+{
+    return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+}
+__host__ __device__ constexpr int vy(int i)
+{
+    return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+}
+__host__ __device__ constexpr int reverse_of(int i)
+{
+    return i == 0 ? 0 : (i <= 4 ? ((i + 1) % 4) + 1 : ((i - 5 + 2) % 4) + 5);
+}
+__host__ __device__ constexpr float wq(int i)
+{
+    return i == 0 ? 4.0f / 9.0f : (i <= 4 ? 1.0f / 9.0f : 1.0f / 36.0f);
+}
+__host__ __device__ constexpr double wq_d(int i)
+{
+    return i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+}
+static_assert(reverse_of(1) == 3 && reverse_of(2) == 4 && reverse_of(3) == 1 &&
+                  reverse_of(4) == 2 && reverse_of(5) == 7 && reverse_of(6) == 8 &&
+                  reverse_of(7) == 5 && reverse_of(8) == 6,
+              "D2Q9 reverse directions");
+
+enum { MODEL_PASSIVE = 0, MODEL_MIPS = 1, MODEL_CIL = 2 };
+enum { ST_F32 = 0, ST_F16 = 1, ST_BF16 = 2 };
+enum { DEVERR_NUMERIC = 1u, DEVERR_TIMEOUT = 2u };
+
+// Per-lattice descriptor, resident in device memory for the whole run.
+struct LatDesc {
+    void *f[2];          // the two population buffers, [9][ny][pitch] of the storage type
+    double *scal;        // [nstrips][5] per-strip sums: rho, jx, jy, rho^2, |j|
+    double *colp;        // [nsy][nx] per-strip-row column sums of rho
+    double *rowp;        // [nsx][ny] per-strip-column row sums of rho
+    double *finp;        // [nchunk][9] finaliser chunk partials
+    double *ring;        // [ring_cap][8] observable records
+    double *now;         // [8] on-demand observable record
+    unsigned *counters;  // [2]: samples written, finaliser arrivals
+    int nx, ny, pitch, id;
+    int nsx, nsy, rows, block_begin;
+    int ring_cap, nchunk, pad0, pad1;
+    float omega;         // 1/tau
+    float sigma_q;       // sigma * 2^-24 (noise scale of one 24-bit step)
+    float C, inv_rho_star, rho_star, u_max, u_max2, A, B;
+    float rho0;          // storage shift
+};
+
+struct StepArgs {
+    const LatDesc *desc;  // lattices of this launch group
+    int nlat;
+    int src;              // index of the buffer holding the current state
+    const uint32_t *t_ptr;
+    uint32_t k;           // step offset of this launch from *t_ptr
+    uint32_t key0, key1;  // Philox key = seed
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32
+// -> 64-bit products of counter words 0 and 2, whose high halves are XORed
+// with the other counter words and the round key; the key advances by the
+// Weyl increments between rounds.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// Noise counter: (x, y, t, id | purpose << 24 | call << 28); purpose 0 =
+// collision noise.  The nine variates are k_i = 2 m_i + 1 - 2^24 with m_i the
+// top 24 bits of words 0..7 of two calls and, for i = 8, the low bytes of
+// words 0, 1, 2.  eta~_i = sigma 2^-24 k_i is uniform on [-sigma, sigma].
+__device__ __forceinline__ void noise_ints(uint32_t x, uint32_t y, uint32_t t, uint32_t id,
+                                           uint32_t key0, uint32_t key1, int k[9])
+{
+    const uint4 a = philox4x32_10(make_uint4(x, y, t, id & 0xFFFFFFu), key0, key1);
+    const uint4 b = philox4x32_10(make_uint4(x, y, t, (id & 0xFFFFFFu) | (1u << 28)), key0, key1);
+    const uint32_t w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+    for (int i = 0; i < 8; ++i) k[i] = (int)((w[i] >> 8) << 1) + 1 - (1 << 24);
+    const uint32_t m8 = (a.x & 0xFFu) | ((a.y & 0xFFu) << 8) | ((a.z & 0xFFu) << 16);
+    k[8] = (int)(m8 << 1) + 1 - (1 << 24);
+}
+
+// ---------------------------------------------------------------------------
+// Storage: FP32, or 16-bit values of s = f - w_i rho0 (FP16 / BF16, RN).
+// ---------------------------------------------------------------------------
+template <int ST> struct Store;
+template <> struct Store<ST_F32> {
+    using T = float;
+    __device__ static __forceinline__ float get(T v, float) { return v; }
+    __device__ static __forceinline__ T put(float f, float) { return f; }
+};
+template <> struct Store<ST_F16> {
+    using T = __half;
+    __device__ static __forceinline__ float get(T v, float shift) { return __half2float(v) + shift; }
+    __device__ static __forceinline__ T put(float f, float shift) { return __float2half_rn(f - shift); }
+};
+template <> struct Store<ST_BF16> {
+    using T = __nv_bfloat16;
+    __device__ static __forceinline__ float get(T v, float shift)
+    {
+        return __bfloat162float(v) + shift;
+    }
+    __device__ static __forceinline__ T put(float f, float shift)
+    {
+        return __float2bfloat16_rn(f - shift);
+    }
+};
+
+template <int BYTES> struct VecWord;
+template <> struct VecWord<2> { using T = unsigned short; };
+template <> struct VecWord<4> { using T = unsigned int; };
+template <> struct VecWord<8> { using T = uint2; };
+template <> struct VecWord<16> { using T = uint4; };
+template <> struct VecWord<32> { using T = uint4; };  // two 16-byte words
+
+// Load VEC consecutive values (aligned to VEC elements) and expand to FP32.
+template <int ST, int VEC>
+__device__ __forceinline__ void load_vec(const typename Store<ST>::T *p, float shift, float out[VEC])
+{
+    using T = typename Store<ST>::T;
+    constexpr int BYTES = (int)sizeof(T) * VEC;
+    if constexpr (BYTES <= 16) {
+        using W = typename VecWord<BYTES>::T;
+        W w = __ldg(reinterpret_cast<const W *>(p));
+        const T *e = reinterpret_cast<const T *>(&w);
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) out[j] = Store<ST>::get(e[j], shift);
+    } else {
+        const uint4 *q = reinterpret_cast<const uint4 *>(p);
+#pragma unroll
+        for (int h = 0; h < BYTES / 16; ++h) {
+            uint4 w = __ldg(q + h);
+            const T *e = reinterpret_cast<const T *>(&w);
+#pragma unroll
+            for (int j = 0; j < 16 / (int)sizeof(T); ++j)
+                out[h * (16 / (int)sizeof(T)) + j] = Store<ST>::get(e[j], shift);
+        }
+    }
+}
+
+template <int ST, int VEC>
+__device__ __forceinline__ void store_vec(typename Store<ST>::T *p, float shift, const float in[VEC])
+{
+    using T = typename Store<ST>::T;
+    constexpr int BYTES = (int)sizeof(T) * VEC;
+    if constexpr (BYTES <= 16) {
+        using W = typename VecWord<BYTES>::T;
+        W w;
+        T *e = reinterpret_cast<T *>(&w);
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) e[j] = Store<ST>::put(in[j], shift);
+        *reinterpret_cast<W *>(p) = w;
+    } else {
+        uint4 *q = reinterpret_cast<uint4 *>(p);
+#pragma unroll
+        for (int h = 0; h < BYTES / 16; ++h) {
+            uint4 w;
+            T *e = reinterpret_cast<T *>(&w);
+#pragma unroll
+            for (int j = 0; j < 16 / (int)sizeof(T); ++j)
+                e[j] = Store<ST>::put(in[h * (16 / (int)sizeof(T)) + j], shift);
+            q[h] = w;
+        }
+    }
+}
+
+template <int ST>
+__device__ __forceinline__ float load_one(const typename Store<ST>::T *p, float shift)
+{
+    return Store<ST>::get(p[0], shift);
+}
+
+__device__ __forceinline__ int wrap_once(int a, int n)
+{
+    a = a < 0 ? a + n : a;
+    return a >= n ? a - n : a;
+}
+
+}  // namespace lbm

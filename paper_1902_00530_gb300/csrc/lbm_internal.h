@@ -1,0 +1,36 @@
+// lbm_internal.h -- declarations shared by the library's translation units.
+#pragma once
+
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+// fused step / observe kernels (lbm_step_*.cu, one unit per storage type)
+cudaError_t launch_step_f32(int model, int vec, bool sample, const StepArgs &a, int blocks, int warps,
+                            cudaStream_t stream);
+cudaError_t launch_step_f16(int model, int vec, bool sample, const StepArgs &a, int blocks, int warps,
+                            cudaStream_t stream);
+cudaError_t launch_step_bf16(int model, int vec, bool sample, const StepArgs &a, int blocks, int warps,
+                             cudaStream_t stream);
+cudaError_t launch_observe_f32(int vec, const StepArgs &a, int blocks, int warps, cudaStream_t stream);
+cudaError_t launch_observe_f16(int vec, const StepArgs &a, int blocks, int warps, cudaStream_t stream);
+cudaError_t launch_observe_bf16(int vec, const StepArgs &a, int blocks, int warps, cudaStream_t stream);
+
+// auxiliary kernels (lbm_aux.cu)
+size_t init_spec_bytes();
+void pack_init_spec(void *dst, double rho_mean, double rho_amp, int u_kind, double u_amp, double ux0,
+                    double uy0, double A, double B);
+cudaError_t launch_init(int storage, const LatDesc *desc, const void *specs, int nlat, long long max_cells,
+                        int dst, uint64_t seed, cudaStream_t s);
+cudaError_t launch_moments(int storage, const LatDesc *desc, int lat, long long cells, int src, float *rho,
+                           float *ux, float *uy, cudaStream_t s);
+cudaError_t launch_export(int storage, const LatDesc *desc, int lat, long long cells, int src, float *out,
+                          cudaStream_t s);
+cudaError_t launch_import(int storage, const LatDesc *desc, int lat, long long cells, int dst,
+                          const float *in, cudaStream_t s);
+cudaError_t launch_finalize(const LatDesc *desc, int nlat, int max_chunk, const uint32_t *t_ptr, uint32_t k,
+                            int to_ring, unsigned *err, cudaStream_t s);
+cudaError_t launch_advance_time(uint32_t *t_ptr, uint32_t n, cudaStream_t s);
+cudaError_t launch_set_time(uint32_t *t_ptr, uint32_t t, cudaStream_t s);
+
+}  // namespace lbm

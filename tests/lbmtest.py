@@ -1,0 +1,50 @@
+"""Shared helpers for the GPU tests: run the CUDA path and the oracle on the
+same seeded inputs and measure their difference."""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle as O
+import workloads as W
+
+
+def split_preset(name: str, **overrides):
+    d = W.preset(name, **overrides)
+    model = d.pop("model")
+    return model, d
+
+
+def gpu_sim(model, d, nx, ny, seed, spec, storage="f32", lattice_id=0, tuning=None,
+            sample_every=0, ring=0, graphs=True):
+    from paper_1902_00530_gb300 import Lattice, Simulation
+    sim = Simulation([Lattice(nx, ny, storage, lattice_id)], [model], [d], sample_every=sample_every,
+                     ring_capacity=ring)
+    if tuning is not None:
+        sim.set_tuning(1, *tuning)
+    sim.set_graphs(graphs)
+    sim.init(seed, [spec])
+    return sim
+
+
+def gpu_run(model, d, nx, ny, steps, seed, spec, **kw):
+    sim = gpu_sim(model, d, nx, ny, seed, spec, **kw)
+    sim.step(steps)
+    f = sim.get_state(host=True).numpy().astype(np.float64)
+    sim.close()
+    return f
+
+
+def oracle_run(model, d, nx, ny, steps, seed, spec, bits=64, lattice_id=0):
+    p = O.params(**d)
+    f = O.init(nx, ny, seed, lattice_id=lattice_id, **spec, prm=p, bits=bits)
+    return O.run(f, model, p, seed, 0, steps, lattice_id=lattice_id, bits=bits)
+
+
+def errors(f, ref):
+    """e_rho = max|rho - rho_ref| / mean rho_ref; e_u = max|u - u_ref| / max(max|u_ref|, 1e-3)."""
+    r, ux, uy = O.moments(np.ascontiguousarray(f, dtype=np.float64))
+    rr, uxr, uyr = O.moments(np.ascontiguousarray(ref, dtype=np.float64))
+    e_rho = np.abs(r - rr).max() / rr.mean()
+    du = max(np.abs(ux - uxr).max(), np.abs(uy - uyr).max())
+    e_u = du / max(np.hypot(uxr, uyr).max(), 1e-3)
+    return float(e_rho), float(e_u)

@@ -1,0 +1,119 @@
+"""C-ABI checks that need no GPU: the library builds, loads, exports every
+symbol include/lbm.h declares, and validates arguments on the host."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1902_00530_gb300 import _abi
+    from paper_1902_00530_gb300.build import build
+    build()
+    return _abi.load()
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbm_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_the_calls():
+    names = declared_symbols()
+    for required in ("lbm_create", "lbm_init", "lbm_step", "lbm_moments", "lbm_observables",
+                     "lbm_create_batch", "lbm_bind", "lbm_buffer_bytes", "lbm_destroy"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_1902_00530_gb300 import _abi
+    for name in declared_symbols():
+        assert hasattr(lib, name), name
+        assert name in _abi.SIGNATURES, f"binding lacks {name}"
+
+
+def _lat(nx=8, ny=8, storage=0, id_=0):
+    from paper_1902_00530_gb300 import _abi
+    return _abi.lbm_lattice(nx, ny, storage, id_)
+
+
+def _prm(**kw):
+    from paper_1902_00530_gb300 import _params
+    return _params(kw)
+
+
+@pytest.mark.parametrize("bad", [
+    dict(lat=dict(nx=0)), dict(lat=dict(ny=70000)), dict(lat=dict(storage=3)), dict(lat=dict(id_=1 << 24)),
+    dict(prm=dict(tau=0.5)), dict(prm=dict(sigma=-1.0)), dict(prm=dict(tau=float("nan"))),
+    dict(model=7), dict(model=1, prm=dict(rho_star=0.0)), dict(prm=dict(rho0=-1.0)),
+    dict(prm=dict(A=float("inf")), model=2),
+])
+def test_create_rejects_bad_arguments(lib, bad):
+    ctx = ctypes.c_void_p(123)
+    lat = _lat(**bad.get("lat", {}))
+    prm = _prm(**{"tau": 1.0, **bad.get("prm", {})})
+    st = lib.lbm_create(ctypes.byref(lat), bad.get("model", 0), ctypes.byref(prm), ctypes.byref(ctx))
+    assert st == 1 and not ctx.value
+
+
+def test_host_only_calls_and_status_codes(lib):
+    ctx = ctypes.c_void_p()
+    lat = _lat(37, 5)
+    prm = _prm(tau=1.0, sigma=0.01)
+    assert lib.lbm_create(ctypes.byref(lat), 0, ctypes.byref(prm), ctypes.byref(ctx)) == 0
+    sb, cb = ctypes.c_size_t(), ctypes.c_size_t()
+    assert lib.lbm_buffer_bytes(ctx, ctypes.byref(sb), ctypes.byref(cb)) == 0
+    # two FP32 buffers of 9 planes, rows padded to 128 bytes
+    assert sb.value >= 2 * 9 * 5 * 64 * 4 and cb.value > 0
+    assert lib.lbm_set_sampling(ctx, 10, 0) == 1          # sampling needs a ring
+    assert lib.lbm_set_sampling(ctx, 10, 8) == 0
+    sb2 = ctypes.c_size_t()
+    assert lib.lbm_buffer_bytes(ctx, ctypes.byref(sb2), ctypes.byref(cb)) == 0
+    assert lib.lbm_step(ctx, 1) == 2                      # not bound
+    assert b"bound" in lib.lbm_last_error(ctx)
+    assert lib.lbm_observables(ctx, 0, None) == 2
+    assert lib.lbm_set_tuning(ctx, 1, 4, 32) == 1         # 4 does not divide 37
+    assert lib.lbm_set_tuning(ctx, 1, 1, 8) == 1          # rows below 16
+    assert lib.lbm_set_tuning(ctx, 1, 1, 32) == 0
+    v, r, w = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    assert lib.lbm_get_tuning(ctx, 0, ctypes.byref(v), ctypes.byref(r), ctypes.byref(w)) == 0
+    assert (v.value, r.value) == (1, 32)
+    assert lib.lbm_get_tuning(ctx, 1, ctypes.byref(v), ctypes.byref(r), ctypes.byref(w)) == 1
+    t = ctypes.c_int64(-1)
+    assert lib.lbm_get_time(ctx, ctypes.byref(t)) == 0 and t.value == 0
+    assert lib.lbm_bind(ctx, None, None, None) == 1
+    assert lib.lbm_bind(ctx, ctypes.c_void_p(0x1001), ctypes.c_void_p(0x2000), None) == 1  # misaligned
+    lib.lbm_destroy(ctx)
+    lib.lbm_destroy(None)
+
+
+def test_batch_create_groups(lib):
+    from paper_1902_00530_gb300 import _abi
+    n = 4
+    lats = (_abi.lbm_lattice * n)(*[_abi.lbm_lattice(64, 32, s, k) for k, s in enumerate([0, 1, 0, 2])])
+    mods = (ctypes.c_int * n)(1, 2, 1, 2)
+    prms = (_abi.lbm_params * n)(*[_prm(tau=1.0, rho_star=2.0) for _ in range(n)])
+    ctx = ctypes.c_void_p()
+    assert lib.lbm_create_batch(n, lats, mods, prms, ctypes.byref(ctx)) == 0
+    sb, cb = ctypes.c_size_t(), ctypes.c_size_t()
+    assert lib.lbm_buffer_bytes(ctx, ctypes.byref(sb), ctypes.byref(cb)) == 0
+    # 2 f32 + 2 16-bit lattices, two buffers each
+    assert sb.value >= 2 * 9 * 32 * (2 * 64 * 4 + 2 * 64 * 2)
+    lib.lbm_destroy(ctx)
+    assert lib.lbm_create_batch(0, lats, mods, prms, ctypes.byref(ctx)) == 1
+
+
+def test_python_binding_refuses_without_library(tmp_path):
+    from paper_1902_00530_gb300 import _abi
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        _abi._lib_saved = _abi._lib
+        try:
+            _abi._lib = None
+            _abi.load(str(tmp_path / "missing.so"))
+        finally:
+            _abi._lib = _abi._lib_saved

@@ -1,0 +1,362 @@
+"""GPU path vs the FP64 oracle, element by element on the same seeded inputs.
+
+Tolerances (relative errors e_rho, e_u as defined in lbmtest.errors):
+  FP32 storage, linearly stable regimes, 1000 steps   <= 1e-5
+  FP16/BF16 shifted storage, stable regimes            <= 2e-3
+  linearly unstable MIPS (rounding differences grow like exp(s_max t)):
+      <= 1e-5 up to t* = ln(1e-5/1e-7)/s_max, and afterwards within 4x the
+      oracle's own FP32-vs-FP64 divergence.
+"""
+import math
+import struct
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from lbmtest import errors, gpu_run, gpu_sim, oracle_run, split_preset
+
+pytestmark = pytest.mark.gpu
+
+SEED = W.seed(1)
+U0_CIL = W.PRESETS["CIL_RHO1"]["B"] - W.PRESETS["CIL_RHO1"]["A"]  # U0 at rho = 1
+
+
+# ------------------------------------------------------------------ init ----
+@pytest.mark.parametrize("storage", ["f32", "f16s", "bf16s"])
+@pytest.mark.parametrize("u_kind", [0, 1, 2])
+def test_init_matches_oracle(storage, u_kind):
+    """App. C.2 initial state: FP64 f^SS rounded once to the storage type."""
+    model, d = split_preset("CIL_RHO1")
+    spec = dict(rho_mean=1.0, rho_amp=0.1, u_kind=u_kind, u_amp=0.02, ux0=0.01, uy0=-0.005)
+    nx, ny = 72, 40
+    sim = gpu_sim(model, d, nx, ny, SEED, spec, storage=storage, lattice_id=17)
+    got = sim.get_state(host=True).numpy().astype(np.float64)
+    sim.close()
+    ref = O.init(nx, ny, SEED, lattice_id=17, **spec, prm=O.params(**d))
+    w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)[:, None, None]
+    if storage == "f32":
+        tol = 2.0 ** -24 * np.abs(ref) * 1.01 + 1e-30
+    else:
+        shift = w * 1.0
+        rel = 2.0 ** -11 if storage == "f16s" else 2.0 ** -8
+        tol = rel * np.abs(ref - shift) * 1.01 + 1e-7
+    assert np.all(np.abs(got - ref) <= tol)
+
+
+# ------------------------------------------------------ stable-regime parity
+STABLE = {
+    # name: (preset, overrides, init spec)
+    "passive_noise": ("PASSIVE", dict(sigma=0.01), W.INIT_CONFIG1),
+    "mips_paper_literal": ("MIPS_PAPER_LITERAL", {}, W.INIT_CONFIG1),
+    "mips_rho1_stable_C": ("MIPS_RHO1", dict(C=0.2), W.INIT_CONFIG1),
+    "cil_rho1_ordered": ("CIL_RHO1", {}, W.init_ordered(U0_CIL)),
+    "cil_paper_literal": ("CIL_PAPER_LITERAL", {}, W.INIT_CONFIG2),
+    "passive_tau_1p7": ("PASSIVE", dict(tau=1.7, sigma=0.005), W.INIT_CONFIG2),
+}
+
+
+@pytest.mark.parametrize("case", sorted(STABLE))
+def test_step_parity_fp32_1000_steps(case):
+    name, over, spec = STABLE[case]
+    model, d = split_preset(name, **over)
+    got = gpu_run(model, d, 64, 64, 1000, SEED, spec)
+    ref = oracle_run(model, d, 64, 64, 1000, SEED, spec)
+    e_rho, e_u = errors(got, ref)
+    assert e_rho <= 1e-5 and e_u <= 1e-5, (e_rho, e_u)
+
+
+@pytest.mark.parametrize("storage", ["f16s", "bf16s"])
+@pytest.mark.parametrize("case", ["mips_paper_literal", "cil_rho1_ordered", "passive_noise"])
+def test_step_parity_16bit_1000_steps(storage, case):
+    name, over, spec = STABLE[case]
+    model, d = split_preset(name, **over)
+    got = gpu_run(model, d, 64, 64, 1000, SEED, spec, storage=storage)
+    ref = oracle_run(model, d, 64, 64, 1000, SEED, spec)
+    e_rho, e_u = errors(got, ref)
+    assert e_rho <= 2e-3 and e_u <= 2e-3, (e_rho, e_u)
+
+
+# ------------------------------------------------------ unstable-regime rule
+def test_unstable_mips_parity_rule():
+    """Config 1 with the rescaled MIPS preset: grid-scale modes grow at about
+    0.13 per step, so GPU-vs-FP64 agreement holds to 1e-5 only for the first
+    ~30 steps; at 1000 steps the GPU error is compared with the oracle's own
+    FP32-vs-FP64 divergence."""
+    model, d = split_preset("MIPS_RHO1")
+    spec = W.INIT_CONFIG1
+    for steps in (1, 10, 30):
+        e = errors(gpu_run(model, d, 64, 64, steps, SEED, spec), oracle_run(model, d, 64, 64, steps, SEED, spec))
+        assert max(e) <= 1e-5, (steps, e)
+    steps = 1000
+    ref = oracle_run(model, d, 64, 64, steps, SEED, spec)
+    f32 = oracle_run(model, d, 64, 64, steps, SEED, spec, bits=32).astype(np.float64)
+    got = gpu_run(model, d, 64, 64, steps, SEED, spec)
+    e_gpu, e_int = errors(got, ref), errors(f32, ref)
+    assert e_gpu[0] <= 4 * e_int[0] + 1e-5 and e_gpu[1] <= 4 * e_int[1] + 1e-5, (e_gpu, e_int)
+    # the conserved mass stays exact and the statistics of the separated state agree
+    m = [O.observables(np.ascontiguousarray(a))["mass"] for a in (got, ref)]
+    assert abs(m[0] - m[1]) / m[1] < 1e-6
+    v = [O.observables(np.ascontiguousarray(a))["var_rho"] for a in (got, ref, f32)]
+    assert abs(v[0] - v[1]) <= 4 * abs(v[2] - v[1]) + 0.05 * v[1]
+
+
+# ------------------------------------------------- ragged sizes and shapes --
+SHAPES = [(1, 1), (1, 7), (7, 1), (3, 3), (5, 17), (33, 9), (64, 20), (100, 37), (130, 3), (257, 18)]
+
+
+@pytest.mark.parametrize("nx,ny", SHAPES)
+def test_ragged_sizes_default_shape(nx, ny):
+    for name, steps, spec in (("CIL_RHO1", 40, W.init_ordered(U0_CIL)), ("MIPS_RHO1", 12, W.INIT_CONFIG1),
+                              ("PASSIVE", 40, W.INIT_CONFIG2)):
+        over = dict(sigma=0.01) if name == "PASSIVE" else {}
+        model, d = split_preset(name, **over)
+        got = gpu_run(model, d, nx, ny, steps, SEED, spec)
+        ref = oracle_run(model, d, nx, ny, steps, SEED, spec)
+        e = errors(got, ref)
+        assert max(e) <= 1e-5, (name, nx, ny, e)
+
+
+@pytest.mark.parametrize("vec,rows", [(1, 16), (2, 16), (4, 16), (4, 48), (2, 128)])
+@pytest.mark.parametrize("storage", ["f32", "bf16s"])
+def test_launch_shapes_give_identical_states(vec, rows, storage):
+    """Every launch shape performs the same per-site arithmetic: the states
+    agree bitwise with the default shape, and with the oracle."""
+    model, d = split_preset("MIPS_RHO1")
+    nx, ny = 264, 70
+    base = gpu_run(model, d, nx, ny, 9, SEED, W.INIT_CONFIG1, storage=storage, tuning=(1, 16))
+    got = gpu_run(model, d, nx, ny, 9, SEED, W.INIT_CONFIG1, storage=storage, tuning=(vec, rows))
+    np.testing.assert_array_equal(got, base)
+    if storage == "f32":
+        assert max(errors(got, oracle_run(model, d, nx, ny, 9, SEED, W.INIT_CONFIG1))) <= 1e-5
+
+
+# ---------------------------------------------------------- noise stream ---
+def _write_state_file(path, f, t, seed, lattice_id, model, storage=0, rho0=1.0):
+    nine, ny, nx = f.shape
+    with open(path, "wb") as fh:
+        fh.write(b"LBMSTAT1")
+        fh.write(struct.pack("<3q", 1, t, seed))
+        fh.write(struct.pack("<5i", nx, ny, storage, model, lattice_id))
+        fh.write(struct.pack("<f", rho0))
+        fh.write(np.ascontiguousarray(f, dtype=np.float32).tobytes())
+
+
+@pytest.mark.parametrize("t,lattice_id,seed", [(0, 0, SEED), (7, 3, 12345), (2 ** 31 + 12345, 2 ** 24 - 1,
+                                                                                  2 ** 63 + 99)])
+def test_noise_stream_matches_oracle(tmp_path, t, lattice_id, seed):
+    """Both sides implement Philox4x32-10 and the 24-bit variate recipe from
+    the published definition.  From a uniform rest state (a BGK fixed point)
+    one step adds exactly the zero-sum noise, which must equal the oracle's
+    sigma (s_i - mean s) to FP32 rounding of f (1e-5 here; a wrong bit in the
+    top ~15 bits of any variate would exceed it)."""
+    from paper_1902_00530_gb300 import Lattice, Simulation
+    nx, ny, rho, sigma = 40, 24, 40.0, 0.5
+    w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+    f0 = np.broadcast_to((w * rho)[:, None, None], (9, ny, nx)).astype(np.float32)
+    path = tmp_path / "rest.lbm"
+    _write_state_file(path, f0, t, seed, lattice_id, 0)
+    sim = Simulation([Lattice(nx, ny, "f32", lattice_id)], ["passive"], [dict(tau=1.3, sigma=sigma)])
+    sim.load(str(path))
+    assert sim.time == t
+    sim.step(1)
+    got = sim.get_state(host=True).numpy().astype(np.float64) - (w * rho)[:, None, None]
+    sim.close()
+    for (x, y) in [(0, 0), (1, 0), (nx - 1, ny - 1), (17, 5), (3, 20)]:
+        s = O.noise_variates(seed, x, y, t, lattice_id)
+        eta = sigma * (s - s.mean())
+        np.testing.assert_allclose(got[:, y, x], eta, rtol=0, atol=1e-5)
+
+
+# ------------------------------------------------------------ observables --
+def test_sampled_observables_match_oracle():
+    """Eq. (phi) and App. D reductions of the stored state every 10 steps."""
+    model, d = split_preset("CIL_RHO1")
+    nx, ny, every, steps = 96, 40, 10, 60
+    spec = W.init_ordered(U0_CIL, rho_amp=0.05, u_amp=0.02)
+    sim = gpu_sim(model, d, nx, ny, SEED, spec, sample_every=every, ring=16)
+    sim.step(steps)
+    series = sim.observable_series()
+    now = sim.observables()
+    sim.close()
+    assert [r["t"] for r in series] == list(range(every, steps + 1, every))
+    p = O.params(**d)
+    f = O.init(nx, ny, SEED, **spec, prm=p)
+    for k, rec in enumerate(series):
+        f = O.run(f, model, p, SEED, k * every, every)
+        ref = O.observables(f, B=d["B"])
+        assert abs(rec["mass"] - ref["mass"]) / ref["mass"] < 1e-6
+        for key in ("phi", "drho_y", "drho_x", "zeta"):
+            assert abs(rec[key] - ref[key]) < 2e-6, (key, rec[key], ref[key])
+        assert abs(rec["var_rho"] - ref["var_rho"]) < 1e-7
+    assert now["t"] == steps
+    for key in ("mass", "phi", "drho_y", "drho_x", "var_rho", "zeta"):
+        assert now[key] == pytest.approx(series[-1][key], rel=1e-12, abs=1e-15)
+
+
+def test_observables_16bit_storage():
+    model, d = split_preset("MIPS_PAPER_LITERAL")
+    nx, ny = 128, 64
+    for storage in ("f16s", "bf16s"):
+        sim = gpu_sim(model, d, nx, ny, SEED, W.INIT_CONFIG2, storage=storage)
+        sim.step(50)
+        ob = sim.observables()
+        f = sim.get_state(host=True).numpy().astype(np.float64)
+        sim.close()
+        ref = O.observables(oracle_run(model, d, nx, ny, 50, SEED, W.INIT_CONFIG2))
+        assert abs(ob["mass"] - ref["mass"]) / ref["mass"] < 2e-3
+        assert abs(ob["drho_y"] - ref["drho_y"]) < 2e-3 and abs(ob["var_rho"] - ref["var_rho"]) < 2e-3
+        # the reduction reads exactly the stored values
+        own = O.observables(np.ascontiguousarray(f))
+        assert abs(ob["mass"] - own["mass"]) / own["mass"] < 1e-7
+
+
+def test_moments_match_oracle():
+    import torch
+    model, d = split_preset("CIL_RHO1")
+    nx, ny = 80, 48
+    sim = gpu_sim(model, d, nx, ny, SEED, W.INIT_CONFIG2)
+    sim.step(25)
+    rho, ux, uy = (a.cpu().numpy().astype(np.float64) for a in sim.moments())
+    sim.close()
+    rr, uxr, uyr = O.moments(oracle_run(model, d, nx, ny, 25, SEED, W.INIT_CONFIG2))
+    assert np.abs(rho - rr).max() < 1e-5
+    assert max(np.abs(ux - uxr).max(), np.abs(uy - uyr).max()) < 1e-5
+    del torch
+
+
+def test_mass_conservation_fp32():
+    model, d = split_preset("MIPS_RHO1")
+    sim = gpu_sim(model, d, 256, 128, SEED, W.INIT_CONFIG1)
+    m0 = sim.observables()["mass"]
+    sim.step(1000)
+    m1 = sim.observables()["mass"]
+    sim.close()
+    assert abs(m1 - m0) / m0 < 1e-6
+
+
+# ------------------------------------------------------ bitwise invariants --
+@pytest.mark.parametrize("name", ["MIPS_RHO1", "CIL_RHO1"])
+def test_density_rescaling_bitwise_gpu(name):
+    """(f, C, rho*, A, sigma) -> (2f, C/2, 2rho*, A/4, 2sigma) gives exactly 2x the trajectory."""
+    model, d = split_preset(name)
+    d2 = dict(d, C=d["C"] / 2, rho_star=d["rho_star"] * 2, A=d["A"] / 4, sigma=d["sigma"] * 2)
+    spec = dict(W.INIT_CONFIG2)
+    spec2 = dict(spec, rho_mean=2 * spec["rho_mean"])
+    a = gpu_run(model, d, 96, 48, 200, SEED, spec)
+    b = gpu_run(model, d2, 96, 48, 200, SEED, spec2)
+    np.testing.assert_array_equal(b, 2 * a)
+
+
+def test_batch_equals_solo_runs():
+    from paper_1902_00530_gb300 import Lattice, Simulation
+    cfg = [(Lattice(64, 64, "f32", 0), "cil", split_preset("CIL_RHO1")[1], W.INIT_CONFIG2),
+           (Lattice(96, 32, "f32", 1), "mips", split_preset("MIPS_RHO1")[1], W.INIT_CONFIG1),
+           (Lattice(64, 64, "f32", 2), "cil", split_preset("CIL_RHO1", B=0.05)[1], dict(W.INIT_CONFIG2, rho_mean=0.7)),
+           (Lattice(128, 40, "bf16s", 3), "mips", split_preset("MIPS_PAPER_LITERAL")[1], W.INIT_CONFIG1)]
+    sim = Simulation([c[0] for c in cfg], [c[1] for c in cfg], [c[2] for c in cfg])
+    sim.init(SEED, [c[3] for c in cfg])
+    sim.step(60)
+    batch = [sim.get_state(k, host=True).numpy() for k in range(len(cfg))]
+    sim.close()
+    for k, (lat, model, d, spec) in enumerate(cfg):
+        solo = gpu_run(model, d, lat.nx, lat.ny, 60, SEED, spec, storage=lat.storage, lattice_id=lat.id)
+        np.testing.assert_array_equal(batch[k], solo.astype(np.float32))
+
+
+def test_resume_is_bit_exact(tmp_path):
+    model, d = split_preset("MIPS_RHO1")
+    sim = gpu_sim(model, d, 64, 48, SEED, W.INIT_CONFIG1)
+    sim.step(30)
+    sim.save(str(tmp_path / "s.lbm"))
+    sim.step(30)
+    full = sim.get_state(host=True).numpy()
+    sim.close()
+    sim = gpu_sim(model, d, 64, 48, SEED + 1, W.INIT_CONFIG2)  # different state, then load
+    sim.load(str(tmp_path / "s.lbm"))
+    assert sim.time == 30
+    sim.step(30)
+    np.testing.assert_array_equal(sim.get_state(host=True).numpy(), full)
+    sim.close()
+
+
+def test_graphs_on_off_identical():
+    model, d = split_preset("CIL_RHO1")
+    a = gpu_run(model, d, 64, 64, 77, SEED, W.INIT_CONFIG2, graphs=True, sample_every=10, ring=8)
+    b = gpu_run(model, d, 64, 64, 77, SEED, W.INIT_CONFIG2, graphs=False, sample_every=10, ring=8)
+    np.testing.assert_array_equal(a, b)
+
+
+def test_rotation_equivariance_gpu():
+    """90-degree rotation commutes with the step (sigma = 0), to round-off."""
+    model, d = split_preset("CIL_RHO1", sigma=0.0)
+    n = 64
+    from paper_1902_00530_gb300 import Lattice, Simulation
+    rot = np.array([0, 2, 3, 4, 1, 6, 7, 8, 5])
+    f0 = O.init(n, n, SEED, **W.INIT_CONFIG2, prm=O.params(**d))
+
+    def rotate(f):
+        g = np.empty_like(f)
+        y, x = np.mgrid[0:n, 0:n]
+        for i in range(9):
+            g[rot[i], x, (-y) % n] = f[i, y, x]
+        return g
+    out = []
+    for f in (f0, rotate(f0)):
+        sim = Simulation([Lattice(n, n)], [model], [d])
+        sim.set_state(f.astype(np.float32))
+        sim.step(20)
+        out.append(sim.get_state(host=True).numpy().astype(np.float64))
+        sim.close()
+    assert np.abs(rotate(out[0]) - out[1]).max() < 1e-6
+
+
+# ---------------------------------------------- full size, sampled sites ---
+@pytest.mark.parametrize("storage", ["f32", "bf16s"])
+def test_full_size_sampled_parity(storage):
+    """The 8192^2 MIPS workload in the tuned launch shape the benchmark uses:
+    after k steps, sampled sites (corners, edges, interior) against oracle
+    windows of the same global coordinates (exact inside the light cone)."""
+    from paper_1902_00530_gb300 import Lattice, Simulation
+    model, d = split_preset("MIPS_RHO1")
+    N, k, R = 8192, 3, 10
+    sim = Simulation([Lattice(N, N, storage)], [model], [d])
+    sim.init(SEED, [W.INIT_CONFIG1])
+    sim.tune()
+    sim.step(k)
+    rho, ux, uy = (a.cpu().numpy().astype(np.float64) for a in sim.moments())
+    sim.close()
+    tol = 1e-5 if storage == "f32" else 2e-3
+    p = O.params(**d)
+    for (cx, cy) in [(0, 0), (N - 1, N - 1), (0, N // 2), (4097, 3), (1234, 5678), (N - 3, 17)]:
+        w = 2 * R + 1
+        win = (cx - R, cy - R, N, N)
+        f = O.run(O.init(w, w, SEED, **W.INIT_CONFIG1, prm=p, window=win), model, p, SEED, 0, k, window=win)
+        rr, uxr, uyr = O.moments(f)
+        m = R - 2 * k
+        ys = [(cy + j) % N for j in range(-m, m + 1)]
+        xs = [(cx + i) % N for i in range(-m, m + 1)]
+        g_r = rho[np.ix_(ys, xs)]
+        sl = slice(R - m, R + m + 1)
+        assert np.abs(g_r - rr[sl, sl]).max() / rr.mean() <= tol
+        du = max(np.abs(ux[np.ix_(ys, xs)] - uxr[sl, sl]).max(), np.abs(uy[np.ix_(ys, xs)] - uyr[sl, sl]).max())
+        assert du / max(np.hypot(uxr, uyr).max(), 1e-3) <= tol
+
+
+# ------------------------------------------------------------ edge cases ---
+def test_zero_steps_and_limits():
+    from paper_1902_00530_gb300 import LBMError
+    model, d = split_preset("PASSIVE", sigma=0.01)
+    sim = gpu_sim(model, d, 16, 16, SEED, W.INIT_CONFIG2)
+    f0 = sim.get_state(host=True).numpy()
+    sim.step(0)
+    assert sim.time == 0
+    np.testing.assert_array_equal(sim.get_state(host=True).numpy(), f0)
+    with pytest.raises(LBMError):
+        sim.step(-1)
+    with pytest.raises(LBMError):
+        sim.step(2 ** 32)
+    with pytest.raises(LBMError):
+        sim.observables(lattice=3)
+    sim.close()
