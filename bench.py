@@ -143,6 +143,10 @@ def workload_spec(name: str):
         d = W.preset("MIPS_RHO1")
         return dict(nx=8192, ny=8192, model=d.pop("model"), params=d, init=W.INIT_CONFIG1, sample_every=100,
                     seed=W.seed(3), label="mips_rho1_8192x8192")
+    if name == "mips4096":  # a smaller case of the same workload, for profiler captures
+        d = W.preset("MIPS_RHO1")
+        return dict(nx=4096, ny=4096, model=d.pop("model"), params=d, init=W.INIT_CONFIG1, sample_every=100,
+                    seed=W.seed(3), label="mips_rho1_4096x4096")
     if name == "cil1024":
         d = W.preset("CIL_RHO1")
         return dict(nx=1024, ny=1024, model=d.pop("model"), params=d, init=W.INIT_CONFIG2, sample_every=100,
@@ -163,7 +167,12 @@ def run_gpu(args, world, rank, local):
     sim = Simulation([Lattice(wl["nx"], wl["ny"], storage, rank)], [wl["model"]], [wl["params"]],
                      sample_every=wl["sample_every"], ring_capacity=max(16, args.steps // wl["sample_every"] + 4))
     sim.init(wl["seed"], [wl["init"]])
-    sim.tune()
+    if args.shape:
+        v, r, w = (int(x) for x in args.shape.split(","))
+        sim.set_tuning(1, v, r, w)
+    else:
+        sim.tune()
+    shape = sim.get_tuning()
     sim.step(args.warmup)
     sim.synchronize()
     cells = wl["nx"] * wl["ny"]
@@ -241,7 +250,7 @@ def run_gpu(args, world, rank, local):
     if rank == 0 and not args.quick:
         extra = secondary_lines(args, wl)
     return dict(value=value, ms=ms_max, clocks=clocks, roofline=roofline, e2e=e2e, launches=launches,
-                obs=obs, extra=extra, wl=wl)
+                obs=obs, extra=extra, wl=wl, shape=shape)
 
 
 def secondary_lines(args, wl):
@@ -363,6 +372,7 @@ def main():
     ap.add_argument("--storage", default="f32", choices=["f32", "f16s", "bf16s"])
     ap.add_argument("--quick", action="store_true", help="skip the secondary (16-bit, batched) lines")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--shape", default="", help="fixed launch shape vec,rows,warps instead of tuning")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -384,7 +394,9 @@ def main():
         "config": {"workload": wl["label"] + "_" + args.storage, "nx": wl["nx"], "ny": wl["ny"],
                    "closure": wl["model"], "storage": args.storage, "sample_every": wl["sample_every"],
                    "replicas": world, "l2": "inputs larger than L2 (populations 4.8 GB FP32); no flush",
-                   "timing": "CUDA events on the library stream around lbm_step(K); per-kernel event pairs"},
+                   "timing": "CUDA events on the library stream around lbm_step(K); per-kernel event pairs",
+                   "launch_shape": {"vec": r["shape"][0], "rows": r["shape"][1], "warps": r["shape"][2],
+                                    "chosen_by": "fixed" if args.shape else "tuner"}},
         "gpu_launches": r["launches"],
         "clocks": clocks,
         "roofline": r["roofline"],

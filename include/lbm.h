@@ -183,9 +183,11 @@ lbm_status lbm_save(lbm_ctx *ctx, const char *path);
 lbm_status lbm_load(lbm_ctx *ctx, const char *path);
 
 /* Launch-shape tuning.  mode 0: automatic on the first lbm_step (default);
- * mode 1: off, use the fixed shape (vec, rows) given; vec = sites per thread
- * along x (1, 2, 4 or 8, dividing nx) and rows = rows per warp strip. */
-lbm_status lbm_set_tuning(lbm_ctx *ctx, int32_t mode, int32_t vec, int32_t rows);
+ * mode 1: off, use the fixed shape given for every lattice: vec = sites per
+ * thread along x (1, 2 or 4 for FP32; 1, 2, 4 or 8 for 16-bit storage; must
+ * divide nx), rows = rows per warp strip (16..4096), warps = warps per block
+ * (1..8).  Host only; re-uploads descriptors (syncs) when bound. */
+lbm_status lbm_set_tuning(lbm_ctx *ctx, int32_t mode, int32_t vec, int32_t rows, int32_t warps);
 
 /* Run the tuner now (times candidate shapes on the bound buffers without
  * changing the state).  Syncs. */

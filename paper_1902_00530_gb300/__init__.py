@@ -191,8 +191,8 @@ class Simulation:
     def tune(self) -> None:
         self._check(self.lib.lbm_tune(self.ctx))
 
-    def set_tuning(self, mode: int, vec: int = 1, rows: int = 32) -> None:
-        self._check(self.lib.lbm_set_tuning(self.ctx, mode, vec, rows))
+    def set_tuning(self, mode: int, vec: int = 1, rows: int = 32, warps: int = 4) -> None:
+        self._check(self.lib.lbm_set_tuning(self.ctx, mode, vec, rows, warps))
 
     def get_tuning(self, lattice: int = 0) -> tuple:
         v, r, w = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()

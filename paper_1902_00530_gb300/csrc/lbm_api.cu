@@ -911,7 +911,7 @@ lbm_status lbm_load(lbm_ctx *c, const char *path)
     return LBM_OK;
 }
 
-lbm_status lbm_set_tuning(lbm_ctx *c, int32_t mode, int32_t vec, int32_t rows)
+lbm_status lbm_set_tuning(lbm_ctx *c, int32_t mode, int32_t vec, int32_t rows, int32_t warps)
 {
     if (!c) return LBM_ERR_INVALID_ARG;
     if (mode == 0) {
@@ -921,6 +921,7 @@ lbm_status lbm_set_tuning(lbm_ctx *c, int32_t mode, int32_t vec, int32_t rows)
     }
     if (mode != 1) return fail(c, LBM_ERR_INVALID_ARG, "mode must be 0 or 1");
     if (rows < ROWS_MIN || rows > 4096) return fail(c, LBM_ERR_INVALID_ARG, "rows must be in [16, 4096]");
+    if (warps < 1 || warps > 8) return fail(c, LBM_ERR_INVALID_ARG, "warps must be in [1, 8]");
     for (auto &g : c->groups) {
         if (!allowed_vec(g.storage, vec)) return fail(c, LBM_ERR_INVALID_ARG, "vec not available for this storage");
         for (int m : g.members)
@@ -929,7 +930,7 @@ lbm_status lbm_set_tuning(lbm_ctx *c, int32_t mode, int32_t vec, int32_t rows)
     for (auto &g : c->groups) {
         g.vec = vec;
         g.rows = rows;
-        g.warps = 4;
+        g.warps = warps;
     }
     c->tune_mode = 1;
     c->tuned = true;

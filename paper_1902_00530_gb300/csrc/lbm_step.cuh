@@ -72,25 +72,27 @@ __device__ __forceinline__ void pull_row(const typename Store<ST>::T *base, size
     pull_pop<ST, VEC, 8>(base + 8 * plane, y, ny, nx, pitch, x0, valid, last, lane, wq(8) * rho0, f[8]);
 }
 
-// Post-stream density of one site by nine scalar pulls (strip-edge halo).
-template <int ST>
-__device__ __forceinline__ float pulled_density(const typename Store<ST>::T *base, size_t plane,
-                                                int x, int y, int nx, int ny, int pitch, float rho0)
-{
-    float s = 0.f;
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        const int xs = wrap_once(x - vx(i), nx), ys = wrap_once(y - vy(i), ny);
-        s += load_one<ST>(base + i * plane + (size_t)ys * pitch + xs, wq(i) * rho0);
-    }
-    return s;
-}
-
 template <int VEC>
 __device__ __forceinline__ float density(const float f[9][VEC], int j)
 {
     return ((f[0][j] + f[1][j]) + (f[2][j] + f[3][j])) + ((f[4][j] + f[5][j]) + (f[6][j] + f[7][j])) +
            f[8][j];
+}
+
+// Post-stream density of one site by nine scalar pulls (strip-edge halo),
+// summed in the same order as density() so the result does not depend on
+// where the strip edges fall.
+template <int ST>
+__device__ __forceinline__ float pulled_density(const typename Store<ST>::T *base, size_t plane,
+                                                int x, int y, int nx, int ny, int pitch, float rho0)
+{
+    float v[9][1];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const int xs = wrap_once(x - vx(i), nx), ys = wrap_once(y - vy(i), ny);
+        v[i][0] = load_one<ST>(base + i * plane + (size_t)ys * pitch + xs, wq(i) * rho0);
+    }
+    return density<1>(v, 0);
 }
 
 // Density of this lane's VEC sites plus the two x-neighbours, for one row.
@@ -112,11 +114,31 @@ __device__ __forceinline__ void density_window(const float f[9][VEC], const type
     r[VEC + 1] = right;
 }
 
+// Model parameters of one lattice, held in registers.
+struct SiteParams {
+    float omega, sigma_q, C, inv_rho_star, rho_star, u_max, u_max2, A, B;
+};
+
+__device__ __forceinline__ SiteParams load_params(const LatDesc *dp)
+{
+    SiteParams p;
+    p.omega = dp->omega;
+    p.sigma_q = dp->sigma_q;
+    p.C = dp->C;
+    p.inv_rho_star = dp->inv_rho_star;
+    p.rho_star = dp->rho_star;
+    p.u_max = dp->u_max;
+    p.u_max2 = dp->u_max2;
+    p.A = dp->A;
+    p.B = dp->B;
+    return p;
+}
+
 // The per-site update after streaming (App. A.2 steps 2-6).  f holds f* on
 // entry and the new populations on exit.  (gx, gy) is the isotropic gradient
 // of the post-stream density (MIPS only).  kn are the nine noise integers.
 template <int MODEL>
-__device__ __forceinline__ void collide_site(float f[9], float gx, float gy, const LatDesc &d,
+__device__ __forceinline__ void collide_site(float f[9], float gx, float gy, const SiteParams &d,
                                              bool noise, const int kn[9])
 {
     // step 2: moments of f*
@@ -242,13 +264,13 @@ __device__ __forceinline__ void observe_row(const float g[9][VEC], bool valid, d
 }
 
 template <int VEC>
-__device__ __forceinline__ void observe_flush(const LatDesc &d, int s, int sx, int sy, int x0,
+__device__ __forceinline__ void observe_flush(double *colp, double *scal, int nx, int s, int sy, int x0,
                                               bool valid, const double col[VEC], double acc[5],
                                               int lane)
 {
     if (valid) {
 #pragma unroll
-        for (int j = 0; j < VEC; ++j) d.colp[(size_t)sy * d.nx + x0 + j] = col[j];
+        for (int j = 0; j < VEC; ++j) colp[(size_t)sy * nx + x0 + j] = col[j];
     }
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
@@ -257,9 +279,8 @@ __device__ __forceinline__ void observe_flush(const LatDesc &d, int s, int sx, i
     }
     if (lane == 0) {
 #pragma unroll
-        for (int q = 0; q < 5; ++q) d.scal[(size_t)s * 5 + q] = acc[q];
+        for (int q = 0; q < 5; ++q) scal[(size_t)s * 5 + q] = acc[q];
     }
-    (void)sx;
 }
 
 __device__ __forceinline__ int find_lattice(const LatDesc *desc, int nlat, int block)
@@ -278,19 +299,22 @@ __global__ void __launch_bounds__(256) step_kernel(const StepArgs a)
 {
     using T = typename Store<ST>::T;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const LatDesc d = a.desc[find_lattice(a.desc, a.nlat, blockIdx.x)];
-    const int s = (blockIdx.x - d.block_begin) * (blockDim.x >> 5) + warp;
-    if (s >= d.nsx * d.nsy) return;  // whole warp leaves together
-    const int nx = d.nx, ny = d.ny, pitch = d.pitch;
-    const int sx = s % d.nsx, sy = s / d.nsx;
+    const LatDesc *dp = a.desc + find_lattice(a.desc, a.nlat, blockIdx.x);
+    const int nsx = dp->nsx, nsy = dp->nsy;
+    const int s = (blockIdx.x - dp->block_begin) * (blockDim.x >> 5) + warp;
+    if (s >= nsx * nsy) return;  // whole warp leaves together
+    const int nx = dp->nx, ny = dp->ny, pitch = dp->pitch, rows = dp->rows;
+    const SiteParams d = load_params(dp);
+    const int sx = s % nsx, sy = s / nsx;
     const int x0 = sx * 32 * VEC + lane * VEC;
     const bool valid = x0 < nx;
     const bool last = (lane == 31) || (x0 + VEC >= nx);
-    const int y_begin = sy * d.rows, y_end = min(y_begin + d.rows, ny);
+    const int y_begin = sy * rows, y_end = min(y_begin + rows, ny);
     const size_t plane = (size_t)ny * pitch;
-    const T *src = reinterpret_cast<const T *>(d.f[a.src]);
-    T *dst = reinterpret_cast<T *>(d.f[a.src ^ 1]);
-    const float rho0 = d.rho0;
+    const T *src = reinterpret_cast<const T *>(dp->f[a.src]);
+    T *dst = reinterpret_cast<T *>(dp->f[a.src ^ 1]);
+    const float rho0 = dp->rho0;
+    const uint32_t id = (uint32_t)dp->id;
     const uint32_t t = *a.t_ptr + a.k;
     const bool noise = d.sigma_q > 0.f;
 
@@ -337,7 +361,7 @@ __global__ void __launch_bounds__(256) step_kernel(const StepArgs a)
                 gy = (1.f / 3.f) * (rn[j + 1] - rm[j + 1]) + (1.f / 12.f) * ((ne + nw) - (se + sw));
             }
             int kn[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-            if (noise && valid) noise_ints((uint32_t)(x0 + j), (uint32_t)y, t, (uint32_t)d.id, a.key0, a.key1, kn);
+            if (noise && valid) noise_ints((uint32_t)(x0 + j), (uint32_t)y, t, id, a.key0, a.key1, kn);
             collide_site<MODEL>(f, gx, gy, d, noise, kn);
 #pragma unroll
             for (int i = 0; i < 9; ++i) out[i][j] = f[i];
@@ -355,7 +379,7 @@ __global__ void __launch_bounds__(256) step_kernel(const StepArgs a)
 #pragma unroll
                 for (int j = 0; j < VEC; ++j)
                     g[i][j] = Store<ST>::get(Store<ST>::put(out[i][j], wq(i) * rho0), wq(i) * rho0);
-            observe_row<VEC>(g, valid, col, acc, d.rowp + (size_t)sx * ny + y, lane);
+            observe_row<VEC>(g, valid, col, acc, dp->rowp + (size_t)sx * ny + y, lane);
         }
         if constexpr (MODEL == MODEL_MIPS) {
 #pragma unroll
@@ -369,7 +393,7 @@ __global__ void __launch_bounds__(256) step_kernel(const StepArgs a)
             }
         }
     }
-    if constexpr (SAMPLE) observe_flush<VEC>(d, s, sx, sy, x0, valid, col, acc, lane);
+    if constexpr (SAMPLE) observe_flush<VEC>(dp->colp, dp->scal, nx, s, sy, x0, valid, col, acc, lane);
 }
 
 // Observable partials of the stored state without stepping (same strip
@@ -379,16 +403,18 @@ __global__ void __launch_bounds__(256) observe_kernel(const StepArgs a)
 {
     using T = typename Store<ST>::T;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const LatDesc d = a.desc[find_lattice(a.desc, a.nlat, blockIdx.x)];
-    const int s = (blockIdx.x - d.block_begin) * (blockDim.x >> 5) + warp;
-    if (s >= d.nsx * d.nsy) return;
-    const int nx = d.nx, ny = d.ny, pitch = d.pitch;
-    const int sx = s % d.nsx, sy = s / d.nsx;
+    const LatDesc *dp = a.desc + find_lattice(a.desc, a.nlat, blockIdx.x);
+    const int nsx = dp->nsx, nsy = dp->nsy;
+    const int s = (blockIdx.x - dp->block_begin) * (blockDim.x >> 5) + warp;
+    if (s >= nsx * nsy) return;
+    const int nx = dp->nx, ny = dp->ny, pitch = dp->pitch, rows = dp->rows;
+    const float rho0 = dp->rho0;
+    const int sx = s % nsx, sy = s / nsx;
     const int x0 = sx * 32 * VEC + lane * VEC;
     const bool valid = x0 < nx;
-    const int y_begin = sy * d.rows, y_end = min(y_begin + d.rows, ny);
+    const int y_begin = sy * rows, y_end = min(y_begin + rows, ny);
     const size_t plane = (size_t)ny * pitch;
-    const T *src = reinterpret_cast<const T *>(d.f[a.src]);
+    const T *src = reinterpret_cast<const T *>(dp->f[a.src]);
     double col[VEC], acc[5];
 #pragma unroll
     for (int j = 0; j < VEC; ++j) col[j] = 0.0;
@@ -399,15 +425,15 @@ __global__ void __launch_bounds__(256) observe_kernel(const StepArgs a)
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             if (valid) {
-                load_vec<ST, VEC>(src + i * plane + (size_t)y * pitch + x0, wq(i) * d.rho0, g[i]);
+                load_vec<ST, VEC>(src + i * plane + (size_t)y * pitch + x0, wq(i) * rho0, g[i]);
             } else {
 #pragma unroll
                 for (int j = 0; j < VEC; ++j) g[i][j] = 0.f;
             }
         }
-        observe_row<VEC>(g, valid, col, acc, d.rowp + (size_t)sx * ny + y, lane);
+        observe_row<VEC>(g, valid, col, acc, dp->rowp + (size_t)sx * ny + y, lane);
     }
-    observe_flush<VEC>(d, s, sx, sy, x0, valid, col, acc, lane);
+    observe_flush<VEC>(dp->colp, dp->scal, nx, s, sy, x0, valid, col, acc, lane);
 }
 
 }  // namespace lbm
