@@ -168,8 +168,8 @@ def run_gpu(args, world, rank, local):
                      sample_every=wl["sample_every"], ring_capacity=max(16, args.steps // wl["sample_every"] + 4))
     sim.init(wl["seed"], [wl["init"]])
     if args.shape:
-        v, r, w = (int(x) for x in args.shape.split(","))
-        sim.set_tuning(1, v, r, w)
+        sh = [int(x) for x in args.shape.split(",")]
+        sim.set_tuning(1, *sh)
     else:
         sim.tune()
     shape = sim.get_tuning()
@@ -372,7 +372,7 @@ def main():
     ap.add_argument("--storage", default="f32", choices=["f32", "f16s", "bf16s"])
     ap.add_argument("--quick", action="store_true", help="skip the secondary (16-bit, batched) lines")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--shape", default="", help="fixed launch shape vec,rows,warps instead of tuning")
+    ap.add_argument("--shape", default="", help="fixed launch shape vec,rows,warps[,stages] instead of tuning")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -396,6 +396,9 @@ def main():
                    "replicas": world, "l2": "inputs larger than L2 (populations 4.8 GB FP32); no flush",
                    "timing": "CUDA events on the library stream around lbm_step(K); per-kernel event pairs",
                    "launch_shape": {"vec": r["shape"][0], "rows": r["shape"][1], "warps": r["shape"][2],
+                                    "stages": r["shape"][3],
+                                    "kernel": "staged (bulk-copy rows in shared memory)" if r["shape"][3]
+                                    else "direct (vector loads + shuffles)",
                                     "chosen_by": "fixed" if args.shape else "tuner"}},
         "gpu_launches": r["launches"],
         "clocks": clocks,

@@ -186,16 +186,22 @@ lbm_status lbm_load(lbm_ctx *ctx, const char *path);
  * mode 1: off, use the fixed shape given for every lattice: vec = sites per
  * thread along x (1, 2 or 4 for FP32; 1, 2, 4 or 8 for 16-bit storage; must
  * divide nx), rows = rows per warp strip (16..4096), warps = warps per block
- * (1..8).  Host only; re-uploads descriptors (syncs) when bound. */
-lbm_status lbm_set_tuning(lbm_ctx *ctx, int32_t mode, int32_t vec, int32_t rows, int32_t warps);
+ * (1..8), stages = 0 for the kernel that loads populations straight from
+ * global memory, or 2..8 (MIPS: 3..8; at most 4 warps) for the kernel that
+ * stages population rows in shared memory with bulk copies, that many rows
+ * per warp (needs nx a multiple of 16 bytes of storage).  Host only;
+ * re-uploads descriptors (syncs) when bound. */
+lbm_status lbm_set_tuning(lbm_ctx *ctx, int32_t mode, int32_t vec, int32_t rows, int32_t warps,
+                          int32_t stages);
 
 /* Run the tuner now (times candidate shapes on the bound buffers without
  * changing the state).  Syncs. */
 lbm_status lbm_tune(lbm_ctx *ctx);
 
-/* The launch shape in use for lattice `lattice`: vec, rows, warps per block. */
+/* The launch shape in use for lattice `lattice`: vec, rows, warps per block,
+ * stages (0 = direct-load kernel). */
 lbm_status lbm_get_tuning(const lbm_ctx *ctx, int32_t lattice, int32_t *vec, int32_t *rows,
-                          int32_t *warps);
+                          int32_t *warps, int32_t *stages);
 
 /* CUDA-graph replay of lbm_step: 1 = capture each distinct step sequence once
  * and replay it (default), 0 = launch kernels directly. */

@@ -191,13 +191,17 @@ class Simulation:
     def tune(self) -> None:
         self._check(self.lib.lbm_tune(self.ctx))
 
-    def set_tuning(self, mode: int, vec: int = 1, rows: int = 32, warps: int = 4) -> None:
-        self._check(self.lib.lbm_set_tuning(self.ctx, mode, vec, rows, warps))
+    def set_tuning(self, mode: int, vec: int = 1, rows: int = 32, warps: int = 4, stages: int = 0) -> None:
+        """mode 0: automatic; mode 1: fixed shape (stages 0 = direct-load kernel,
+        2..8 = shared-memory staged kernel with that many row buffers per warp)."""
+        self._check(self.lib.lbm_set_tuning(self.ctx, mode, vec, rows, warps, stages))
 
     def get_tuning(self, lattice: int = 0) -> tuple:
-        v, r, w = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
-        self._check(self.lib.lbm_get_tuning(self.ctx, lattice, ctypes.byref(v), ctypes.byref(r), ctypes.byref(w)))
-        return v.value, r.value, w.value
+        """(vec, rows, warps, stages) of the launch shape in use."""
+        v, r, w, s = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        self._check(self.lib.lbm_get_tuning(self.ctx, lattice, ctypes.byref(v), ctypes.byref(r), ctypes.byref(w),
+                                            ctypes.byref(s)))
+        return v.value, r.value, w.value, s.value
 
     def set_graphs(self, enabled: bool) -> None:
         self._check(self.lib.lbm_set_graphs(self.ctx, 1 if enabled else 0))

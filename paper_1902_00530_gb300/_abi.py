@@ -56,10 +56,12 @@ SIGNATURES = {
     "lbm_get_time": (ctypes.c_int, [_CTX, ctypes.POINTER(ctypes.c_int64)]),
     "lbm_save": (ctypes.c_int, [_CTX, ctypes.c_char_p]),
     "lbm_load": (ctypes.c_int, [_CTX, ctypes.c_char_p]),
-    "lbm_set_tuning": (ctypes.c_int, [_CTX, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
+    "lbm_set_tuning": (ctypes.c_int, [_CTX, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                      ctypes.c_int32]),
     "lbm_tune": (ctypes.c_int, [_CTX]),
     "lbm_get_tuning": (ctypes.c_int, [_CTX, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
-                                      ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
+                                      ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                      ctypes.POINTER(ctypes.c_int32)]),
     "lbm_set_graphs": (ctypes.c_int, [_CTX, ctypes.c_int32]),
     "lbm_last_launch_count": (ctypes.c_int, [_CTX, ctypes.POINTER(ctypes.c_int64)]),
     "lbm_set_profiling": (ctypes.c_int, [_CTX, ctypes.c_int32]),

@@ -50,6 +50,7 @@ struct GroupHost {
     int model = 0, storage = 0;
     std::vector<int> members;
     int vec = 1, rows = 32, warps = 4, blocks = 0;
+    int stages = 0;  // 0: direct-load kernel; >= 2: TMA-staged kernel with that many row buffers
     size_t desc_off = 0;
 };
 
@@ -129,6 +130,15 @@ std::string validate(const lbm_lattice &l, int model, const lbm_params &p)
     if (model == LBM_MIPS && !(p.rho_star > 0)) return "MIPS needs rho_star > 0";
     if (model == LBM_MIPS && p.u_max < 0) return "MIPS needs u_max >= 0";
     return "";
+}
+
+// The staged kernel copies 16-byte halos: nx must be a multiple of that width.
+bool staged_ok(const lbm_ctx *c, const GroupHost &g)
+{
+    const int halo = g.storage == LBM_F32 ? 4 : 8;
+    for (int m : g.members)
+        if (c->lats[m].lat.nx % halo != 0 || c->lats[m].lat.nx < halo) return false;
+    return true;
 }
 
 int allowed_vec(int storage, int v)
@@ -290,9 +300,14 @@ cudaError_t launch_group_step(const lbm_ctx *c, const GroupHost &g, int src, uin
     a.k = k;
     a.key0 = (uint32_t)c->seed;
     a.key1 = (uint32_t)(c->seed >> 32);
-    if (g.storage == LBM_F32) return launch_step_f32(g.model, g.vec, sample, a, g.blocks, g.warps, c->stream);
-    if (g.storage == LBM_F16_SHIFTED) return launch_step_f16(g.model, g.vec, sample, a, g.blocks, g.warps, c->stream);
-    return launch_step_bf16(g.model, g.vec, sample, a, g.blocks, g.warps, c->stream);
+    a.stages = g.stages;
+    a.err = err_dev(c);
+    const int kind = g.stages > 0 ? 1 : 0;
+    if (g.storage == LBM_F32)
+        return launch_step_f32(g.model, kind, g.vec, sample, a, g.blocks, g.warps, c->stream);
+    if (g.storage == LBM_F16_SHIFTED)
+        return launch_step_f16(g.model, kind, g.vec, sample, a, g.blocks, g.warps, c->stream);
+    return launch_step_bf16(g.model, kind, g.vec, sample, a, g.blocks, g.warps, c->stream);
 }
 
 cudaError_t launch_group_observe(const lbm_ctx *c, const GroupHost &g, int src)
@@ -304,6 +319,8 @@ cudaError_t launch_group_observe(const lbm_ctx *c, const GroupHost &g, int src)
     a.t_ptr = t_dev(c);
     a.k = 0;
     a.key0 = a.key1 = 0;
+    a.stages = 0;
+    a.err = err_dev(c);
     if (g.storage == LBM_F32) return launch_observe_f32(g.vec, a, g.blocks, g.warps, c->stream);
     if (g.storage == LBM_F16_SHIFTED) return launch_observe_f16(g.vec, a, g.blocks, g.warps, c->stream);
     return launch_observe_bf16(g.vec, a, g.blocks, g.warps, c->stream);
@@ -387,56 +404,69 @@ lbm_status require_ready(lbm_ctx *c, bool need_init)
     return LBM_OK;
 }
 
+struct Shape {
+    int vec, rows, warps, stages;
+};
+
 lbm_status tune_group(lbm_ctx *c, GroupHost &g)
 {
-    std::vector<int> vecs;
+    std::vector<Shape> cands;
+    long long max_ny = 1;
+    for (int m : g.members) max_ny = std::max<long long>(max_ny, c->lats[m].lat.ny);
     const int all_v[] = {1, 2, 4, 8};
+    const bool staged = staged_ok(c, g);
+    const int base_stages = g.model == LBM_MIPS ? 4 : 3;
     for (int v : all_v) {
         if (!allowed_vec(g.storage, v)) continue;
         bool ok = true;
         for (int m : g.members) ok = ok && (c->lats[m].lat.nx % v == 0);
-        if (ok) vecs.push_back(v);
+        if (!ok) continue;
+        for (int r : {16, 32, 64, 128}) {
+            if (r > 16 && r > 2 * max_ny) continue;
+            for (int w : {4, 8}) cands.push_back({v, r, w, 0});
+            if (staged && v >= 2)
+                for (int w : {2, 4})
+                    for (int st : {base_stages, base_stages + 2}) cands.push_back({v, r, w, st});
+        }
     }
-    const int rows_c[] = {16, 32, 64, 128};
-    const int warps_c[] = {4, 8};
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0), "create event");
     CK(cudaEventCreate(&e1), "create event");
     float best = 1e30f;
-    int bv = g.vec, br = g.rows, bw = g.warps;
-    long long max_ny = 1;
-    for (int m : g.members) max_ny = std::max<long long>(max_ny, c->lats[m].lat.ny);
-    for (int v : vecs)
-        for (int r : rows_c) {
-            if (r > 16 && r > 2 * max_ny) continue;
-            for (int w : warps_c) {
-                g.vec = v;
-                g.rows = r;
-                g.warps = w;
-                lbm_status st = upload_descs(c);
-                if (st != LBM_OK) return st;
-                CK(launch_group_step(c, g, c->parity, 0, false), "tuning launch");
-                CK(cudaEventRecord(e0, c->stream), "record event");
-                const int reps = 3;
-                for (int q = 0; q < reps; ++q) CK(launch_group_step(c, g, c->parity, 0, false), "tuning launch");
-                CK(cudaEventRecord(e1, c->stream), "record event");
-                CK(cudaEventSynchronize(e1), "synchronise event");
-                float ms = 0.f;
-                CK(cudaEventElapsedTime(&ms, e0, e1), "event time");
-                if (ms < best) {
-                    best = ms;
-                    bv = v;
-                    br = r;
-                    bw = w;
-                }
-            }
+    Shape bs{g.vec, g.rows, g.warps, g.stages};
+    for (const Shape &sh : cands) {
+        g.vec = sh.vec;
+        g.rows = sh.rows;
+        g.warps = sh.warps;
+        g.stages = sh.stages;
+        lbm_status st = upload_descs(c);
+        if (st != LBM_OK) return st;
+        cudaError_t e = launch_group_step(c, g, c->parity, 0, false);
+        if (e != cudaSuccess) {  // a shape this device cannot launch (e.g. shared memory): skip it
+            cudaGetLastError();
+            continue;
         }
+        CK(cudaEventRecord(e0, c->stream), "record event");
+        const int reps = 3;
+        for (int q = 0; q < reps; ++q) CK(launch_group_step(c, g, c->parity, 0, false), "tuning launch");
+        CK(cudaEventRecord(e1, c->stream), "record event");
+        CK(cudaEventSynchronize(e1), "synchronise event");
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1), "event time");
+        if (ms < best) {
+            best = ms;
+            bs = sh;
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    g.vec = bv;
-    g.rows = br;
-    g.warps = bw;
-    return upload_descs(c);
+    g.vec = bs.vec;
+    g.rows = bs.rows;
+    g.warps = bs.warps;
+    g.stages = bs.stages;
+    lbm_status st = upload_descs(c);
+    if (st != LBM_OK) return st;
+    return read_error_flag(c);
 }
 
 lbm_status do_tune(lbm_ctx *c)
@@ -911,7 +941,7 @@ lbm_status lbm_load(lbm_ctx *c, const char *path)
     return LBM_OK;
 }
 
-lbm_status lbm_set_tuning(lbm_ctx *c, int32_t mode, int32_t vec, int32_t rows, int32_t warps)
+lbm_status lbm_set_tuning(lbm_ctx *c, int32_t mode, int32_t vec, int32_t rows, int32_t warps, int32_t stages)
 {
     if (!c) return LBM_ERR_INVALID_ARG;
     if (mode == 0) {
@@ -922,6 +952,13 @@ lbm_status lbm_set_tuning(lbm_ctx *c, int32_t mode, int32_t vec, int32_t rows, i
     if (mode != 1) return fail(c, LBM_ERR_INVALID_ARG, "mode must be 0 or 1");
     if (rows < ROWS_MIN || rows > 4096) return fail(c, LBM_ERR_INVALID_ARG, "rows must be in [16, 4096]");
     if (warps < 1 || warps > 8) return fail(c, LBM_ERR_INVALID_ARG, "warps must be in [1, 8]");
+    if (stages != 0 && (stages < 2 || stages > 8 || warps > 4))
+        return fail(c, LBM_ERR_INVALID_ARG, "stages must be 0 (direct) or 2..8 with at most 4 warps");
+    if (stages != 0 && c->groups.size() && c->groups[0].model == LBM_MIPS && stages < 3)
+        return fail(c, LBM_ERR_INVALID_ARG, "MIPS needs at least 3 stages");
+    if (stages != 0)
+        for (auto &g : c->groups)
+            if (!staged_ok(c, g)) return fail(c, LBM_ERR_INVALID_ARG, "staged kernel needs nx a multiple of 16 bytes");
     for (auto &g : c->groups) {
         if (!allowed_vec(g.storage, vec)) return fail(c, LBM_ERR_INVALID_ARG, "vec not available for this storage");
         for (int m : g.members)
@@ -931,6 +968,7 @@ lbm_status lbm_set_tuning(lbm_ctx *c, int32_t mode, int32_t vec, int32_t rows, i
         g.vec = vec;
         g.rows = rows;
         g.warps = warps;
+        g.stages = stages;
     }
     c->tune_mode = 1;
     c->tuned = true;
@@ -946,14 +984,16 @@ lbm_status lbm_tune(lbm_ctx *c)
     return do_tune(c);
 }
 
-lbm_status lbm_get_tuning(const lbm_ctx *c, int32_t lattice, int32_t *vec, int32_t *rows, int32_t *warps)
+lbm_status lbm_get_tuning(const lbm_ctx *c, int32_t lattice, int32_t *vec, int32_t *rows, int32_t *warps,
+                          int32_t *stages)
 {
-    if (!c || !vec || !rows || !warps || lattice < 0 || lattice >= (int32_t)c->lats.size())
+    if (!c || !vec || !rows || !warps || !stages || lattice < 0 || lattice >= (int32_t)c->lats.size())
         return LBM_ERR_INVALID_ARG;
     const GroupHost &g = c->groups[c->lats[lattice].group];
     *vec = g.vec;
     *rows = g.rows;
     *warps = g.warps;
+    *stages = g.stages;
     return LBM_OK;
 }
 

@@ -73,6 +73,8 @@ struct StepArgs {
     const uint32_t *t_ptr;
     uint32_t k;           // step offset of this launch from *t_ptr
     uint32_t key0, key1;  // Philox key = seed
+    int stages;           // staged kernel: shared-memory row buffers per warp
+    unsigned *err;        // device error word (bounded waits report here)
 };
 
 // ---------------------------------------------------------------------------
@@ -168,6 +170,20 @@ __device__ __forceinline__ void load_vec(const typename Store<ST>::T *p, float s
                 out[h * (16 / (int)sizeof(T)) + j] = Store<ST>::get(e[j], shift);
         }
     }
+}
+
+// The same from any address space (shared memory): a plain vector load.
+template <int ST, int VEC>
+__device__ __forceinline__ void load_vec_plain(const typename Store<ST>::T *p, float shift, float out[VEC])
+{
+    using T = typename Store<ST>::T;
+    constexpr int BYTES = (int)sizeof(T) * VEC;
+    static_assert(BYTES <= 16, "vector wider than 16 bytes");
+    using W = typename VecWord<BYTES>::T;
+    const W w = *reinterpret_cast<const W *>(p);
+    const T *e = reinterpret_cast<const T *>(&w);
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) out[j] = Store<ST>::get(e[j], shift);
 }
 
 template <int ST, int VEC>

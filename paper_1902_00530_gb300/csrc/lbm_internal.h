@@ -6,11 +6,11 @@
 namespace lbm {
 
 // fused step / observe kernels (lbm_step_*.cu, one unit per storage type)
-cudaError_t launch_step_f32(int model, int vec, bool sample, const StepArgs &a, int blocks, int warps,
+cudaError_t launch_step_f32(int model, int kind, int vec, bool sample, const StepArgs &a, int blocks, int warps,
                             cudaStream_t stream);
-cudaError_t launch_step_f16(int model, int vec, bool sample, const StepArgs &a, int blocks, int warps,
+cudaError_t launch_step_f16(int model, int kind, int vec, bool sample, const StepArgs &a, int blocks, int warps,
                             cudaStream_t stream);
-cudaError_t launch_step_bf16(int model, int vec, bool sample, const StepArgs &a, int blocks, int warps,
+cudaError_t launch_step_bf16(int model, int kind, int vec, bool sample, const StepArgs &a, int blocks, int warps,
                              cudaStream_t stream);
 cudaError_t launch_observe_f32(int vec, const StepArgs &a, int blocks, int warps, cudaStream_t stream);
 cudaError_t launch_observe_f16(int vec, const StepArgs &a, int blocks, int warps, cudaStream_t stream);

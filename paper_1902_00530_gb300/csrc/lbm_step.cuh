@@ -182,10 +182,13 @@ __device__ __forceinline__ void collide_site(float f[9], float gx, float gy, con
         }
     }
     // step 3 (cont.): f^SS = w rho [1 + 3 e.u* + 9/2 (e.u*)^2 - 3/2 |u*|^2]
+    // The rest population takes rho minus the moving ones: identical to
+    // w_0 rho [1 - 3/2 |u*|^2] in exact arithmetic, but the FP32 weights sum
+    // to 1 + 7.5e-9, which would otherwise change the mass by that much at
+    // every collision.
     const float base = 1.f - 1.5f * (sx * sx + sy * sy);
-    const float r0 = wq(0) * rho, r1 = wq(1) * rho, r5 = wq(5) * rho;
+    const float r1 = wq(1) * rho, r5 = wq(5) * rho;
     float eq[9];
-    eq[0] = r0 * base;
     {
         const float tx = fmaf(4.5f * sx, sx, base), ty = fmaf(4.5f * sy, sy, base);
         eq[1] = r1 * fmaf(3.f, sx, tx);
@@ -198,6 +201,7 @@ __device__ __forceinline__ void collide_site(float f[9], float gx, float gy, con
         eq[7] = r5 * fmaf(-3.f, p, tp);
         eq[6] = r5 * fmaf(3.f, m, tm);
         eq[8] = r5 * fmaf(-3.f, m, tm);
+        eq[0] = rho - (((eq[1] + eq[3]) + (eq[2] + eq[4])) + ((eq[5] + eq[7]) + (eq[6] + eq[8])));
     }
     // step 4: BGK redistribution f = f* - (f* - f^SS)/tau
 #pragma unroll
@@ -439,48 +443,3 @@ __global__ void __launch_bounds__(256) observe_kernel(const StepArgs a)
 }  // namespace lbm
 
 
-#define LBM_INSTANTIATE_STORAGE(ST, SUFFIX)                                                       \
-    namespace lbm {                                                                               \
-    template <int MODEL, int VEC>                                                                 \
-    static cudaError_t launch_mv_##SUFFIX(bool sample, const StepArgs &a, int blocks, int warps,  \
-                                          cudaStream_t stream)                                    \
-    {                                                                                             \
-        if (sample) step_kernel<MODEL, ST, VEC, true><<<blocks, warps * 32, 0, stream>>>(a);      \
-        else step_kernel<MODEL, ST, VEC, false><<<blocks, warps * 32, 0, stream>>>(a);            \
-        return cudaGetLastError();                                                                \
-    }                                                                                             \
-    template <int MODEL>                                                                          \
-    static cudaError_t launch_m_##SUFFIX(int vec, bool sample, const StepArgs &a, int blocks,     \
-                                         int warps, cudaStream_t stream)                          \
-    {                                                                                             \
-        switch (vec) {                                                                            \
-        case 1: return launch_mv_##SUFFIX<MODEL, 1>(sample, a, blocks, warps, stream);            \
-        case 2: return launch_mv_##SUFFIX<MODEL, 2>(sample, a, blocks, warps, stream);            \
-        case 4: return launch_mv_##SUFFIX<MODEL, 4>(sample, a, blocks, warps, stream);            \
-        case 8: return launch_mv_##SUFFIX<MODEL, 8>(sample, a, blocks, warps, stream);            \
-        default: return cudaErrorInvalidValue;                                                    \
-        }                                                                                         \
-    }                                                                                             \
-    cudaError_t launch_step_##SUFFIX(int model, int vec, bool sample, const StepArgs &a,          \
-                                     int blocks, int warps, cudaStream_t stream)                  \
-    {                                                                                             \
-        switch (model) {                                                                          \
-        case MODEL_PASSIVE: return launch_m_##SUFFIX<MODEL_PASSIVE>(vec, sample, a, blocks, warps, stream); \
-        case MODEL_MIPS: return launch_m_##SUFFIX<MODEL_MIPS>(vec, sample, a, blocks, warps, stream);       \
-        case MODEL_CIL: return launch_m_##SUFFIX<MODEL_CIL>(vec, sample, a, blocks, warps, stream);         \
-        default: return cudaErrorInvalidValue;                                                    \
-        }                                                                                         \
-    }                                                                                             \
-    cudaError_t launch_observe_##SUFFIX(int vec, const StepArgs &a, int blocks, int warps,        \
-                                        cudaStream_t stream)                                      \
-    {                                                                                             \
-        switch (vec) {                                                                            \
-        case 1: observe_kernel<ST, 1><<<blocks, warps * 32, 0, stream>>>(a); break;               \
-        case 2: observe_kernel<ST, 2><<<blocks, warps * 32, 0, stream>>>(a); break;               \
-        case 4: observe_kernel<ST, 4><<<blocks, warps * 32, 0, stream>>>(a); break;               \
-        case 8: observe_kernel<ST, 8><<<blocks, warps * 32, 0, stream>>>(a); break;               \
-        default: return cudaErrorInvalidValue;                                                    \
-        }                                                                                         \
-        return cudaGetLastError();                                                                \
-    }                                                                                             \
-    }

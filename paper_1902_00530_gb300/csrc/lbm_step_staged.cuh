@@ -1,0 +1,431 @@
+// lbm_step_staged.cuh -- the fused step with TMA-staged population rows.
+//
+// Same per-site arithmetic as step_kernel (lbm_step.cuh), different data
+// movement: each warp owns a ring of `stages` shared-memory buffers.  Buffer q
+// holds, for destination row r(q), the nine source-row segments it pulls from
+// (row r - e_y of population i), each covering the warp's 32*VEC columns plus
+// 16 bytes of halo on both sides (the periodic wrap is resolved by copying the
+// halo from the other end of the row).  The segments arrive by bulk copies
+// (cp.async.bulk, global -> shared) that complete on the buffer's mbarrier,
+// issued `stages - 1` (MIPS: `stages - 2`) rows ahead of use, so the memory
+// latency is hidden without holding the rows in registers.  Lanes read their
+// pulled values straight from shared memory, halo included: no shuffles and no
+// lane-divergent edge loads.
+//
+// Requirements (checked on the host): nx a multiple of the 16-byte halo width
+// (4 FP32 / 8 16-bit values) and at least that wide.  Every wait is bounded:
+// on expiry the warp raises DEVERR_TIMEOUT in the error word, drains its
+// copies (again bounded) and returns.
+#pragma once
+
+#include "lbm_step.cuh"
+
+namespace lbm {
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_init_fence()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// ~1 s at the GB300 clock; a healthy copy completes in microseconds.
+constexpr long long WAIT_LIMIT_CYCLES = 2000000000LL;
+
+// Warp-uniform bounded wait for one phase of a stage barrier.
+__device__ __forceinline__ bool stage_wait(uint64_t *bar, uint32_t parity)
+{
+    const long long t0 = clock64();
+    while (true) {
+        const bool ok = mbar_try_wait(bar, parity);
+        if (__all_sync(FULL, ok)) return true;
+        if (clock64() - t0 > WAIT_LIMIT_CYCLES) return false;
+    }
+}
+
+template <int ST, int VEC> struct StageGeom {
+    using T = typename Store<ST>::T;
+    static constexpr int HALO = 16 / (int)sizeof(T);        // halo width in elements (16 bytes)
+    static constexpr int W = 32 * VEC;                       // strip width
+    static constexpr int SEG = W + 2 * HALO;                 // elements per population segment
+    static constexpr int STAGE_BYTES = 9 * SEG * (int)sizeof(T);
+};
+
+// Issue the nine segment copies of destination row y into stage buffer `buf`
+// and arm its barrier (lanes 0..26 issue one copy each; lane 0 arms).
+template <int ST, int VEC>
+__device__ __forceinline__ void issue_row(typename Store<ST>::T *buf, uint64_t *bar,
+                                          const typename Store<ST>::T *src, size_t plane, int pitch,
+                                          int nx, int ny, int xs, int xe, int y, int lane)
+{
+    using G = StageGeom<ST, VEC>;
+    using T = typename Store<ST>::T;
+    const uint32_t main_bytes = (uint32_t)(xe - xs) * (uint32_t)sizeof(T);
+    __syncwarp();  // every lane has finished reading this buffer's previous row
+    if (lane == 0) mbar_arrive_expect_tx(bar, 9u * (main_bytes + 32u));
+    __syncwarp();
+    if (lane < 27) {
+        fence_proxy_async_smem();  // order those reads before the copy's writes
+        const int i = lane / 3, part = lane % 3;
+        const int dy = (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+        const int r = wrap_once(y - dy, ny);
+        const T *row = src + (size_t)i * plane + (size_t)r * pitch;
+        T *seg = buf + i * G::SEG;
+        if (part == 0) {  // left halo: columns xs-HALO .. xs-1 (periodic)
+            const int c = xs == 0 ? nx - G::HALO : xs - G::HALO;
+            bulk_copy_g2s(seg, row + c, 16u, bar);
+        } else if (part == 1) {  // the strip itself
+            bulk_copy_g2s(seg + G::HALO, row + xs, main_bytes, bar);
+        } else {  // right halo: columns xe .. xe+HALO-1 (periodic)
+            const int c = xe >= nx ? 0 : xe;
+            bulk_copy_g2s(seg + G::HALO + (xe - xs), row + c, 16u, bar);
+        }
+    }
+}
+
+// Pulled values of population I for this lane's VEC sites, from the stage:
+// f_I(x0 + j - e_x), read at shared index b + j - e_x.
+template <int ST, int VEC, int I>
+__device__ __forceinline__ void stage_pop(const typename Store<ST>::T *seg, int b, float shift, float out[VEC])
+{
+    float a[VEC];
+    load_vec_plain<ST, VEC>(seg + b, shift, a);
+    if constexpr (vx(I) == 0) {
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) out[j] = a[j];
+    } else if constexpr (vx(I) == 1) {
+        out[0] = Store<ST>::get(seg[b - 1], shift);
+#pragma unroll
+        for (int j = 1; j < VEC; ++j) out[j] = a[j - 1];
+    } else {
+#pragma unroll
+        for (int j = 0; j < VEC - 1; ++j) out[j] = a[j + 1];
+        out[VEC - 1] = Store<ST>::get(seg[b + VEC], shift);
+    }
+}
+
+template <int ST, int VEC>
+__device__ __forceinline__ void stage_row(const typename Store<ST>::T *buf, int b, float rho0, float f[9][VEC])
+{
+    using G = StageGeom<ST, VEC>;
+    stage_pop<ST, VEC, 0>(buf + 0 * G::SEG, b, wq(0) * rho0, f[0]);
+    stage_pop<ST, VEC, 1>(buf + 1 * G::SEG, b, wq(1) * rho0, f[1]);
+    stage_pop<ST, VEC, 2>(buf + 2 * G::SEG, b, wq(2) * rho0, f[2]);
+    stage_pop<ST, VEC, 3>(buf + 3 * G::SEG, b, wq(3) * rho0, f[3]);
+    stage_pop<ST, VEC, 4>(buf + 4 * G::SEG, b, wq(4) * rho0, f[4]);
+    stage_pop<ST, VEC, 5>(buf + 5 * G::SEG, b, wq(5) * rho0, f[5]);
+    stage_pop<ST, VEC, 6>(buf + 6 * G::SEG, b, wq(6) * rho0, f[6]);
+    stage_pop<ST, VEC, 7>(buf + 7 * G::SEG, b, wq(7) * rho0, f[7]);
+    stage_pop<ST, VEC, 8>(buf + 8 * G::SEG, b, wq(8) * rho0, f[8]);
+}
+
+// Post-stream density at shared index c (one site) of a staged row.
+template <int ST, int VEC>
+__device__ __forceinline__ float stage_density_at(const typename Store<ST>::T *buf, int c, float rho0)
+{
+    using G = StageGeom<ST, VEC>;
+    float v[9][1];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) v[i][0] = Store<ST>::get(buf[i * G::SEG + c - vx(i)], wq(i) * rho0);
+    return density<1>(v, 0);
+}
+
+// Density window of a staged row: r[0] at x0-1, r[1..VEC] the lane's sites,
+// r[VEC+1] at x0+VEC.  Neighbours inside the warp come by shuffle; lane 0's
+// left and every lane's right neighbour are summed from shared memory.
+template <int ST, int VEC>
+__device__ __forceinline__ void stage_density_window(const typename Store<ST>::T *buf, int b, float rho0,
+                                                     int lane, float r[VEC + 2])
+{
+    float f[9][VEC];
+    stage_row<ST, VEC>(buf, b, rho0, f);
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) r[j + 1] = density<VEC>(f, j);
+    const float right = stage_density_at<ST, VEC>(buf, b + VEC, rho0);
+    float left = __shfl_up_sync(FULL, r[VEC], 1);
+    if (lane == 0) left = stage_density_at<ST, VEC>(buf, b - 1, rho0);
+    r[0] = left;
+    r[VEC + 1] = right;
+}
+
+template <int MODEL, int ST, int VEC, bool SAMPLE>
+__global__ void __launch_bounds__(256) step_staged_kernel(const StepArgs a)
+{
+    using T = typename Store<ST>::T;
+    using G = StageGeom<ST, VEC>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int S = a.stages;
+    // per-warp carve-out: S stage buffers, then S barriers
+    T *ring = reinterpret_cast<T *>(smem_raw + (size_t)warp * S * G::STAGE_BYTES);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw + (size_t)(blockDim.x >> 5) * S * G::STAGE_BYTES) +
+                     warp * S;
+
+    const LatDesc *dp = a.desc + find_lattice(a.desc, a.nlat, blockIdx.x);
+    const int nsx = dp->nsx, nsy = dp->nsy;
+    const int s = (blockIdx.x - dp->block_begin) * (blockDim.x >> 5) + warp;
+    if (s >= nsx * nsy) return;  // whole warp leaves together; its barriers are never used
+    const int nx = dp->nx, ny = dp->ny, pitch = dp->pitch, rows = dp->rows;
+    const SiteParams d = load_params(dp);
+    const int sx = s % nsx, sy = s / nsx;
+    const int xs = sx * G::W, xe = min(xs + G::W, nx);
+    const int x0 = xs + lane * VEC;
+    const bool valid = x0 < nx;
+    const int b = G::HALO + lane * VEC;  // shared index of x0 within a segment
+    const int y_begin = sy * rows, y_end = min(y_begin + rows, ny);
+    const size_t plane = (size_t)ny * pitch;
+    const T *src = reinterpret_cast<const T *>(dp->f[a.src]);
+    T *dst = reinterpret_cast<T *>(dp->f[a.src ^ 1]);
+    const float rho0 = dp->rho0;
+    const uint32_t id = (uint32_t)dp->id;
+    const uint32_t t = *a.t_ptr + a.k;
+    const bool noise = d.sigma_q > 0.f;
+
+    if (lane == 0) {
+        for (int k = 0; k < S; ++k) mbar_init(&bars[k], 1);
+        mbar_init_fence();
+    }
+    __syncwarp();
+
+    // rows in order of use: MIPS also needs y_begin-1 and y_end (density halo)
+    constexpr bool MIPS = (MODEL == MODEL_MIPS);
+    const int q_first_row = MIPS ? y_begin - 1 : y_begin;
+    const int nq = (y_end - y_begin) + (MIPS ? 2 : 0);
+    int issued = 0;
+    auto issue_next = [&]() {
+        if (issued < nq) {
+            const int k = issued % S;
+            issue_row<ST, VEC>(ring + (size_t)k * (G::STAGE_BYTES / sizeof(T)), &bars[k], src, plane, pitch, nx, ny,
+                               xs, xe, wrap_once(q_first_row + issued, ny), lane);
+            ++issued;
+        }
+    };
+    for (int k = 0; k < S; ++k) issue_next();
+
+    auto stage_ptr = [&](int q) { return ring + (size_t)(q % S) * (G::STAGE_BYTES / sizeof(T)); };
+    bool ok = true;
+    auto wait_q = [&](int q) {
+        if (ok && !stage_wait(&bars[q % S], (uint32_t)((q / S) & 1))) {
+            ok = false;
+            if (lane == 0) atomicOr(a.err, (unsigned)DEVERR_TIMEOUT);
+        }
+        return ok;
+    };
+
+    double col[VEC], acc[5];
+    if constexpr (SAMPLE) {
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) col[j] = 0.0;
+#pragma unroll
+        for (int q = 0; q < 5; ++q) acc[q] = 0.0;
+    }
+
+    float rm[VEC + 2], rc[VEC + 2], rn[VEC + 2];
+    int q = 0;  // next stage to consume
+    if constexpr (MIPS) {
+        if (wait_q(0)) stage_density_window<ST, VEC>(stage_ptr(0), b, rho0, lane, rm);
+        issue_next();
+        q = 1;
+        if (wait_q(1)) stage_density_window<ST, VEC>(stage_ptr(1), b, rho0, lane, rc);
+    }
+
+    for (int y = y_begin; y < y_end && ok; ++y) {
+        const int qc = q;  // stage of row y
+        float f[9][VEC];
+        if constexpr (MIPS) {
+            if (!wait_q(qc + 1)) break;
+            stage_density_window<ST, VEC>(stage_ptr(qc + 1), b, rho0, lane, rn);
+        } else {
+            if (!wait_q(qc)) break;
+        }
+        stage_row<ST, VEC>(stage_ptr(qc), b, rho0, f);
+        issue_next();  // refills this row's buffer (issue_row syncs the warp first)
+        q = qc + 1;
+
+        float out[9][VEC];
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) {
+            float g[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) g[i] = f[i][j];
+            float gx = 0.f, gy = 0.f;
+            if constexpr (MIPS) {
+                const float e = rc[j + 2], w = rc[j];
+                const float ne = rn[j + 2], nw = rn[j], se = rm[j + 2], sw = rm[j];
+                gx = (1.f / 3.f) * (e - w) + (1.f / 12.f) * ((ne + se) - (nw + sw));
+                gy = (1.f / 3.f) * (rn[j + 1] - rm[j + 1]) + (1.f / 12.f) * ((ne + nw) - (se + sw));
+            }
+            int kn[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+            if (noise && valid) noise_ints((uint32_t)(x0 + j), (uint32_t)y, t, id, a.key0, a.key1, kn);
+            collide_site<MODEL>(g, gx, gy, d, noise, kn);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) out[i][j] = g[i];
+        }
+        if (valid) {
+#pragma unroll
+            for (int i = 0; i < 9; ++i)
+                store_vec<ST, VEC>(dst + i * plane + (size_t)y * pitch + x0, wq(i) * rho0, out[i]);
+        }
+        if constexpr (SAMPLE) {
+            float g[9][VEC];
+#pragma unroll
+            for (int i = 0; i < 9; ++i)
+#pragma unroll
+                for (int j = 0; j < VEC; ++j)
+                    g[i][j] = Store<ST>::get(Store<ST>::put(out[i][j], wq(i) * rho0), wq(i) * rho0);
+            observe_row<VEC>(g, valid, col, acc, dp->rowp + (size_t)sx * ny + y, lane);
+        }
+        if constexpr (MIPS) {
+#pragma unroll
+            for (int j = 0; j < VEC + 2; ++j) {
+                rm[j] = rc[j];
+                rc[j] = rn[j];
+            }
+        }
+    }
+    if (!ok) {
+        // drain the copies still in flight (bounded) before the warp exits
+        for (int qq = q; qq < issued; ++qq) (void)stage_wait(&bars[qq % S], (uint32_t)((qq / S) & 1));
+        return;
+    }
+    // MIPS consumed its halo rows; make sure nothing is left in flight
+    for (int qq = q + (MIPS ? 1 : 0); qq < issued; ++qq) (void)stage_wait(&bars[qq % S], (uint32_t)((qq / S) & 1));
+    if constexpr (SAMPLE) observe_flush<VEC>(dp->colp, dp->scal, nx, s, sy, x0, valid, col, acc, lane);
+}
+
+template <int ST, int VEC>
+constexpr int staged_stage_bytes()
+{
+    return StageGeom<ST, VEC>::STAGE_BYTES;
+}
+
+}  // namespace lbm
+
+// ---------------------------------------------------------------------------
+// Launchers (instantiated once per storage type by LBM_INSTANTIATE_STORAGE).
+// ---------------------------------------------------------------------------
+namespace lbm {
+
+template <int MODEL, int ST, int VEC, bool SAMPLE>
+static cudaError_t launch_one_staged(const StepArgs &a, int blocks, int warps, cudaStream_t stream)
+{
+    const size_t bytes = (size_t)warps * a.stages * (StageGeom<ST, VEC>::STAGE_BYTES + sizeof(uint64_t));
+    auto kern = step_staged_kernel<MODEL, ST, VEC, SAMPLE>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    kern<<<blocks, warps * 32, bytes, stream>>>(a);
+    return cudaGetLastError();
+}
+
+template <int MODEL, int ST, int VEC>
+static cudaError_t launch_mv(int kind, bool sample, const StepArgs &a, int blocks, int warps, cudaStream_t stream)
+{
+    if (kind == 1) {
+        if (sample) return launch_one_staged<MODEL, ST, VEC, true>(a, blocks, warps, stream);
+        return launch_one_staged<MODEL, ST, VEC, false>(a, blocks, warps, stream);
+    }
+    if (sample) step_kernel<MODEL, ST, VEC, true><<<blocks, warps * 32, 0, stream>>>(a);
+    else step_kernel<MODEL, ST, VEC, false><<<blocks, warps * 32, 0, stream>>>(a);
+    return cudaGetLastError();
+}
+
+template <int MODEL, int ST>
+static cudaError_t launch_m(int kind, int vec, bool sample, const StepArgs &a, int blocks, int warps,
+                            cudaStream_t stream)
+{
+    switch (vec) {
+    case 1: return launch_mv<MODEL, ST, 1>(kind, sample, a, blocks, warps, stream);
+    case 2: return launch_mv<MODEL, ST, 2>(kind, sample, a, blocks, warps, stream);
+    case 4: return launch_mv<MODEL, ST, 4>(kind, sample, a, blocks, warps, stream);
+    case 8:
+        if constexpr (ST != ST_F32) return launch_mv<MODEL, ST, 8>(kind, sample, a, blocks, warps, stream);
+        return cudaErrorInvalidValue;
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int ST>
+static cudaError_t launch_step_storage(int model, int kind, int vec, bool sample, const StepArgs &a, int blocks,
+                                       int warps, cudaStream_t stream)
+{
+    switch (model) {
+    case MODEL_PASSIVE: return launch_m<MODEL_PASSIVE, ST>(kind, vec, sample, a, blocks, warps, stream);
+    case MODEL_MIPS: return launch_m<MODEL_MIPS, ST>(kind, vec, sample, a, blocks, warps, stream);
+    case MODEL_CIL: return launch_m<MODEL_CIL, ST>(kind, vec, sample, a, blocks, warps, stream);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int ST>
+static cudaError_t launch_observe_storage(int vec, const StepArgs &a, int blocks, int warps, cudaStream_t stream)
+{
+    switch (vec) {
+    case 1: observe_kernel<ST, 1><<<blocks, warps * 32, 0, stream>>>(a); break;
+    case 2: observe_kernel<ST, 2><<<blocks, warps * 32, 0, stream>>>(a); break;
+    case 4: observe_kernel<ST, 4><<<blocks, warps * 32, 0, stream>>>(a); break;
+    case 8:
+        if constexpr (ST != ST_F32) {
+            observe_kernel<ST, 8><<<blocks, warps * 32, 0, stream>>>(a);
+            break;
+        }
+        return cudaErrorInvalidValue;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace lbm
+
+#define LBM_INSTANTIATE_STORAGE(ST, SUFFIX)                                                                  \
+    namespace lbm {                                                                                          \
+    cudaError_t launch_step_##SUFFIX(int model, int kind, int vec, bool sample, const StepArgs &a, int blocks, \
+                                     int warps, cudaStream_t stream)                                         \
+    {                                                                                                        \
+        return launch_step_storage<ST>(model, kind, vec, sample, a, blocks, warps, stream);                   \
+    }                                                                                                        \
+    cudaError_t launch_observe_##SUFFIX(int vec, const StepArgs &a, int blocks, int warps,                    \
+                                        cudaStream_t stream)                                                 \
+    {                                                                                                        \
+        return launch_observe_storage<ST>(vec, a, blocks, warps, stream);                                     \
+    }                                                                                                        \
+    }

@@ -77,14 +77,16 @@ def test_host_only_calls_and_status_codes(lib):
     assert lib.lbm_step(ctx, 1) == 2                      # not bound
     assert b"bound" in lib.lbm_last_error(ctx)
     assert lib.lbm_observables(ctx, 0, None) == 2
-    assert lib.lbm_set_tuning(ctx, 1, 4, 32, 4) == 1      # 4 does not divide 37
-    assert lib.lbm_set_tuning(ctx, 1, 1, 8, 4) == 1       # rows below 16
-    assert lib.lbm_set_tuning(ctx, 1, 1, 32, 9) == 1      # too many warps
-    assert lib.lbm_set_tuning(ctx, 1, 1, 32, 2) == 0
-    v, r, w = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
-    assert lib.lbm_get_tuning(ctx, 0, ctypes.byref(v), ctypes.byref(r), ctypes.byref(w)) == 0
-    assert (v.value, r.value, w.value) == (1, 32, 2)
-    assert lib.lbm_get_tuning(ctx, 1, ctypes.byref(v), ctypes.byref(r), ctypes.byref(w)) == 1
+    assert lib.lbm_set_tuning(ctx, 1, 4, 32, 4, 0) == 1   # 4 does not divide 37
+    assert lib.lbm_set_tuning(ctx, 1, 1, 8, 4, 0) == 1    # rows below 16
+    assert lib.lbm_set_tuning(ctx, 1, 1, 32, 9, 0) == 1   # too many warps
+    assert lib.lbm_set_tuning(ctx, 1, 1, 32, 2, 3) == 1   # staged needs nx % 4 == 0 (37)
+    assert lib.lbm_set_tuning(ctx, 1, 1, 32, 2, 0) == 0
+    v, r, w, s = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    args = [ctypes.byref(x) for x in (v, r, w, s)]
+    assert lib.lbm_get_tuning(ctx, 0, *args) == 0
+    assert (v.value, r.value, w.value, s.value) == (1, 32, 2, 0)
+    assert lib.lbm_get_tuning(ctx, 1, *args) == 1
     t = ctypes.c_int64(-1)
     assert lib.lbm_get_time(ctx, ctypes.byref(t)) == 0 and t.value == 0
     assert lib.lbm_bind(ctx, None, None, None) == 1
