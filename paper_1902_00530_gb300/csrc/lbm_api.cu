@@ -302,6 +302,10 @@ cudaError_t launch_group_step(const lbm_ctx *c, const GroupHost &g, int src, uin
     a.key1 = (uint32_t)(c->seed >> 32);
     a.stages = g.stages;
     a.err = err_dev(c);
+    for (int r = 0; r < 10; ++r) {  // Philox round keys (Weyl increments, Salmon et al. 2011)
+        a.rk[2 * r] = a.key0 + (uint32_t)r * 0x9E3779B9u;
+        a.rk[2 * r + 1] = a.key1 + (uint32_t)r * 0xBB67AE85u;
+    }
     const int kind = g.stages > 0 ? 1 : 0;
     if (g.storage == LBM_F32)
         return launch_step_f32(g.model, kind, g.vec, sample, a, g.blocks, g.warps, c->stream);
@@ -321,6 +325,7 @@ cudaError_t launch_group_observe(const lbm_ctx *c, const GroupHost &g, int src)
     a.key0 = a.key1 = 0;
     a.stages = 0;
     a.err = err_dev(c);
+    for (int r = 0; r < 20; ++r) a.rk[r] = 0;
     if (g.storage == LBM_F32) return launch_observe_f32(g.vec, a, g.blocks, g.warps, c->stream);
     if (g.storage == LBM_F16_SHIFTED) return launch_observe_f16(g.vec, a, g.blocks, g.warps, c->stream);
     return launch_observe_bf16(g.vec, a, g.blocks, g.warps, c->stream);

@@ -75,6 +75,7 @@ struct StepArgs {
     uint32_t key0, key1;  // Philox key = seed
     int stages;           // staged kernel: shared-memory row buffers per warp
     unsigned *err;        // device error word (bounded waits report here)
+    uint32_t rk[20];      // Philox round keys: (key0 + r W0, key1 + r W1), r = 0..9
 };
 
 // ---------------------------------------------------------------------------
@@ -87,13 +88,24 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
 {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        const uint32_t lo0 = 0xD2511F53u * c.x;
-        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
-        const uint32_t lo1 = 0xCD9E8D57u * c.z;
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
-        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        const unsigned long long p0 = (unsigned long long)c.x * 0xD2511F53u;
+        const unsigned long long p1 = (unsigned long long)c.z * 0xCD9E8D57u;
+        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k0, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ k1, (uint32_t)p0);
         k0 += 0x9E3779B9u;
         k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// The same with the ten round keys precomputed (rk[2r], rk[2r+1]).
+__device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const uint32_t *rk)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const unsigned long long p0 = (unsigned long long)c.x * 0xD2511F53u;
+        const unsigned long long p1 = (unsigned long long)c.z * 0xCD9E8D57u;
+        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ rk[2 * r], (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ rk[2 * r + 1],
+                       (uint32_t)p0);
     }
     return c;
 }
@@ -102,11 +114,11 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
 // collision noise.  The nine variates are k_i = 2 m_i + 1 - 2^24 with m_i the
 // top 24 bits of words 0..7 of two calls and, for i = 8, the low bytes of
 // words 0, 1, 2.  eta~_i = sigma 2^-24 k_i is uniform on [-sigma, sigma].
-__device__ __forceinline__ void noise_ints(uint32_t x, uint32_t y, uint32_t t, uint32_t id,
-                                           uint32_t key0, uint32_t key1, int k[9])
+__device__ __forceinline__ void noise_ints(uint32_t x, uint32_t y, uint32_t t, uint32_t id, const uint32_t *rk,
+                                           int k[9])
 {
-    const uint4 a = philox4x32_10(make_uint4(x, y, t, id & 0xFFFFFFu), key0, key1);
-    const uint4 b = philox4x32_10(make_uint4(x, y, t, (id & 0xFFFFFFu) | (1u << 28)), key0, key1);
+    const uint4 a = philox4x32_10_rk(make_uint4(x, y, t, id & 0xFFFFFFu), rk);
+    const uint4 b = philox4x32_10_rk(make_uint4(x, y, t, (id & 0xFFFFFFu) | (1u << 28)), rk);
     const uint32_t w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
 #pragma unroll
     for (int i = 0; i < 8; ++i) k[i] = (int)((w[i] >> 8) << 1) + 1 - (1 << 24);

@@ -163,7 +163,7 @@ __device__ __forceinline__ void collide_site(float f[9], float gx, float gy, con
         sy = c * gy;
         const float m2 = sx * sx + sy * sy;
         if (m2 > d.u_max2) {
-            const float sc = d.u_max / sqrtf(m2);
+            const float sc = d.u_max * rsqrtf(m2);
             sx *= sc;
             sy *= sc;
         }
@@ -171,9 +171,9 @@ __device__ __forceinline__ void collide_site(float f[9], float gx, float gy, con
         // Eqs. (bu_CIL), (U0): U0(rho) u/|u|, U0 = max(B - A rho^2, 0)
         const float ar2 = d.A * rho * rho;
         const float U0 = d.B >= ar2 ? d.B - ar2 : 0.f;
-        const float m = sqrtf(ux * ux + uy * uy);
-        if (m > 0.f) {
-            const float sc = U0 / m;
+        const float m2 = ux * ux + uy * uy;
+        if (m2 > 0.f) {
+            const float sc = U0 * rsqrtf(m2);
             sx = ux * sc;
             sy = uy * sc;
         } else {
@@ -215,10 +215,13 @@ __device__ __forceinline__ void collide_site(float f[9], float gx, float gy, con
 #pragma unroll
         for (int i = 0; i < 9; ++i) f[i] += fmaf((float)kn[i], d.sigma_q, -mean);
     }
-    // step 6: negative correction (App. A.3)
-    float mn = fminf(fminf(fminf(f[0], f[1]), fminf(f[2], f[3])),
-                     fminf(fminf(f[4], f[5]), fminf(fminf(f[6], f[7]), f[8])));
-    if (mn < 0.f) {
+    // step 6: negative correction (App. A.3); a set sign bit flags a candidate
+    const unsigned sg = (__float_as_uint(f[0]) | __float_as_uint(f[1]) | __float_as_uint(f[2])) |
+                        (__float_as_uint(f[3]) | __float_as_uint(f[4]) | __float_as_uint(f[5])) |
+                        (__float_as_uint(f[6]) | __float_as_uint(f[7]) | __float_as_uint(f[8]));
+    if ((sg & 0x80000000u) &&
+        fminf(fminf(fminf(f[0], f[1]), fminf(f[2], f[3])), fminf(fminf(f[4], f[5]), fminf(fminf(f[6], f[7]), f[8]))) <
+            0.f) {
         if (f[0] < 0.f) f[0] = 0.f;
 #pragma unroll
         for (int i = 1; i < 9; ++i) {
@@ -228,7 +231,7 @@ __device__ __forceinline__ void collide_site(float f[9], float gx, float gy, con
             }
         }
         const float s = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
-        const float sc = rho / s;
+        const float sc = rho * __frcp_rn(s);
 #pragma unroll
         for (int i = 0; i < 9; ++i) f[i] *= sc;
     }
@@ -365,7 +368,7 @@ __global__ void __launch_bounds__(256) step_kernel(const StepArgs a)
                 gy = (1.f / 3.f) * (rn[j + 1] - rm[j + 1]) + (1.f / 12.f) * ((ne + nw) - (se + sw));
             }
             int kn[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-            if (noise && valid) noise_ints((uint32_t)(x0 + j), (uint32_t)y, t, id, a.key0, a.key1, kn);
+            if (noise && valid) noise_ints((uint32_t)(x0 + j), (uint32_t)y, t, id, a.rk, kn);
             collide_site<MODEL>(f, gx, gy, d, noise, kn);
 #pragma unroll
             for (int i = 0; i < 9; ++i) out[i][j] = f[i];

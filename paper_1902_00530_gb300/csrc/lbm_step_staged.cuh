@@ -296,7 +296,7 @@ __global__ void __launch_bounds__(256) step_staged_kernel(const StepArgs a)
                 gy = (1.f / 3.f) * (rn[j + 1] - rm[j + 1]) + (1.f / 12.f) * ((ne + nw) - (se + sw));
             }
             int kn[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-            if (noise && valid) noise_ints((uint32_t)(x0 + j), (uint32_t)y, t, id, a.key0, a.key1, kn);
+            if (noise && valid) noise_ints((uint32_t)(x0 + j), (uint32_t)y, t, id, a.rk, kn);
             collide_site<MODEL>(g, gx, gy, d, noise, kn);
 #pragma unroll
             for (int i = 0; i < 9; ++i) out[i][j] = g[i];
