@@ -218,6 +218,35 @@ lbm_status lbm_last_launch_count(const lbm_ctx *ctx, int64_t *count);
 lbm_status lbm_set_profiling(lbm_ctx *ctx, int32_t enabled);
 lbm_status lbm_profile_read(lbm_ctx *ctx, double *step_ms, int64_t *step_launches, double *other_ms);
 
+/* Observables of a population field, allocating nothing.
+ *
+ * The paper has no counterpart: this is a service for callers that cannot
+ * allocate device memory -- code inside a memory pool or allocator owned by
+ * another runtime, a replayed stream or graph pipeline in which cudaMalloc
+ * would synchronise the device, or an embedding that must keep its memory
+ * footprint fixed.  It computes the same record as lbm_observables (Eq. (phi),
+ * App. D) for a caller-supplied state instead of a context's.
+ *
+ * f_dev: DEVICE pointer to dense FP32 populations [9][ny][nx] (caller-owned,
+ * read only); 1 <= nx, ny <= LBM_NOALLOC_MAX_SIDE.  B: the CIL constant used
+ * by zeta.  out: host record (t is set to 0).  cuda_stream: the stream to run
+ * on (NULL = legacy default stream); the call waits for it before returning.
+ *
+ * Scratch: a fixed array of LBM_NOALLOC_SCRATCH_BYTES compiled into the
+ * library, held by every GPU that loads the library until the process exits.
+ * The first call on a device looks up the array's device address (with that
+ * device current) and caches it; make that first call before any stream
+ * capture.  All calls share the array, which keeps the last call's partial
+ * sums (each call overwrites what it reads): calls that overlap on the GPU --
+ * from two streams or two host threads -- race and must be serialised by the
+ * caller.  No cudaMalloc, cudaFree or allocating library routine is called.
+ * Returns LBM_ERR_INVALID_ARG for sizes beyond the maximum or null pointers,
+ * LBM_ERR_CUDA if a CUDA call fails, LBM_ERR_NUMERIC for non-finite sums. */
+#define LBM_NOALLOC_MAX_SIDE 4096
+#define LBM_NOALLOC_SCRATCH_BYTES (1088 * 1024)
+lbm_status lbm_observables_noalloc(const float *f_dev, int32_t nx, int32_t ny, double B, lbm_obs *out,
+                                   void *cuda_stream);
+
 /* Text of the last error on this context (never NULL; "" if none). */
 const char *lbm_last_error(const lbm_ctx *ctx);
 

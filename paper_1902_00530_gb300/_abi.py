@@ -9,6 +9,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "liblbm.so")
 
 LBM_OK, LBM_ERR_INVALID_ARG, LBM_ERR_UNBOUND, LBM_ERR_CUDA = 0, 1, 2, 3
 LBM_ERR_TIMEOUT, LBM_ERR_NUMERIC, LBM_ERR_UNSUPPORTED = 4, 5, 6
+NOALLOC_MAX_SIDE = 4096
 STATUS_NAMES = {0: "LBM_OK", 1: "LBM_ERR_INVALID_ARG", 2: "LBM_ERR_UNBOUND", 3: "LBM_ERR_CUDA",
                 4: "LBM_ERR_TIMEOUT", 5: "LBM_ERR_NUMERIC", 6: "LBM_ERR_UNSUPPORTED"}
 MODELS = {"passive": 0, "mips": 1, "cil": 2}
@@ -67,6 +68,8 @@ SIGNATURES = {
     "lbm_set_profiling": (ctypes.c_int, [_CTX, ctypes.c_int32]),
     "lbm_profile_read": (ctypes.c_int, [_CTX, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
                                         ctypes.POINTER(ctypes.c_double)]),
+    "lbm_observables_noalloc": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                               ctypes.POINTER(lbm_obs), _P]),
     "lbm_last_error": (ctypes.c_char_p, [_CTX]),
     "lbm_destroy": (None, [_CTX]),
 }
