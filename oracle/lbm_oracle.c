@@ -105,23 +105,29 @@ static void draw(uint64_t seed, uint32_t x, uint32_t y, uint32_t t, uint32_t id,
     orc_philox4x32_10(ctr, key, out);
 }
 
-/* The nine noise variates s_i in (-1, 1) of one site and step: two Philox calls
- * give eight words; s_i for i < 8 uses the top 24 bits of word i, s_8 the low
- * bytes of words 0, 1, 2.  s = (2m + 1 - 2^24) / 2^24 with m the 24-bit
- * integer: an odd multiple of 2^-24, exact in FP32 and FP64, symmetric
- * about 0, so eta~_i = sigma * s_i is uniform on [-sigma, sigma] (Sec. 2,
- * below Eq. (noiseDensityConservation)) to 24 bits. */
+/* The nine noise variates s_i in (-1, 1) of one site and step, from one
+ * Philox call (call index 0): split the four words into eight 16-bit halves
+ * h_0..h_7 (h_2j = low half of word j, h_2j+1 = high half); variate i < 8
+ * takes the top 14 bits of h_i, variate 8 the low 2 bits of h_0..h_6 (h_0's
+ * lowest).  s = (2m + 1 - 2^14) / 2^14 for the 14-bit integer m: an odd
+ * multiple of 2^-14, exact in FP32 and FP64 and symmetric about 0, so
+ * eta~_i = sigma * s_i is uniform on [-sigma, sigma] (Sec. 2, below Eq.
+ * (noiseDensityConservation)) to 14 bits. */
 void orc_noise_variates(uint64_t seed, uint32_t x, uint32_t y, uint32_t t, uint32_t id,
                         double s[Q])
 {
-    uint32_t w[8];
+    uint32_t w[4];
     draw(seed, x, y, t, id, 0u, 0u, w);
-    draw(seed, x, y, t, id, 0u, 1u, w + 4);
+    uint32_t h[8];
+    for (int j = 0; j < 4; ++j) {
+        h[2 * j] = w[j] & 0xFFFFu;
+        h[2 * j + 1] = w[j] >> 16;
+    }
     uint32_t m[Q];
-    for (int i = 0; i < 8; ++i) m[i] = w[i] >> 8;
-    m[8] = (w[0] & 0xFFu) | ((w[1] & 0xFFu) << 8) | ((w[2] & 0xFFu) << 16);
-    for (int i = 0; i < Q; ++i)
-        s[i] = ((double)(2.0 * (double)m[i] + 1.0) - 16777216.0) / 16777216.0;
+    for (int i = 0; i < 8; ++i) m[i] = h[i] >> 2;
+    m[8] = 0;
+    for (int i = 0; i < 7; ++i) m[8] |= (h[i] & 3u) << (2 * i);
+    for (int i = 0; i < Q; ++i) s[i] = (2.0 * (double)m[i] + 1.0 - 16384.0) / 16384.0;
 }
 
 /* Four uniforms U_j in (0, 1) for the initial state of a site:

@@ -237,7 +237,7 @@ LatDesc make_desc(const lbm_ctx *c, const LatHost &L, int block_begin, const Gro
     const long long nstrip = (long long)d.nsx * d.nsy;
     d.nchunk = std::min(L.nchunk_max, std::max(1, ceil_div(std::max<long long>({L.lat.nx, L.lat.ny, nstrip}), CHUNK_COLS)));
     d.omega = (float)(1.0 / L.p.tau);
-    d.sigma_q = (float)(L.p.sigma / 16777216.0);
+    d.sigma_q = (float)(2.0 * L.p.sigma);
     d.C = (float)L.p.C;
     d.rho_star = (float)L.p.rho_star;
     d.inv_rho_star = L.p.rho_star > 0 ? (float)(1.0 / L.p.rho_star) : 0.f;

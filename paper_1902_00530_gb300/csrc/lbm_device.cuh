@@ -61,7 +61,7 @@ struct LatDesc {
     int nsx, nsy, rows, block_begin;
     int ring_cap, nchunk, pad0, pad1;
     float omega;         // 1/tau
-    float sigma_q;       // sigma * 2^-24 (noise scale of one 24-bit step)
+    float sigma_q;       // 2 sigma: noise scale of u in [1, 2) (0 = no noise)
     float C, inv_rho_star, rho_star, u_max, u_max2, A, B;
     float rho0;          // storage shift
 };
@@ -110,20 +110,38 @@ __device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const uint32_t *rk)
     return c;
 }
 
-// Noise counter: (x, y, t, id | purpose << 24 | call << 28); purpose 0 =
-// collision noise.  The nine variates are k_i = 2 m_i + 1 - 2^24 with m_i the
-// top 24 bits of words 0..7 of two calls and, for i = 8, the low bytes of
-// words 0, 1, 2.  eta~_i = sigma 2^-24 k_i is uniform on [-sigma, sigma].
-__device__ __forceinline__ void noise_ints(uint32_t x, uint32_t y, uint32_t t, uint32_t id, const uint32_t *rk,
-                                           int k[9])
+// Noise counter: (x, y, t, id | purpose << 24 | call << 28), purpose 0 and
+// call 0 for the collision noise.  One Philox call gives 128 bits: the eight
+// 16-bit halves h_0..h_7 (h_2j = low half of word j) each give a 14-bit
+// integer m_i = h_i >> 2 (i < 8), and m_8 gathers the low 2 bits of h_0..h_6
+// (h_0's lowest).  The variate s_i = (2 m_i + 1 - 2^14) 2^-14 is built without
+// an integer conversion: u_i = 1 + (m_i + 1/2) 2^-14 is assembled directly as
+// FP32 bits (exponent of 1, m_i in the top 14 mantissa bits, then a 1), and
+// s_i = 2 u_i - 3 exactly.  The zero-sum noise eta_i = sigma (s_i - mean s)
+// = 2 sigma (u_i - mean u) is returned in eta[].
+__device__ __forceinline__ float u_from_bits(uint32_t mantissa14_at_bit9)
+{
+    return __uint_as_float(0x3F800100u | mantissa14_at_bit9);
+}
+
+__device__ __forceinline__ void noise_eta(uint32_t x, uint32_t y, uint32_t t, uint32_t id, const uint32_t *rk,
+                                          float two_sigma, float eta[9])
 {
     const uint4 a = philox4x32_10_rk(make_uint4(x, y, t, id & 0xFFFFFFu), rk);
-    const uint4 b = philox4x32_10_rk(make_uint4(x, y, t, (id & 0xFFFFFFu) | (1u << 28)), rk);
-    const uint32_t w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+    const uint32_t w[4] = {a.x, a.y, a.z, a.w};
+    float u[9];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) k[i] = (int)((w[i] >> 8) << 1) + 1 - (1 << 24);
-    const uint32_t m8 = (a.x & 0xFFu) | ((a.y & 0xFFu) << 8) | ((a.z & 0xFFu) << 16);
-    k[8] = (int)(m8 << 1) + 1 - (1 << 24);
+    for (int j = 0; j < 4; ++j) {
+        u[2 * j] = u_from_bits((w[j] << 7) & 0x007FFE00u);      // low half: bits 2..15 -> 9..22
+        u[2 * j + 1] = u_from_bits((w[j] >> 9) & 0x007FFE00u);  // high half: bits 18..31 -> 9..22
+    }
+    const uint32_t m8 = (w[0] & 3u) | ((w[0] >> 14) & 0xCu) | ((w[1] & 3u) << 4) | ((w[1] >> 10) & 0xC0u) |
+                        ((w[2] & 3u) << 8) | ((w[2] >> 6) & 0xC00u) | ((w[3] & 3u) << 12);
+    u[8] = u_from_bits(m8 << 9);
+    const float su = ((u[0] + u[1]) + (u[2] + u[3])) + ((u[4] + u[5]) + (u[6] + u[7])) + u[8];  // exact
+    const float mean = su * (1.f / 9.f);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) eta[i] = two_sigma * (u[i] - mean);
 }
 
 // ---------------------------------------------------------------------------

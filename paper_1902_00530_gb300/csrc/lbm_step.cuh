@@ -136,10 +136,10 @@ __device__ __forceinline__ SiteParams load_params(const LatDesc *dp)
 
 // The per-site update after streaming (App. A.2 steps 2-6).  f holds f* on
 // entry and the new populations on exit.  (gx, gy) is the isotropic gradient
-// of the post-stream density (MIPS only).  kn are the nine noise integers.
+// of the post-stream density (MIPS only).  eta is the zero-sum noise.
 template <int MODEL>
 __device__ __forceinline__ void collide_site(float f[9], float gx, float gy, const SiteParams &d,
-                                             bool noise, const int kn[9])
+                                             bool noise, const float eta[9])
 {
     // step 2: moments of f*
     const float rho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
@@ -208,12 +208,8 @@ __device__ __forceinline__ void collide_site(float f[9], float gx, float gy, con
     for (int i = 0; i < 9; ++i) f[i] = fmaf(d.omega, eq[i] - f[i], f[i]);
     // step 5: zero-sum noise eta_i = eta~_i - mean(eta~)
     if (noise) {
-        int ks = 0;
 #pragma unroll
-        for (int i = 0; i < 9; ++i) ks += kn[i];
-        const float mean = (float)ks * (d.sigma_q * (1.f / 9.f));
-#pragma unroll
-        for (int i = 0; i < 9; ++i) f[i] += fmaf((float)kn[i], d.sigma_q, -mean);
+        for (int i = 0; i < 9; ++i) f[i] += eta[i];
     }
     // step 6: negative correction (App. A.3); a set sign bit flags a candidate
     const unsigned sg = (__float_as_uint(f[0]) | __float_as_uint(f[1]) | __float_as_uint(f[2])) |
@@ -367,9 +363,9 @@ __global__ void __launch_bounds__(256) step_kernel(const StepArgs a)
                 gx = (1.f / 3.f) * (e - w) + (1.f / 12.f) * ((ne + se) - (nw + sw));
                 gy = (1.f / 3.f) * (rn[j + 1] - rm[j + 1]) + (1.f / 12.f) * ((ne + nw) - (se + sw));
             }
-            int kn[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-            if (noise && valid) noise_ints((uint32_t)(x0 + j), (uint32_t)y, t, id, a.rk, kn);
-            collide_site<MODEL>(f, gx, gy, d, noise, kn);
+            float eta[9];
+            if (noise) noise_eta((uint32_t)(x0 + j), (uint32_t)y, t, id, a.rk, d.sigma_q, eta);
+            collide_site<MODEL>(f, gx, gy, d, noise, eta);
 #pragma unroll
             for (int i = 0; i < 9; ++i) out[i][j] = f[i];
         }

@@ -295,9 +295,9 @@ __global__ void __launch_bounds__(256) step_staged_kernel(const StepArgs a)
                 gx = (1.f / 3.f) * (e - w) + (1.f / 12.f) * ((ne + se) - (nw + sw));
                 gy = (1.f / 3.f) * (rn[j + 1] - rm[j + 1]) + (1.f / 12.f) * ((ne + nw) - (se + sw));
             }
-            int kn[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-            if (noise && valid) noise_ints((uint32_t)(x0 + j), (uint32_t)y, t, id, a.rk, kn);
-            collide_site<MODEL>(g, gx, gy, d, noise, kn);
+            float eta[9];
+            if (noise) noise_eta((uint32_t)(x0 + j), (uint32_t)y, t, id, a.rk, d.sigma_q, eta);
+            collide_site<MODEL>(g, gx, gy, d, noise, eta);
 #pragma unroll
             for (int i = 0; i < 9; ++i) out[i][j] = g[i];
         }

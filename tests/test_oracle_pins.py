@@ -398,9 +398,11 @@ def test_noise_statistics():
     assert np.abs(eta.sum(1)).max() < 1e-15
     hx = (eta * EX).sum(1)
     assert abs(hx.var() - 2.0) < 5 * 2.0 * math.sqrt(2 / n)  # sigma = 1
-    # 24-bit grid: every variate is an odd multiple of 2^-24
-    k = (s * 2 ** 24)
+    # 14-bit grid: every variate is an odd multiple of 2^-14, and all 2^13
+    # positive levels occur
+    k = (s * 2 ** 14)
     assert np.all(np.abs(k - np.round(k)) == 0) and np.all(np.round(k) % 2 == 1)
+    assert len(np.unique(np.round(k[:, 0]))) > 8000
     # different step, site or lattice id: different draws
     assert not np.array_equal(O.noise_variates(1, 3, 4, 5, 0), O.noise_variates(1, 3, 4, 6, 0))
     assert not np.array_equal(O.noise_variates(1, 3, 4, 5, 0), O.noise_variates(1, 3, 4, 5, 1))
