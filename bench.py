@@ -130,6 +130,19 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def aggregate_over_ranks(cells_per_rank: int, steps: int, ms_local: float, world: int, dist=None):
+    """Replicas: every rank advances its own lattice (lattice id = rank), so the
+    whole-job rate is the work of all ranks over the slowest rank's time."""
+    ms = ms_local
+    if world > 1 and dist is not None:
+        import torch
+        dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([ms_local], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return world * cells_per_rank * steps / (ms * 1e-3) / 1e9, ms
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -201,12 +214,7 @@ def run_gpu(args, world, rank, local):
     prof = sim.profile_read()
     sim.set_profiling(False)
     ms = e0.elapsed_time(e1)
-    ms_max = ms
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-    value = world * cells * args.steps / (ms_max * 1e-3) / 1e9
+    value, ms_max = aggregate_over_ranks(cells, args.steps, ms, world, dist if world > 1 else None)
 
     # ---------------- roofline of the dominant kernel (the fused step) -------
     peak, peak_kind = measured_peak()
@@ -233,12 +241,8 @@ def run_gpu(args, world, rank, local):
     sim.get_state(host=True, out=out_state)  # D2H of the result
     obs = sim.observables()                # D2H of the observables (syncs)
     t1 = time.perf_counter()
-    e2e_s = t1 - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": round(world * cells * args.steps / e2e_s / 1e9, 3), "unit": UNIT,
+    e2e_value, _ = aggregate_over_ranks(cells, args.steps, (t1 - t0) * 1e3, world, dist if world > 1 else None)
+    e2e = {"value": round(e2e_value, 3), "unit": UNIT,
            "h2d_bytes_per_step": round(state_bytes / args.steps, 1),
            "d2h_bytes_per_step": round((out_state.numel() * 4 + 56) / args.steps, 1)}
     del out_state, host_state

@@ -117,31 +117,11 @@ __device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const uint32_t *rk)
 // (h_0's lowest).  The variate s_i = (2 m_i + 1 - 2^14) 2^-14 is built without
 // an integer conversion: u_i = 1 + (m_i + 1/2) 2^-14 is assembled directly as
 // FP32 bits (exponent of 1, m_i in the top 14 mantissa bits, then a 1), and
-// s_i = 2 u_i - 3 exactly.  The zero-sum noise eta_i = sigma (s_i - mean s)
-// = 2 sigma (u_i - mean u) is returned in eta[].
+// s_i = 2 u_i - 3 exactly.  The zero-sum noise is then eta_i = sigma (s_i -
+// mean s) = 2 sigma (u_i - mean u).
 __device__ __forceinline__ float u_from_bits(uint32_t mantissa14_at_bit9)
 {
     return __uint_as_float(0x3F800100u | mantissa14_at_bit9);
-}
-
-__device__ __forceinline__ void noise_eta(uint32_t x, uint32_t y, uint32_t t, uint32_t id, const uint32_t *rk,
-                                          float two_sigma, float eta[9])
-{
-    const uint4 a = philox4x32_10_rk(make_uint4(x, y, t, id & 0xFFFFFFu), rk);
-    const uint32_t w[4] = {a.x, a.y, a.z, a.w};
-    float u[9];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        u[2 * j] = u_from_bits((w[j] << 7) & 0x007FFE00u);      // low half: bits 2..15 -> 9..22
-        u[2 * j + 1] = u_from_bits((w[j] >> 9) & 0x007FFE00u);  // high half: bits 18..31 -> 9..22
-    }
-    const uint32_t m8 = (w[0] & 3u) | ((w[0] >> 14) & 0xCu) | ((w[1] & 3u) << 4) | ((w[1] >> 10) & 0xC0u) |
-                        ((w[2] & 3u) << 8) | ((w[2] >> 6) & 0xC00u) | ((w[3] & 3u) << 12);
-    u[8] = u_from_bits(m8 << 9);
-    const float su = ((u[0] + u[1]) + (u[2] + u[3])) + ((u[4] + u[5]) + (u[6] + u[7])) + u[8];  // exact
-    const float mean = su * (1.f / 9.f);
-#pragma unroll
-    for (int i = 0; i < 9; ++i) eta[i] = two_sigma * (u[i] - mean);
 }
 
 // ---------------------------------------------------------------------------

@@ -75,8 +75,9 @@ __device__ __forceinline__ void pull_row(const typename Store<ST>::T *base, size
 template <int VEC>
 __device__ __forceinline__ float density(const float f[9][VEC], int j)
 {
-    return ((f[0][j] + f[1][j]) + (f[2][j] + f[3][j])) + ((f[4][j] + f[5][j]) + (f[6][j] + f[7][j])) +
-           f[8][j];
+    return __fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(f[0][j], f[1][j]), __fadd_rn(f[2][j], f[3][j])),
+                               __fadd_rn(__fadd_rn(f[4][j], f[5][j]), __fadd_rn(f[6][j], f[7][j]))),
+                     f[8][j]);
 }
 
 // Post-stream density of one site by nine scalar pulls (strip-edge halo),
@@ -134,102 +135,248 @@ __device__ __forceinline__ SiteParams load_params(const LatDesc *dp)
     return p;
 }
 
-// The per-site update after streaming (App. A.2 steps 2-6).  f holds f* on
-// entry and the new populations on exit.  (gx, gy) is the isotropic gradient
-// of the post-stream density (MIPS only).  eta is the zero-sum noise.
-template <int MODEL>
-__device__ __forceinline__ void collide_site(float f[9], float gx, float gy, const SiteParams &d,
-                                             bool noise, const float eta[9])
+// ---------------------------------------------------------------------------
+// The per-site update after streaming (App. A.2 steps 2-6), written once for
+// one site (V = float) and for two sites at a time (V = float2, issued as the
+// paired FP32 instructions of sm_100+).  Every arithmetic step is an explicit
+// round-to-nearest operation, so a site's result does not depend on whether
+// it was computed alone or paired: all launch shapes agree bitwise.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float vsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float vfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 vsub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+template <typename V> __device__ __forceinline__ V splat(float s);
+template <> __device__ __forceinline__ float splat<float>(float s) { return s; }
+template <> __device__ __forceinline__ float2 splat<float2>(float s) { return make_float2(s, s); }
+
+// per-component operations (no paired form): apply a scalar function
+template <typename F> __device__ __forceinline__ float vmap(float a, F fn) { return fn(a); }
+template <typename F> __device__ __forceinline__ float2 vmap(float2 a, F fn) { return make_float2(fn(a.x), fn(a.y)); }
+template <typename F> __device__ __forceinline__ float vmap2(float a, float b, F fn) { return fn(a, b); }
+template <typename F> __device__ __forceinline__ float2 vmap2(float2 a, float2 b, F fn)
+{
+    return make_float2(fn(a.x, b.x), fn(a.y, b.y));
+}
+
+template <typename V>
+__device__ __forceinline__ V vdensity(const V f[9])
+{
+    return vadd(vadd(vadd(vadd(f[0], f[1]), vadd(f[2], f[3])), vadd(vadd(f[4], f[5]), vadd(f[6], f[7]))), f[8]);
+}
+
+// Steps 2-5: moments of f*, u*, f^SS, BGK, noise.  Returns rho (for step 6).
+template <int MODEL, typename V>
+__device__ __forceinline__ V collide_v(V f[9], V gx, V gy, const SiteParams &d, bool noise, const V eta[9])
 {
     // step 2: moments of f*
-    const float rho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
-    const float jx = (f[1] + f[5] + f[8]) - (f[3] + f[6] + f[7]);
-    const float jy = (f[2] + f[5] + f[6]) - (f[4] + f[7] + f[8]);
-    float ux = 0.f, uy = 0.f;
-    if (rho > 0.f) {
-        const float inv = __frcp_rn(rho);
-        ux = jx * inv;
-        uy = jy * inv;
-    }
+    const V rho = vdensity(f);
+    const V jx = vsub(vadd(vadd(f[1], f[5]), f[8]), vadd(vadd(f[3], f[6]), f[7]));
+    const V jy = vsub(vadd(vadd(f[2], f[5]), f[6]), vadd(vadd(f[4], f[7]), f[8]));
+    const V inv = vmap(rho, [](float r) { return r > 0.f ? __frcp_rn(r) : 0.f; });  // u = 0 where rho <= 0
+    const V ux = vmul(jx, inv), uy = vmul(jy, inv);
     // step 3: u* of the model
-    float sx, sy;
+    V sx, sy;
     if constexpr (MODEL == MODEL_PASSIVE) {
         sx = ux;
         sy = uy;
     } else if constexpr (MODEL == MODEL_MIPS) {
         // Eq. (bu_mips): C (1 - rho/rho*) grad rho below rho*, then |u*| <= U_max
-        const float c = rho < d.rho_star ? d.C * (1.f - rho * d.inv_rho_star) : 0.f;
-        sx = c * gx;
-        sy = c * gy;
-        const float m2 = sx * sx + sy * sy;
-        if (m2 > d.u_max2) {
-            const float sc = d.u_max * rsqrtf(m2);
-            sx *= sc;
-            sy *= sc;
-        }
+        const V c0 = vmul(splat<V>(d.C), vfma(vsub(splat<V>(0.f), rho), splat<V>(d.inv_rho_star), splat<V>(1.f)));
+        const float rs = d.rho_star;
+        const V c = vmap2(c0, rho, [rs](float cc, float r) { return r < rs ? cc : 0.f; });
+        sx = vmul(c, gx);
+        sy = vmul(c, gy);
+        const V m2 = vfma(sx, sx, vmul(sy, sy));
+        const float um = d.u_max, um2 = d.u_max2;
+        const V sc = vmap(m2, [um, um2](float q) { return q > um2 ? __fmul_rn(um, rsqrtf(q)) : 1.f; });
+        sx = vmul(sx, sc);
+        sy = vmul(sy, sc);
     } else {
-        // Eqs. (bu_CIL), (U0): U0(rho) u/|u|, U0 = max(B - A rho^2, 0)
-        const float ar2 = d.A * rho * rho;
-        const float U0 = d.B >= ar2 ? d.B - ar2 : 0.f;
-        const float m2 = ux * ux + uy * uy;
-        if (m2 > 0.f) {
-            const float sc = U0 * rsqrtf(m2);
-            sx = ux * sc;
-            sy = uy * sc;
-        } else {
-            sx = 0.f;
-            sy = 0.f;
-        }
+        // Eqs. (bu_CIL), (U0): U0(rho) u/|u|, U0 = max(B - A rho^2, 0); u* = 0 where u = 0
+        const V ar2 = vmul(vmul(splat<V>(d.A), rho), rho);
+        const float B = d.B;
+        const V U0 = vmap(ar2, [B](float q) { return B >= q ? __fsub_rn(B, q) : 0.f; });
+        const V m2 = vfma(ux, ux, vmul(uy, uy));
+        const V sc = vmap2(U0, m2, [](float u0, float q) { return q > 0.f ? __fmul_rn(u0, rsqrtf(q)) : 0.f; });
+        sx = vmul(ux, sc);
+        sy = vmul(uy, sc);
     }
-    // step 3 (cont.): f^SS = w rho [1 + 3 e.u* + 9/2 (e.u*)^2 - 3/2 |u*|^2]
-    // The rest population takes rho minus the moving ones: identical to
-    // w_0 rho [1 - 3/2 |u*|^2] in exact arithmetic, but the FP32 weights sum
-    // to 1 + 7.5e-9, which would otherwise change the mass by that much at
-    // every collision.
-    const float base = 1.f - 1.5f * (sx * sx + sy * sy);
-    const float r1 = wq(1) * rho, r5 = wq(5) * rho;
-    float eq[9];
+    // step 3 (cont.): f^SS = w rho [1 + 3 e.u* + 9/2 (e.u*)^2 - 3/2 |u*|^2].  The
+    // rest population takes rho minus the moving ones: identical in exact
+    // arithmetic, but the FP32 weights sum to 1 + 7.5e-9, which would otherwise
+    // change the mass by that much at every collision.
+    const V base = vfma(splat<V>(-1.5f), vfma(sx, sx, vmul(sy, sy)), splat<V>(1.f));
+    const V r1 = vmul(splat<V>(wq(1)), rho), r5 = vmul(splat<V>(wq(5)), rho);
+    V eq[9];
     {
-        const float tx = fmaf(4.5f * sx, sx, base), ty = fmaf(4.5f * sy, sy, base);
-        eq[1] = r1 * fmaf(3.f, sx, tx);
-        eq[3] = r1 * fmaf(-3.f, sx, tx);
-        eq[2] = r1 * fmaf(3.f, sy, ty);
-        eq[4] = r1 * fmaf(-3.f, sy, ty);
-        const float p = sx + sy, m = sy - sx;
-        const float tp = fmaf(4.5f * p, p, base), tm = fmaf(4.5f * m, m, base);
-        eq[5] = r5 * fmaf(3.f, p, tp);
-        eq[7] = r5 * fmaf(-3.f, p, tp);
-        eq[6] = r5 * fmaf(3.f, m, tm);
-        eq[8] = r5 * fmaf(-3.f, m, tm);
-        eq[0] = rho - (((eq[1] + eq[3]) + (eq[2] + eq[4])) + ((eq[5] + eq[7]) + (eq[6] + eq[8])));
+        const V tx = vfma(vmul(splat<V>(4.5f), sx), sx, base), ty = vfma(vmul(splat<V>(4.5f), sy), sy, base);
+        eq[1] = vmul(r1, vfma(splat<V>(3.f), sx, tx));
+        eq[3] = vmul(r1, vfma(splat<V>(-3.f), sx, tx));
+        eq[2] = vmul(r1, vfma(splat<V>(3.f), sy, ty));
+        eq[4] = vmul(r1, vfma(splat<V>(-3.f), sy, ty));
+        const V p = vadd(sx, sy), m = vsub(sy, sx);
+        const V tp = vfma(vmul(splat<V>(4.5f), p), p, base), tm = vfma(vmul(splat<V>(4.5f), m), m, base);
+        eq[5] = vmul(r5, vfma(splat<V>(3.f), p, tp));
+        eq[7] = vmul(r5, vfma(splat<V>(-3.f), p, tp));
+        eq[6] = vmul(r5, vfma(splat<V>(3.f), m, tm));
+        eq[8] = vmul(r5, vfma(splat<V>(-3.f), m, tm));
+        eq[0] = vsub(rho, vadd(vadd(vadd(eq[1], eq[3]), vadd(eq[2], eq[4])), vadd(vadd(eq[5], eq[7]), vadd(eq[6], eq[8]))));
     }
     // step 4: BGK redistribution f = f* - (f* - f^SS)/tau
+    const V om = splat<V>(d.omega);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) f[i] = fmaf(d.omega, eq[i] - f[i], f[i]);
-    // step 5: zero-sum noise eta_i = eta~_i - mean(eta~)
+    for (int i = 0; i < 9; ++i) f[i] = vfma(om, vsub(eq[i], f[i]), f[i]);
+    // step 5: zero-sum noise
     if (noise) {
 #pragma unroll
-        for (int i = 0; i < 9; ++i) f[i] += eta[i];
+        for (int i = 0; i < 9; ++i) f[i] = vadd(f[i], eta[i]);
     }
-    // step 6: negative correction (App. A.3); a set sign bit flags a candidate
+    return rho;
+}
+
+// Step 6, the negative correction of App. A.3, for one site: f_0 < 0 -> 0;
+// for i = 1..8 in index order, f_i < 0 moves |f_i| to the opposite population
+// and zeroes f_i; if anything changed, rescale to rho.  The opposite pairs are
+// disjoint, so each pair (i, j), i < j, is settled in closed form: the lower
+// index first, then the upper.
+__device__ __forceinline__ void settle_pair(float &a, float &b, float &def)
+{
+    const float na = fminf(a, 0.f);
+    a = __fsub_rn(a, na);
+    b = __fsub_rn(b, na);
+    const float nb = fminf(b, 0.f);
+    b = __fsub_rn(b, nb);
+    a = __fsub_rn(a, nb);
+    def = __fadd_rn(def, __fadd_rn(na, nb));
+}
+
+__device__ __forceinline__ void negative_correction(float f[9], float rho)
+{
     const unsigned sg = (__float_as_uint(f[0]) | __float_as_uint(f[1]) | __float_as_uint(f[2])) |
                         (__float_as_uint(f[3]) | __float_as_uint(f[4]) | __float_as_uint(f[5])) |
                         (__float_as_uint(f[6]) | __float_as_uint(f[7]) | __float_as_uint(f[8]));
-    if ((sg & 0x80000000u) &&
-        fminf(fminf(fminf(f[0], f[1]), fminf(f[2], f[3])), fminf(fminf(f[4], f[5]), fminf(fminf(f[6], f[7]), f[8]))) <
-            0.f) {
-        if (f[0] < 0.f) f[0] = 0.f;
+    if (!(sg & 0x80000000u)) return;  // no sign bit set: nothing can be negative
+    float def = fminf(f[0], 0.f);
+    f[0] = __fsub_rn(f[0], def);
+    settle_pair(f[1], f[3], def);
+    settle_pair(f[2], f[4], def);
+    settle_pair(f[5], f[7], def);
+    settle_pair(f[6], f[8], def);
+    if (def < 0.f) {
+        const float s = __fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(f[0], f[1]), __fadd_rn(f[2], f[3])),
+                                            __fadd_rn(__fadd_rn(f[4], f[5]), __fadd_rn(f[6], f[7]))),
+                                  f[8]);
+        const float sc = __fmul_rn(rho, __frcp_rn(s));
 #pragma unroll
-        for (int i = 1; i < 9; ++i) {
-            if (f[i] < 0.f) {
-                f[reverse_of(i)] += -f[i];
-                f[i] = 0.f;
+        for (int i = 0; i < 9; ++i) f[i] = __fmul_rn(f[i], sc);
+    }
+}
+
+// Zero-sum noise of one site as uniforms u_i = 1 + (m_i + 1/2) 2^-14 (see
+// noise_eta); the paired form turns them into eta below.
+__device__ __forceinline__ void noise_u(uint32_t x, uint32_t y, uint32_t t, uint32_t id, const uint32_t *rk,
+                                        float u[9])
+{
+    const uint4 a = philox4x32_10_rk(make_uint4(x, y, t, id & 0xFFFFFFu), rk);
+    const uint32_t w[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        u[2 * j] = u_from_bits((w[j] << 7) & 0x007FFE00u);
+        u[2 * j + 1] = u_from_bits((w[j] >> 9) & 0x007FFE00u);
+    }
+    const uint32_t m8 = (w[0] & 3u) | ((w[0] >> 14) & 0xCu) | ((w[1] & 3u) << 4) | ((w[1] >> 10) & 0xC0u) |
+                        ((w[2] & 3u) << 8) | ((w[2] >> 6) & 0xC00u) | ((w[3] & 3u) << 12);
+    u[8] = u_from_bits(m8 << 9);
+}
+
+// eta_i = 2 sigma (u_i - mean u) (the sum of nine u in [1, 2) is exact in FP32)
+template <typename V>
+__device__ __forceinline__ void eta_from_u(const V u[9], float two_sigma, V eta[9])
+{
+    const V su = vdensity(u);
+    const V mean = vmul(su, splat<V>(1.f / 9.f));
+#pragma unroll
+    for (int i = 0; i < 9; ++i) eta[i] = vmul(splat<V>(two_sigma), vsub(u[i], mean));
+}
+
+// The update of a lane's VEC sites, paired two at a time when VEC is even.
+// f[i][j] holds f*_i of site j on entry and the new f_i on exit; g*[j] are the
+// MIPS gradients (ignored otherwise).
+template <int MODEL, int VEC>
+__device__ __forceinline__ void collide_sites(float f[9][VEC], const float gxs[VEC], const float gys[VEC],
+                                              const SiteParams &d, bool noise, uint32_t x0, uint32_t y, uint32_t t,
+                                              uint32_t id, const uint32_t *rk)
+{
+    if constexpr (VEC % 2 == 0) {
+#pragma unroll
+        for (int j = 0; j < VEC; j += 2) {
+            float2 g[9], eta[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) g[i] = make_float2(f[i][j], f[i][j + 1]);
+            if (noise) {
+                float ua[9], ub[9];
+                noise_u(x0 + j, y, t, id, rk, ua);
+                noise_u(x0 + j + 1, y, t, id, rk, ub);
+                float2 u[9];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) u[i] = make_float2(ua[i], ub[i]);
+                eta_from_u(u, d.sigma_q, eta);
+            }
+            const float2 rho = collide_v<MODEL, float2>(g, make_float2(gxs[j], gxs[j + 1]),
+                                                        make_float2(gys[j], gys[j + 1]), d, noise, eta);
+            float a[9], b[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                a[i] = g[i].x;
+                b[i] = g[i].y;
+            }
+            negative_correction(a, rho.x);
+            negative_correction(b, rho.y);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                f[i][j] = a[i];
+                f[i][j + 1] = b[i];
             }
         }
-        const float s = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
-        const float sc = rho * __frcp_rn(s);
+    } else {
 #pragma unroll
-        for (int i = 0; i < 9; ++i) f[i] *= sc;
+        for (int j = 0; j < VEC; ++j) {
+            float g[9], eta[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) g[i] = f[i][j];
+            if (noise) {
+                float u[9];
+                noise_u(x0 + j, y, t, id, rk, u);
+                eta_from_u(u, d.sigma_q, eta);
+            }
+            const float rho = collide_v<MODEL, float>(g, gxs[j], gys[j], d, noise, eta);
+            negative_correction(g, rho);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) f[i][j] = g[i];
+        }
+    }
+}
+
+// The MIPS gradient 3 sum_i w_i rho(r + e_i) e_i at the lane's VEC sites from
+// the density windows of rows y-1 (rm), y (rc), y+1 (rn): index j+1 is site j.
+template <int VEC>
+__device__ __forceinline__ void mips_gradients(const float rm[VEC + 2], const float rc[VEC + 2],
+                                               const float rn[VEC + 2], float gx[VEC], float gy[VEC])
+{
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) {
+        const float e = rc[j + 2], w = rc[j];
+        const float ne = rn[j + 2], nw = rn[j], se = rm[j + 2], sw = rm[j];
+        gx[j] = __fmaf_rn(1.f / 3.f, __fsub_rn(e, w),
+                          __fmul_rn(1.f / 12.f, __fsub_rn(__fadd_rn(ne, se), __fadd_rn(nw, sw))));
+        gy[j] = __fmaf_rn(1.f / 3.f, __fsub_rn(rn[j + 1], rm[j + 1]),
+                          __fmul_rn(1.f / 12.f, __fsub_rn(__fadd_rn(ne, nw), __fadd_rn(se, sw))));
     }
 }
 
@@ -349,26 +496,19 @@ __global__ void __launch_bounds__(256) step_kernel(const StepArgs a)
         } else {
             pull_row<ST, VEC>(src, plane, y, ny, nx, pitch, x0, valid, last, lane, rho0, fc);
         }
+        float gx[VEC], gy[VEC];
+        if constexpr (MODEL == MODEL_MIPS) {
+            mips_gradients<VEC>(rm, rc, rn, gx, gy);
+        } else {
+#pragma unroll
+            for (int j = 0; j < VEC; ++j) gx[j] = gy[j] = 0.f;
+        }
         float out[9][VEC];
 #pragma unroll
-        for (int j = 0; j < VEC; ++j) {
-            float f[9];
+        for (int i = 0; i < 9; ++i)
 #pragma unroll
-            for (int i = 0; i < 9; ++i) f[i] = fc[i][j];
-            float gx = 0.f, gy = 0.f;
-            if constexpr (MODEL == MODEL_MIPS) {
-                // 3 sum_i w_i rho(r + e_i) e_i (Sec. 3 isotropic stencil, D2Q9 form)
-                const float e = rc[j + 2], w = rc[j];
-                const float ne = rn[j + 2], nw = rn[j], se = rm[j + 2], sw = rm[j];
-                gx = (1.f / 3.f) * (e - w) + (1.f / 12.f) * ((ne + se) - (nw + sw));
-                gy = (1.f / 3.f) * (rn[j + 1] - rm[j + 1]) + (1.f / 12.f) * ((ne + nw) - (se + sw));
-            }
-            float eta[9];
-            if (noise) noise_eta((uint32_t)(x0 + j), (uint32_t)y, t, id, a.rk, d.sigma_q, eta);
-            collide_site<MODEL>(f, gx, gy, d, noise, eta);
-#pragma unroll
-            for (int i = 0; i < 9; ++i) out[i][j] = f[i];
-        }
+            for (int j = 0; j < VEC; ++j) out[i][j] = fc[i][j];
+        collide_sites<MODEL, VEC>(out, gx, gy, d, noise, (uint32_t)x0, (uint32_t)y, t, id, a.rk);
         if (valid) {
 #pragma unroll
             for (int i = 0; i < 9; ++i)

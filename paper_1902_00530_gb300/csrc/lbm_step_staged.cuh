@@ -282,25 +282,19 @@ __global__ void __launch_bounds__(256) step_staged_kernel(const StepArgs a)
         issue_next();  // refills this row's buffer (issue_row syncs the warp first)
         q = qc + 1;
 
+        float gx[VEC], gy[VEC];
+        if constexpr (MIPS) {
+            mips_gradients<VEC>(rm, rc, rn, gx, gy);
+        } else {
+#pragma unroll
+            for (int j = 0; j < VEC; ++j) gx[j] = gy[j] = 0.f;
+        }
         float out[9][VEC];
 #pragma unroll
-        for (int j = 0; j < VEC; ++j) {
-            float g[9];
+        for (int i = 0; i < 9; ++i)
 #pragma unroll
-            for (int i = 0; i < 9; ++i) g[i] = f[i][j];
-            float gx = 0.f, gy = 0.f;
-            if constexpr (MIPS) {
-                const float e = rc[j + 2], w = rc[j];
-                const float ne = rn[j + 2], nw = rn[j], se = rm[j + 2], sw = rm[j];
-                gx = (1.f / 3.f) * (e - w) + (1.f / 12.f) * ((ne + se) - (nw + sw));
-                gy = (1.f / 3.f) * (rn[j + 1] - rm[j + 1]) + (1.f / 12.f) * ((ne + nw) - (se + sw));
-            }
-            float eta[9];
-            if (noise) noise_eta((uint32_t)(x0 + j), (uint32_t)y, t, id, a.rk, d.sigma_q, eta);
-            collide_site<MODEL>(g, gx, gy, d, noise, eta);
-#pragma unroll
-            for (int i = 0; i < 9; ++i) out[i][j] = g[i];
-        }
+            for (int j = 0; j < VEC; ++j) out[i][j] = f[i][j];
+        collide_sites<MODEL, VEC>(out, gx, gy, d, noise, (uint32_t)x0, (uint32_t)y, t, id, a.rk);
         if (valid) {
 #pragma unroll
             for (int i = 0; i < 9; ++i)
