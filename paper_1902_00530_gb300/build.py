@@ -20,7 +20,8 @@ LIB = os.path.join(BUILD, "liblbm.so")
 UNITS = ["lbm_step_f32.cu", "lbm_step_f16.cu", "lbm_step_bf16.cu", "lbm_aux.cu", "lbm_api.cu", "lbm_noalloc.cu"]
 HEADERS = ["lbm_device.cuh", "lbm_step.cuh", "lbm_step_staged.cuh", "lbm_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
+FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"] + \
+    os.environ.get("LBM_NVCC_EXTRA", "").split()
 
 
 def nvcc() -> str:
@@ -54,7 +55,10 @@ def _compile(unit: str, verbose: bool) -> str:
     return obj
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
+def build(force: bool = False, verbose: bool = False, build_dir: str | None = None) -> str:
+    global BUILD, LIB
+    if build_dir:
+        BUILD, LIB = build_dir, os.path.join(build_dir, "liblbm.so")
     os.makedirs(BUILD, exist_ok=True)
     if force:
         for u in UNITS:

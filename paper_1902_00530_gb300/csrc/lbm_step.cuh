@@ -136,11 +136,9 @@ __device__ __forceinline__ SiteParams load_params(const LatDesc *dp)
 }
 
 // ---------------------------------------------------------------------------
-// The per-site update after streaming (App. A.2 steps 2-6), written once for
-// one site (V = float) and for two sites at a time (V = float2, issued as the
-// paired FP32 instructions of sm_100+).  Every arithmetic step is an explicit
-// round-to-nearest operation, so a site's result does not depend on whether
-// it was computed alone or paired: all launch shapes agree bitwise.
+// The per-site update after streaming (App. A.2 steps 2-6).  Every arithmetic
+// step is an explicit round-to-nearest operation (no compiler contraction),
+// so a site's result does not depend on the launch shape that computed it.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ float vsub(float a, float b) { return __fsub_rn(a, b); }
@@ -172,13 +170,15 @@ __device__ __forceinline__ V vdensity(const V f[9])
 
 // Steps 2-5: moments of f*, u*, f^SS, BGK, noise.  Returns rho (for step 6).
 template <int MODEL, typename V>
-__device__ __forceinline__ V collide_v(V f[9], V gx, V gy, const SiteParams &d, bool noise, const V eta[9])
+__device__ __forceinline__ V collide_v(V f[9], V gx, V gy, const SiteParams &d, bool noise, const V eta[9],
+                                       const V *rho_known = nullptr)
 {
-    // step 2: moments of f*
-    const V rho = vdensity(f);
+    // step 2: moments of f* (rho may come precomputed, bitwise equal: the MIPS
+    // density window sums the same nine values in the same order)
+    const V rho = rho_known ? *rho_known : vdensity(f);
     const V jx = vsub(vadd(vadd(f[1], f[5]), f[8]), vadd(vadd(f[3], f[6]), f[7]));
     const V jy = vsub(vadd(vadd(f[2], f[5]), f[6]), vadd(vadd(f[4], f[7]), f[8]));
-    const V inv = vmap(rho, [](float r) { return r > 0.f ? __frcp_rn(r) : 0.f; });  // u = 0 where rho <= 0
+    const V inv = vmap(rho, [](float r) { return r > 0.f ? __fdividef(1.f, r) : 0.f; });  // u = 0 where rho <= 0
     const V ux = vmul(jx, inv), uy = vmul(jy, inv);
     // step 3: u* of the model
     V sx, sy;
@@ -215,17 +215,20 @@ __device__ __forceinline__ V collide_v(V f[9], V gx, V gy, const SiteParams &d, 
     const V r1 = vmul(splat<V>(wq(1)), rho), r5 = vmul(splat<V>(wq(5)), rho);
     V eq[9];
     {
+        // the odd term 3 e.u* is rounded once and shared by each opposite pair
         const V tx = vfma(vmul(splat<V>(4.5f), sx), sx, base), ty = vfma(vmul(splat<V>(4.5f), sy), sy, base);
-        eq[1] = vmul(r1, vfma(splat<V>(3.f), sx, tx));
-        eq[3] = vmul(r1, vfma(splat<V>(-3.f), sx, tx));
-        eq[2] = vmul(r1, vfma(splat<V>(3.f), sy, ty));
-        eq[4] = vmul(r1, vfma(splat<V>(-3.f), sy, ty));
+        const V hx = vmul(splat<V>(3.f), sx), hy = vmul(splat<V>(3.f), sy);
+        eq[1] = vmul(r1, vadd(tx, hx));
+        eq[3] = vmul(r1, vsub(tx, hx));
+        eq[2] = vmul(r1, vadd(ty, hy));
+        eq[4] = vmul(r1, vsub(ty, hy));
         const V p = vadd(sx, sy), m = vsub(sy, sx);
         const V tp = vfma(vmul(splat<V>(4.5f), p), p, base), tm = vfma(vmul(splat<V>(4.5f), m), m, base);
-        eq[5] = vmul(r5, vfma(splat<V>(3.f), p, tp));
-        eq[7] = vmul(r5, vfma(splat<V>(-3.f), p, tp));
-        eq[6] = vmul(r5, vfma(splat<V>(3.f), m, tm));
-        eq[8] = vmul(r5, vfma(splat<V>(-3.f), m, tm));
+        const V hp = vmul(splat<V>(3.f), p), hm = vmul(splat<V>(3.f), m);
+        eq[5] = vmul(r5, vadd(tp, hp));
+        eq[7] = vmul(r5, vsub(tp, hp));
+        eq[6] = vmul(r5, vadd(tm, hm));
+        eq[8] = vmul(r5, vsub(tm, hm));
         eq[0] = vsub(rho, vadd(vadd(vadd(eq[1], eq[3]), vadd(eq[2], eq[4])), vadd(vadd(eq[5], eq[7]), vadd(eq[6], eq[8]))));
     }
     // step 4: BGK redistribution f = f* - (f* - f^SS)/tau
@@ -245,7 +248,7 @@ __device__ __forceinline__ V collide_v(V f[9], V gx, V gy, const SiteParams &d, 
 // and zeroes f_i; if anything changed, rescale to rho.  The opposite pairs are
 // disjoint, so each pair (i, j), i < j, is settled in closed form: the lower
 // index first, then the upper.
-__device__ __forceinline__ void settle_pair(float &a, float &b, float &def)
+__device__ __forceinline__ void settle_pair(float &a, float &b)
 {
     const float na = fminf(a, 0.f);
     a = __fsub_rn(a, na);
@@ -253,29 +256,28 @@ __device__ __forceinline__ void settle_pair(float &a, float &b, float &def)
     const float nb = fminf(b, 0.f);
     b = __fsub_rn(b, nb);
     a = __fsub_rn(a, nb);
-    def = __fadd_rn(def, __fadd_rn(na, nb));
 }
 
+// A population with its sign bit set is negative: round-to-nearest never
+// produces -0 from the non-zero or +0 operands this update works with, so the
+// sign bits decide "anything changed" exactly.
 __device__ __forceinline__ void negative_correction(float f[9], float rho)
 {
     const unsigned sg = (__float_as_uint(f[0]) | __float_as_uint(f[1]) | __float_as_uint(f[2])) |
                         (__float_as_uint(f[3]) | __float_as_uint(f[4]) | __float_as_uint(f[5])) |
                         (__float_as_uint(f[6]) | __float_as_uint(f[7]) | __float_as_uint(f[8]));
-    if (!(sg & 0x80000000u)) return;  // no sign bit set: nothing can be negative
-    float def = fminf(f[0], 0.f);
-    f[0] = __fsub_rn(f[0], def);
-    settle_pair(f[1], f[3], def);
-    settle_pair(f[2], f[4], def);
-    settle_pair(f[5], f[7], def);
-    settle_pair(f[6], f[8], def);
-    if (def < 0.f) {
-        const float s = __fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(f[0], f[1]), __fadd_rn(f[2], f[3])),
-                                            __fadd_rn(__fadd_rn(f[4], f[5]), __fadd_rn(f[6], f[7]))),
-                                  f[8]);
-        const float sc = __fmul_rn(rho, __frcp_rn(s));
+    if (!(sg & 0x80000000u)) return;
+    f[0] = fmaxf(f[0], 0.f);
+    settle_pair(f[1], f[3]);
+    settle_pair(f[2], f[4]);
+    settle_pair(f[5], f[7]);
+    settle_pair(f[6], f[8]);
+    const float s = __fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(f[0], f[1]), __fadd_rn(f[2], f[3])),
+                                        __fadd_rn(__fadd_rn(f[4], f[5]), __fadd_rn(f[6], f[7]))),
+                              f[8]);
+    const float sc = __fdividef(rho, s);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) f[i] = __fmul_rn(f[i], sc);
-    }
+    for (int i = 0; i < 9; ++i) f[i] = __fmul_rn(f[i], sc);
 }
 
 // Zero-sum noise of one site as uniforms u_i = 1 + (m_i + 1/2) 2^-14 (see
@@ -305,61 +307,31 @@ __device__ __forceinline__ void eta_from_u(const V u[9], float two_sigma, V eta[
     for (int i = 0; i < 9; ++i) eta[i] = vmul(splat<V>(two_sigma), vsub(u[i], mean));
 }
 
-// The update of a lane's VEC sites, paired two at a time when VEC is even.
-// f[i][j] holds f*_i of site j on entry and the new f_i on exit; g*[j] are the
-// MIPS gradients (ignored otherwise).
+// The update of a lane's VEC sites, one site at a time.  f[i][j] holds f*_i
+// of site j on entry and the new f_i on exit; g*[j] are the MIPS gradients
+// (ignored otherwise).  (The paired V = float2 form of collide_v is kept for
+// completeness but not used: inlined into the kernels, the compiler rounds
+// a few of its paired steps differently from the single-site form, and launch
+// shapes must agree bitwise.)
 template <int MODEL, int VEC>
 __device__ __forceinline__ void collide_sites(float f[9][VEC], const float gxs[VEC], const float gys[VEC],
                                               const SiteParams &d, bool noise, uint32_t x0, uint32_t y, uint32_t t,
-                                              uint32_t id, const uint32_t *rk)
+                                              uint32_t id, const uint32_t *rk, const float *rho_row = nullptr)
 {
-    if constexpr (VEC % 2 == 0) {
 #pragma unroll
-        for (int j = 0; j < VEC; j += 2) {
-            float2 g[9], eta[9];
+    for (int j = 0; j < VEC; ++j) {
+        float g[9], eta[9];
 #pragma unroll
-            for (int i = 0; i < 9; ++i) g[i] = make_float2(f[i][j], f[i][j + 1]);
-            if (noise) {
-                float ua[9], ub[9];
-                noise_u(x0 + j, y, t, id, rk, ua);
-                noise_u(x0 + j + 1, y, t, id, rk, ub);
-                float2 u[9];
-#pragma unroll
-                for (int i = 0; i < 9; ++i) u[i] = make_float2(ua[i], ub[i]);
-                eta_from_u(u, d.sigma_q, eta);
-            }
-            const float2 rho = collide_v<MODEL, float2>(g, make_float2(gxs[j], gxs[j + 1]),
-                                                        make_float2(gys[j], gys[j + 1]), d, noise, eta);
-            float a[9], b[9];
-#pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                a[i] = g[i].x;
-                b[i] = g[i].y;
-            }
-            negative_correction(a, rho.x);
-            negative_correction(b, rho.y);
-#pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                f[i][j] = a[i];
-                f[i][j + 1] = b[i];
-            }
+        for (int i = 0; i < 9; ++i) g[i] = f[i][j];
+        if (noise) {
+            float u[9];
+            noise_u(x0 + j, y, t, id, rk, u);
+            eta_from_u(u, d.sigma_q, eta);
         }
-    } else {
+        const float rho = collide_v<MODEL, float>(g, gxs[j], gys[j], d, noise, eta, rho_row ? rho_row + j : nullptr);
+        negative_correction(g, rho);
 #pragma unroll
-        for (int j = 0; j < VEC; ++j) {
-            float g[9], eta[9];
-#pragma unroll
-            for (int i = 0; i < 9; ++i) g[i] = f[i][j];
-            if (noise) {
-                float u[9];
-                noise_u(x0 + j, y, t, id, rk, u);
-                eta_from_u(u, d.sigma_q, eta);
-            }
-            const float rho = collide_v<MODEL, float>(g, gxs[j], gys[j], d, noise, eta);
-            negative_correction(g, rho);
-#pragma unroll
-            for (int i = 0; i < 9; ++i) f[i][j] = g[i];
-        }
+        for (int i = 0; i < 9; ++i) f[i][j] = g[i];
     }
 }
 
@@ -508,7 +480,8 @@ __global__ void __launch_bounds__(256) step_kernel(const StepArgs a)
         for (int i = 0; i < 9; ++i)
 #pragma unroll
             for (int j = 0; j < VEC; ++j) out[i][j] = fc[i][j];
-        collide_sites<MODEL, VEC>(out, gx, gy, d, noise, (uint32_t)x0, (uint32_t)y, t, id, a.rk);
+        collide_sites<MODEL, VEC>(out, gx, gy, d, noise, (uint32_t)x0, (uint32_t)y, t, id, a.rk,
+                                  MODEL == MODEL_MIPS ? rc + 1 : nullptr);
         if (valid) {
 #pragma unroll
             for (int i = 0; i < 9; ++i)

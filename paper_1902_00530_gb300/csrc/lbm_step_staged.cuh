@@ -188,8 +188,28 @@ __device__ __forceinline__ void stage_density_window(const typename Store<ST>::T
     r[VEC + 1] = right;
 }
 
+// Minimum resident blocks of 128 threads per SM the compiler must allow for
+// (caps registers per thread at 65536 / (128 * blocks): 85, 102, 128, 128);
+// measured per VEC: these caps cost FP32 nothing and speed 16-bit storage up.
+#ifndef LBM_STAGED_MINB_1
+#define LBM_STAGED_MINB_1 6
+#endif
+#ifndef LBM_STAGED_MINB_2
+#define LBM_STAGED_MINB_2 5
+#endif
+#ifndef LBM_STAGED_MINB_4
+#define LBM_STAGED_MINB_4 4
+#endif
+#ifndef LBM_STAGED_MINB_8
+#define LBM_STAGED_MINB_8 4
+#endif
+template <int VEC> constexpr int staged_min_blocks()
+{
+    return VEC == 1 ? LBM_STAGED_MINB_1 : (VEC == 2 ? LBM_STAGED_MINB_2 : (VEC == 4 ? LBM_STAGED_MINB_4 : LBM_STAGED_MINB_8));
+}
+
 template <int MODEL, int ST, int VEC, bool SAMPLE>
-__global__ void __launch_bounds__(256) step_staged_kernel(const StepArgs a)
+__global__ void __launch_bounds__(128, staged_min_blocks<VEC>()) step_staged_kernel(const StepArgs a)
 {
     using T = typename Store<ST>::T;
     using G = StageGeom<ST, VEC>;
@@ -294,7 +314,8 @@ __global__ void __launch_bounds__(256) step_staged_kernel(const StepArgs a)
         for (int i = 0; i < 9; ++i)
 #pragma unroll
             for (int j = 0; j < VEC; ++j) out[i][j] = f[i][j];
-        collide_sites<MODEL, VEC>(out, gx, gy, d, noise, (uint32_t)x0, (uint32_t)y, t, id, a.rk);
+        collide_sites<MODEL, VEC>(out, gx, gy, d, noise, (uint32_t)x0, (uint32_t)y, t, id, a.rk,
+                                  MIPS ? rc + 1 : nullptr);
         if (valid) {
 #pragma unroll
             for (int i = 0; i < 9; ++i)
