@@ -1,0 +1,101 @@
+"""The pins catch plausible mistakes in the oracle.
+
+Each case plants one slip in a temporary copy of the oracle's C source (a
+wrong opposite direction, a dropped or mis-signed term, a reversed stream, a
+wrong constant...), compiles it, swaps it in for the real oracle and runs a
+set of pin tests: at least one must fail.  The committed oracle is never
+modified; the planted copies live in a temporary directory.
+"""
+import ctypes
+import os
+import subprocess
+
+import pytest
+
+import oracle as O
+import test_oracle_pins as P
+
+SRC = os.path.join(os.path.dirname(O.__file__), "lbm_oracle.c")
+
+# (name, text in lbm_oracle.c, replacement)
+MUTATIONS = [
+    ("opposite_table", "static const int OPP[Q] = {0, 3, 4, 1, 2, 7, 8, 5, 6};",
+     "static const int OPP[Q] = {0, 3, 4, 1, 2, 8, 7, 6, 5};"),
+    ("equilibrium_quadratic_coefficient", "(real)4.5 * eu * eu", "(real)4.0 * eu * eu"),
+    ("equilibrium_linear_sign", "((real)1 + (real)3 * eu", "((real)1 - (real)3 * eu"),
+    ("equilibrium_velocity_square", "- (real)1.5 * usq)", "- (real)1.0 * usq)"),
+    ("weights_swapped", "if (i <= 4) return (real)1 / (real)9;\n    return (real)1 / (real)36;",
+     "if (i <= 4) return (real)1 / (real)36;\n    return (real)1 / (real)9;"),
+    ("stream_reversed", "AT(fin, i, wrap(y - EY[i], ny), wrap(x - EX[i], nx))",
+     "AT(fin, i, wrap(y + EY[i], ny), wrap(x + EX[i], nx))"),
+    ("bgk_times_tau", "f[i] = fi - (fi - feq[i]) / tau;", "f[i] = fi - (fi - feq[i]) * ((real)1 / tau) * ((real)1 / tau);"),
+    ("noise_mean_not_removed", "for (int i = 0; i < Q; ++i) f[i] += et[i] - mean;",
+     "for (int i = 0; i < Q; ++i) f[i] += et[i];"),
+    ("gradient_factor", "g[0] = (real)3 * gx;", "g[0] = (real)2 * gx;"),
+    ("gradient_y_sign", "gy += weight(i) * r * (real)EY[i];", "gy -= weight(i) * r * (real)EY[i];"),
+    ("mips_ceiling_inverted", "if (rho < rs) {", "if (rho > rs) {"),
+    ("cil_u0_linear", "real a_rho2 = (real)p->A * rho * rho;", "real a_rho2 = (real)p->A * rho;"),
+    ("correction_no_rescale", "for (int i = 0; i < Q; ++i) f[i] = f[i] * (rho / sum);", "(void)sum;"),
+    ("correction_not_moved", "f[OPP[i]] += -f[i];", "(void)OPP;"),
+    ("phi_not_normalised", "out[1] = sqrt(px * px + py * py) / m;", "out[1] = sqrt(px * px + py * py);"),
+    ("column_std_over_rows", "double d = col[x] / ny - mean;", "double d = col[x] / nx - mean;"),
+    ("noise_variance", "s[i] = (2.0 * (double)m[i] + 1.0 - 16384.0) / 16384.0;",
+     "s[i] = (2.0 * (double)m[i] + 1.0 - 16384.0) / 32768.0;"),
+    ("clamp_ignored", "if (mag > (real)p->u_max) {", "if (mag > (real)1e30) {"),
+]
+
+# the pin checks run against each planted copy (all fast)
+PINS = [
+    (P.test_equilibrium_moments_textbook_d2q9, {}),
+    (P.test_equilibrium_at_rest_is_weights, {}),
+    (P.test_negative_correction_bruteforce, {}),
+    (P.test_negative_correction_examples, {}),
+    (P.test_gradient_stencil_single_mode, dict(n=16, m=1)),
+    (P.test_ustar_closures, {}),
+    (P.test_mass_conservation, dict(name="MIPS_RHO1")),
+    (P.test_fixed_points, dict(case="passive_u")),
+    (P.test_homogeneous_relaxation_closed_forms, dict(tau=1.5)),
+    (P.test_passive_shear_wave_viscosity, dict(tau=1.0)),
+    (P.test_mips_growth_rate_matches_chapman_enskog, dict(tau=1.5, C=0.2)),
+    (P.test_cil_growth_rate_matches_banding_condition, dict(A=0.4, B=0.5)),
+    (P.test_rotation_equivariance, dict(name="MIPS_RHO1")),
+    (P.test_observables_closed_forms, {}),
+    (P.test_noise_statistics, {}),
+]
+
+
+def _build(tmp_path, name, old, new):
+    text = open(SRC).read()
+    assert old in text, f"mutation site of {name} not found in the oracle"
+    src = tmp_path / f"{name}.c"
+    src.write_text(text.replace(old, new, 1))
+    libs = {}
+    for bits, real in ((64, "double"), (32, "float")):
+        out = tmp_path / f"{name}{bits}.so"
+        subprocess.run(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", f"-DREAL={real}", "-o", str(out),
+                        str(src), "-lm"], check=True)
+        libs[bits] = str(out)
+    return libs
+
+
+@pytest.mark.parametrize("name,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_pins_catch_planted_mistake(tmp_path, monkeypatch, name, old, new):
+    libs = _build(tmp_path, name, old, new)
+    O._lib(64)
+    O._lib(32)
+    saved = dict(O._LIBS)
+    caught = []
+    try:
+        for bits in (64, 32):
+            O._LIBS.pop(bits, None)
+        monkeypatch.setattr(O, "_lib_path", lambda bits: libs[bits])
+        monkeypatch.setattr(O, "build", lambda force=False: None)
+        for fn, kw in PINS:
+            try:
+                fn(**kw)
+            except AssertionError:
+                caught.append(fn.__name__)
+    finally:
+        O._LIBS.clear()
+        O._LIBS.update(saved)
+    assert caught, f"no pin caught the planted mistake {name}"

@@ -361,22 +361,28 @@ def test_phi_bounded_by_B():
 
 # -------------------------------------------------------- observables ------
 def test_observables_closed_forms():
-    """Eq. (phi), App. D on constructed states: a uniform flow, and a density
-    cosine along x (population std of a full-period cosine = amplitude/sqrt 2)."""
-    n = 32
-    f = O.from_moments(np.full((n, n), 1.2), np.full((n, n), 0.03), np.full((n, n), -0.04))
+    """Eq. (phi), App. D on constructed states (rectangular, so rows and columns
+    differ): a uniform flow, and density cosines along x and along y
+    (population std of a full-period cosine = amplitude / sqrt 2)."""
+    nx, ny = 32, 24
+    f = O.from_moments(np.full((ny, nx), 1.2), np.full((ny, nx), 0.03), np.full((ny, nx), -0.04))
     ob = O.observables(f, B=0.3)
     assert abs(ob["phi"] - 0.05) < 1e-14 and abs(ob["zeta"] - 0.25) < 1e-14
     assert ob["drho_y"] < 1e-12 and ob["drho_x"] < 1e-12 and ob["var_rho"] < 1e-24
-    assert abs(ob["mass"] - 1.2 * n * n) < 1e-13 * 1.2 * n * n
-    x = np.arange(n)[None, :] * np.ones((n, 1))
+    assert abs(ob["mass"] - 1.2 * nx * ny) < 1e-13 * 1.2 * nx * ny
+    y, x = np.mgrid[0:ny, 0:nx]
     a = 0.07
-    f = O.from_moments(1 + a * np.cos(2 * np.pi * x / n), np.zeros((n, n)), np.zeros((n, n)))
+    f = O.from_moments(1 + a * np.cos(2 * np.pi * x / nx), np.zeros((ny, nx)), np.zeros((ny, nx)))
     ob = O.observables(f, B=0.3)
     assert abs(ob["drho_y"] - a / math.sqrt(2)) < 1e-14
     assert ob["drho_x"] < 1e-12
     assert abs(ob["var_rho"] - a * a / 2) < 1e-14
     assert ob["phi"] < 1e-15 and abs(ob["zeta"] - 0.3) < 1e-14
+    b = 0.05
+    f = O.from_moments(1 + b * np.sin(2 * np.pi * 2 * y / ny), np.zeros((ny, nx)), np.zeros((ny, nx)))
+    ob = O.observables(f, B=0.3)
+    assert abs(ob["drho_x"] - b / math.sqrt(2)) < 1e-14 and ob["drho_y"] < 1e-12
+    assert abs(ob["mass"] - nx * ny) < 1e-12 * nx * ny
 
 
 # ---------------------------------------------------------------- P10 ------
