@@ -231,14 +231,15 @@ __device__ __forceinline__ V collide_v(V f[9], V gx, V gy, const SiteParams &d, 
         eq[8] = vmul(r5, vsub(tm, hm));
         eq[0] = vsub(rho, vadd(vadd(vadd(eq[1], eq[3]), vadd(eq[2], eq[4])), vadd(vadd(eq[5], eq[7]), vadd(eq[6], eq[8]))));
     }
-    // step 4: BGK redistribution f = f* - (f* - f^SS)/tau
+    // step 4: BGK redistribution f = f* - (f* - f^SS)/tau, and step 5: the
+    // zero-sum noise, added in the same expression: f* + eta + (f^SS - f*)/tau
     const V om = splat<V>(d.omega);
-#pragma unroll
-    for (int i = 0; i < 9; ++i) f[i] = vfma(om, vsub(eq[i], f[i]), f[i]);
-    // step 5: zero-sum noise
     if (noise) {
 #pragma unroll
-        for (int i = 0; i < 9; ++i) f[i] = vadd(f[i], eta[i]);
+        for (int i = 0; i < 9; ++i) f[i] = vfma(om, vsub(eq[i], f[i]), vadd(f[i], eta[i]));
+    } else {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) f[i] = vfma(om, vsub(eq[i], f[i]), f[i]);
     }
     return rho;
 }
@@ -297,14 +298,15 @@ __device__ __forceinline__ void noise_u(uint32_t x, uint32_t y, uint32_t t, uint
     u[8] = u_from_bits(m8 << 9);
 }
 
-// eta_i = 2 sigma (u_i - mean u) (the sum of nine u in [1, 2) is exact in FP32)
+// eta_i = 2 sigma (u_i - mean u) = 2 sigma u_i - 2 sigma mean u (the sum of
+// nine u in [1, 2) is exact in FP32); one fused multiply-add per population.
 template <typename V>
 __device__ __forceinline__ void eta_from_u(const V u[9], float two_sigma, V eta[9])
 {
     const V su = vdensity(u);
-    const V mean = vmul(su, splat<V>(1.f / 9.f));
+    const V shift = vmul(su, splat<V>(-two_sigma * (1.f / 9.f)));
 #pragma unroll
-    for (int i = 0; i < 9; ++i) eta[i] = vmul(splat<V>(two_sigma), vsub(u[i], mean));
+    for (int i = 0; i < 9; ++i) eta[i] = vfma(splat<V>(two_sigma), u[i], shift);
 }
 
 // The update of a lane's VEC sites, one site at a time.  f[i][j] holds f*_i
