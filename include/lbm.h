@@ -172,6 +172,19 @@ lbm_status lbm_get_state(lbm_ctx *ctx, int32_t lattice, float *dst, int32_t dst_
  * w_i rho0 rounded to nearest.  Does not change t.  Syncs. */
 lbm_status lbm_set_state(lbm_ctx *ctx, int32_t lattice, const float *src, int32_t src_is_host);
 
+/* Change the mean density of lattice `lattice` (-1: every lattice) without
+ * re-initialising, as in the paper's adiabatic density sweeps (App. C.2:
+ * "adding delta rho-bar / 7 to every f_i"; on D2Q9 delta / 9 to each of the
+ * nine populations of every site).  For 16-bit storage the shifted stored
+ * values are updated and rounded to nearest.  Enqueued on the bound stream. */
+lbm_status lbm_add_density(lbm_ctx *ctx, int32_t lattice, double delta_rho_bar);
+
+/* Replace the model parameters of lattice `lattice` (-1: every lattice)
+ * between steps (noise sweeps, App. C.1; activity sweeps, App. C.4).  Same
+ * validation as lbm_create; rho0 (the 16-bit storage shift) cannot change
+ * after lbm_init and is ignored.  Host side plus a descriptor upload (syncs). */
+lbm_status lbm_set_params(lbm_ctx *ctx, int32_t lattice, const lbm_params *params);
+
 /* Current time step t (steps taken since lbm_init or loaded with lbm_load). */
 lbm_status lbm_get_time(const lbm_ctx *ctx, int64_t *t);
 

@@ -186,6 +186,11 @@ def run(f: np.ndarray, model: str, prm: OrcParams, seed: int, t0: int, nsteps: i
     return g
 
 
+def add_density(f: np.ndarray, delta_rho_bar: float) -> np.ndarray:
+    """App. C.2 density step: add delta / Q to every population (Q = 9)."""
+    return f + np.asarray(delta_rho_bar / 9.0, dtype=f.dtype)
+
+
 def moments(f: np.ndarray, bits: int | None = None):
     """(rho, ux, uy) as float64 (ny, nx) arrays."""
     bits = 64 if f.dtype == np.float64 else 32

@@ -182,6 +182,15 @@ class Simulation:
             self.stream.wait_stream(torch.cuda.current_stream(self.device))
         self._check(self.lib.lbm_set_state(self.ctx, lattice, f.data_ptr(), 1 if host else 0))
 
+    def add_density(self, delta_rho_bar: float, lattice: int = -1) -> None:
+        """Shift the mean density by delta (App. C.2), every lattice if -1."""
+        self._check(self.lib.lbm_add_density(self.ctx, lattice, float(delta_rho_bar)))
+
+    def set_params(self, params: dict, lattice: int = -1) -> None:
+        """Replace the model parameters between steps (rho0 is kept)."""
+        p = _params(params)
+        self._check(self.lib.lbm_set_params(self.ctx, lattice, ctypes.byref(p)))
+
     def save(self, path: str) -> None:
         self._check(self.lib.lbm_save(self.ctx, str(path).encode()))
 

@@ -54,6 +54,8 @@ SIGNATURES = {
                                              ctypes.POINTER(ctypes.c_int32)]),
     "lbm_get_state": (ctypes.c_int, [_CTX, ctypes.c_int32, _P, ctypes.c_int32]),
     "lbm_set_state": (ctypes.c_int, [_CTX, ctypes.c_int32, _P, ctypes.c_int32]),
+    "lbm_add_density": (ctypes.c_int, [_CTX, ctypes.c_int32, ctypes.c_double]),
+    "lbm_set_params": (ctypes.c_int, [_CTX, ctypes.c_int32, ctypes.POINTER(lbm_params)]),
     "lbm_get_time": (ctypes.c_int, [_CTX, ctypes.POINTER(ctypes.c_int64)]),
     "lbm_save": (ctypes.c_int, [_CTX, ctypes.c_char_p]),
     "lbm_load": (ctypes.c_int, [_CTX, ctypes.c_char_p]),

@@ -853,6 +853,42 @@ lbm_status lbm_set_state(lbm_ctx *c, int32_t lattice, const float *src, int32_t 
     return LBM_OK;
 }
 
+lbm_status lbm_add_density(lbm_ctx *c, int32_t lattice, double delta_rho_bar)
+{
+    lbm_status st = require_ready(c, true);
+    if (st != LBM_OK) return st;
+    if (lattice < -1 || lattice >= (int32_t)c->lats.size()) return fail(c, LBM_ERR_INVALID_ARG, "bad lattice index");
+    if (!std::isfinite(delta_rho_bar)) return fail(c, LBM_ERR_INVALID_ARG, "delta must be finite");
+    for (int k = 0; k < (int)c->lats.size(); ++k) {
+        if (lattice != -1 && k != lattice) continue;
+        const LatHost &L = c->lats[k];
+        CK(launch_add_density(L.lat.storage, all_desc(c), k, (long long)L.lat.nx * L.lat.ny, c->parity,
+                              (float)(delta_rho_bar / 9.0), c->stream),
+           "launch density step");
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_set_params(lbm_ctx *c, int32_t lattice, const lbm_params *params)
+{
+    if (!c || !params) return LBM_ERR_INVALID_ARG;
+    if (lattice < -1 || lattice >= (int32_t)c->lats.size()) return fail(c, LBM_ERR_INVALID_ARG, "bad lattice index");
+    for (int k = 0; k < (int)c->lats.size(); ++k) {
+        if (lattice != -1 && k != lattice) continue;
+        const std::string why = validate(c->lats[k].lat, c->lats[k].model, *params);
+        if (!why.empty()) return fail(c, LBM_ERR_INVALID_ARG, why);
+    }
+    for (int k = 0; k < (int)c->lats.size(); ++k) {
+        if (lattice != -1 && k != lattice) continue;
+        const double keep_rho0 = c->lats[k].p.rho0;
+        c->lats[k].p = *params;
+        c->lats[k].p.rho0 = keep_rho0;
+    }
+    drop_graphs(c);
+    if (c->bound) return upload_descs(c);
+    return LBM_OK;
+}
+
 lbm_status lbm_get_time(const lbm_ctx *c, int64_t *t)
 {
     if (!c || !t) return LBM_ERR_INVALID_ARG;

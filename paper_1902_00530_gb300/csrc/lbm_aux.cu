@@ -124,6 +124,26 @@ __global__ void import_kernel(const LatDesc *desc, int lat, int dst, const float
     }
 }
 
+// Add a constant to every population of one lattice (App. C.2 density step).
+template <int ST>
+__global__ void add_density_kernel(const LatDesc *desc, int lat, int buf, float per_population)
+{
+    using T = typename Store<ST>::T;
+    const LatDesc d = desc[lat];
+    T *base = reinterpret_cast<T *>(d.f[buf]);
+    const size_t plane = (size_t)d.ny * d.pitch;
+    const long long n = (long long)d.nx * d.ny;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < 9 * n;
+         c += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(c / n);
+        const long long r = c % n;
+        const int x = (int)(r % d.nx), y = (int)(r / d.nx);
+        T *p = base + i * plane + (size_t)y * d.pitch + x;
+        const float shift = wq(i) * d.rho0;
+        *p = Store<ST>::put(__fadd_rn(Store<ST>::get(*p, shift), per_population), shift);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Observable finaliser.  Grid (nchunk, nlat): block (c, l) sums, in a fixed
 // order, chunk c of lattice l's column partials (over strip rows), row
@@ -300,6 +320,16 @@ cudaError_t launch_import(int storage, const LatDesc *desc, int lat, long long c
     if (storage == ST_F32) import_kernel<ST_F32><<<g, 256, 0, s>>>(desc, lat, dst, in);
     else if (storage == ST_F16) import_kernel<ST_F16><<<g, 256, 0, s>>>(desc, lat, dst, in);
     else import_kernel<ST_BF16><<<g, 256, 0, s>>>(desc, lat, dst, in);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_add_density(int storage, const LatDesc *desc, int lat, long long cells, int buf, float per_pop,
+                               cudaStream_t s)
+{
+    const int g = grid_for(9 * cells, 256);
+    if (storage == ST_F32) add_density_kernel<ST_F32><<<g, 256, 0, s>>>(desc, lat, buf, per_pop);
+    else if (storage == ST_F16) add_density_kernel<ST_F16><<<g, 256, 0, s>>>(desc, lat, buf, per_pop);
+    else add_density_kernel<ST_BF16><<<g, 256, 0, s>>>(desc, lat, buf, per_pop);
     return cudaGetLastError();
 }
 

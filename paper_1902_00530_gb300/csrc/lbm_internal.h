@@ -31,6 +31,8 @@ cudaError_t launch_import(int storage, const LatDesc *desc, int lat, long long c
 cudaError_t launch_finalize(const LatDesc *desc, int nlat, int max_chunk, const uint32_t *t_ptr, uint32_t k,
                             int to_ring, unsigned *err, cudaStream_t s);
 cudaError_t launch_advance_time(uint32_t *t_ptr, uint32_t n, cudaStream_t s);
+cudaError_t launch_add_density(int storage, const LatDesc *desc, int lat, long long cells, int buf, float per_pop,
+                               cudaStream_t s);
 cudaError_t launch_set_time(uint32_t *t_ptr, uint32_t t, cudaStream_t s);
 
 }  // namespace lbm

@@ -178,7 +178,7 @@ __device__ __forceinline__ V collide_v(V f[9], V gx, V gy, const SiteParams &d, 
     const V rho = rho_known ? *rho_known : vdensity(f);
     const V jx = vsub(vadd(vadd(f[1], f[5]), f[8]), vadd(vadd(f[3], f[6]), f[7]));
     const V jy = vsub(vadd(vadd(f[2], f[5]), f[6]), vadd(vadd(f[4], f[7]), f[8]));
-    const V inv = vmap(rho, [](float r) { return r > 0.f ? __fdividef(1.f, r) : 0.f; });  // u = 0 where rho <= 0
+    const V inv = vmap(rho, [](float r) { return r > 0.f ? __frcp_rn(r) : 0.f; });  // u = 0 where rho <= 0
     const V ux = vmul(jx, inv), uy = vmul(jy, inv);
     // step 3: u* of the model
     V sx, sy;
@@ -276,7 +276,7 @@ __device__ __forceinline__ void negative_correction(float f[9], float rho)
     const float s = __fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(f[0], f[1]), __fadd_rn(f[2], f[3])),
                                         __fadd_rn(__fadd_rn(f[4], f[5]), __fadd_rn(f[6], f[7]))),
                               f[8]);
-    const float sc = __fdividef(rho, s);
+    const float sc = __fmul_rn(rho, __frcp_rn(s));  // correctly rounded: an approximate one biases the mass
 #pragma unroll
     for (int i = 0; i < 9; ++i) f[i] = __fmul_rn(f[i], sc);
 }
@@ -298,15 +298,20 @@ __device__ __forceinline__ void noise_u(uint32_t x, uint32_t y, uint32_t t, uint
     u[8] = u_from_bits(m8 << 9);
 }
 
-// eta_i = 2 sigma (u_i - mean u) = 2 sigma u_i - 2 sigma mean u (the sum of
-// nine u in [1, 2) is exact in FP32); one fused multiply-add per population.
+// eta_i = 2 sigma (u_i - mean u) (the sum of nine u in [1, 2) is exact in
+// FP32).  The ninth takes minus the sum of the other eight, which is the same
+// in exact arithmetic and keeps sum eta = 0 to one unbiased rounding: a shared
+// rounded factor (such as 2 sigma / 9) would bias every site the same way and
+// drift the mass.
 template <typename V>
 __device__ __forceinline__ void eta_from_u(const V u[9], float two_sigma, V eta[9])
 {
     const V su = vdensity(u);
     const V shift = vmul(su, splat<V>(-two_sigma * (1.f / 9.f)));
 #pragma unroll
-    for (int i = 0; i < 9; ++i) eta[i] = vfma(splat<V>(two_sigma), u[i], shift);
+    for (int i = 0; i < 8; ++i) eta[i] = vfma(splat<V>(two_sigma), u[i], shift);
+    eta[8] = vsub(splat<V>(0.f),
+                  vadd(vadd(vadd(eta[0], eta[1]), vadd(eta[2], eta[3])), vadd(vadd(eta[4], eta[5]), vadd(eta[6], eta[7]))));
 }
 
 // The update of a lane's VEC sites, one site at a time.  f[i][j] holds f*_i

@@ -1,0 +1,64 @@
+"""Regime classification and adiabatic sweeps (App. C and D of arXiv:1902.00530).
+
+Host-side logic on top of the observables the library reduces on the GPU:
+
+* ``classify_cil``: the App. D table for the CIL model -- homogeneous
+  disordered (HD: phi below its cutoff), homogeneous ordered (HO: drho at or
+  below its cutoff), banding (B) and reverse banding (RB: zeta above its
+  cutoff), plus "motionless" where B - A rho-bar^2 <= 0 (the paper's fifth,
+  trivial phase).
+* ``mips_separated``: App. C.1's phase-separation criterion drho > 0.0430.
+* ``density_sweep``: App. C.3's adiabatic procedure -- step t_sample steps,
+  take a sample, change the mean density by delta (App. C.2), repeat.
+
+The paper's cutoffs are in its units (mean densities 0.1-0.35).  Under the
+model's density-rescaling symmetry (rho -> s rho with C/s, s rho*, A/s^2,
+s sigma) velocities are unchanged and densities scale by s, so phi and zeta
+cutoffs carry over while the drho cutoffs scale by s: pass
+``density_scale = s`` for the rescaled ("RHO1") presets.
+"""
+from __future__ import annotations
+
+PHI_CUT = 0.024           # App. D: phi < 0.024 is HD (CIL)
+DRHO_CUT_CIL = 0.012      # App. D: drho > 0.012 is B or RB
+ZETA_CUT = 0.1            # App. D: zeta > 0.1 is RB
+DRHO_CUT_MIPS = 0.0430    # App. C.1: drho > 0.0430 is phase separated
+
+
+def classify_cil(phi: float, drho: float, zeta: float, density_scale: float = 1.0,
+                 A: float | None = None, B: float | None = None, rho_bar: float | None = None) -> str:
+    """The App. D regime of one CIL sample (or of averaged observables)."""
+    if A is not None and B is not None and rho_bar is not None and B - A * rho_bar * rho_bar <= 0:
+        return "motionless"
+    if phi < PHI_CUT:
+        return "HD"
+    if drho <= DRHO_CUT_CIL * density_scale:
+        return "HO"
+    return "RB" if zeta > ZETA_CUT else "B"
+
+
+def mips_separated(drho: float, density_scale: float = 1.0) -> bool:
+    """App. C.1: phase separation when drho exceeds 0.0430 (paper units)."""
+    return drho > DRHO_CUT_MIPS * density_scale
+
+
+def density_sweep(sim, rho_start: float, rho_end: float, delta: float, t_sample: int, lattice: int = -1,
+                  t_sample_of=None):
+    """App. C.3: from mean density rho_start, repeat {step t_sample steps; sample
+    the observables; add delta to the mean density} until rho_end is passed.
+    ``t_sample_of(rho)`` may vary the interval with the density (the paper uses
+    500 steps above rho-bar 0.2 and 1500 below).  Returns [(rho_bar, obs)]
+    for the lattice (lattice 0 if -1)."""
+    if delta == 0 or (rho_end - rho_start) * delta < 0:
+        raise ValueError("delta must move rho_start towards rho_end")
+    out = []
+    rho = rho_start
+    k = 0
+    target = lattice if lattice >= 0 else 0
+    while (rho - rho_end) * (1 if delta > 0 else -1) <= 1e-12:
+        sim.step(t_sample_of(rho) if t_sample_of else t_sample)
+        out.append((rho, sim.observables(target)))
+        sim.add_density(delta, lattice)
+        k += 1
+        rho = rho_start + k * delta
+    return out

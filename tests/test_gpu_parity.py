@@ -463,3 +463,41 @@ def test_zero_steps_and_limits():
     with pytest.raises(LBMError):
         sim.observables(lattice=3)
     sim.close()
+
+
+# --------------------------------------------- sweeps: density and params ---
+@pytest.mark.parametrize("storage", ["f32", "f16s"])
+def test_add_density_matches_oracle(storage):
+    """App. C.2: delta rho-bar / Q added to every population mid-run."""
+    model, d = split_preset("CIL_PAPER_LITERAL")
+    nx, ny, spec = 64, 48, W.INIT_CONFIG2
+    sim = gpu_sim(model, d, nx, ny, SEED, spec, storage=storage)
+    sim.step(20)
+    m0 = sim.observables()["mass"]
+    sim.add_density(0.05)
+    assert abs(sim.observables()["mass"] - (m0 + 0.05 * nx * ny)) / m0 < 1e-6
+    sim.step(20)
+    got = sim.get_state(host=True).numpy().astype(np.float64)
+    sim.close()
+    p = O.params(**d)
+    f = O.run(O.init(nx, ny, SEED, **spec, prm=p), model, p, SEED, 0, 20)
+    f = O.run(O.add_density(f, 0.05), model, p, SEED, 20, 20)
+    tol = 1e-5 if storage == "f32" else 2e-3
+    assert max(errors(got, f)) <= tol
+
+
+def test_set_params_mid_run_matches_oracle():
+    """Noise sweep step (App. C.1): sigma changed between steps."""
+    model, d = split_preset("MIPS_PAPER_LITERAL")
+    d2 = dict(d, sigma=2 * d["sigma"])
+    nx, ny, spec = 64, 48, W.INIT_CONFIG1
+    sim = gpu_sim(model, d, nx, ny, SEED, spec)
+    sim.step(30)
+    sim.set_params(d2)
+    sim.step(30)
+    got = sim.get_state(host=True).numpy().astype(np.float64)
+    sim.close()
+    p, p2 = O.params(**d), O.params(**d2)
+    f = O.run(O.init(nx, ny, SEED, **spec, prm=p), model, p, SEED, 0, 30)
+    f = O.run(f, model, p2, SEED, 30, 30)
+    assert max(errors(got, f)) <= 1e-5

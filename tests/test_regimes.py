@@ -1,0 +1,72 @@
+"""App. D regime table and the App. C.3 sweep loop (host logic, no GPU)."""
+import json
+import os
+
+import pytest
+
+from paper_1902_00530_gb300 import regimes as R
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+G = json.load(open(os.path.join(HERE, "golden", "paper_parameters.json")))
+
+
+def test_cutoffs_are_the_papers():
+    assert R.PHI_CUT == G["cil_thresholds"]["phi"]
+    assert R.DRHO_CUT_CIL == G["cil_thresholds"]["drho"]
+    assert R.ZETA_CUT == G["cil_thresholds"]["zeta"]
+    assert R.DRHO_CUT_MIPS == G["mips_sweep"]["drho_threshold"]
+
+
+@pytest.mark.parametrize("phi,drho,zeta,expect", [
+    (0.010, 0.050, 0.20, "HD"),      # phi below cutoff: HD whatever the rest
+    (0.024, 0.012, 0.20, "HO"),      # at both cutoffs: ordered, homogeneous
+    (0.100, 0.013, 0.05, "B"),
+    (0.100, 0.013, 0.10, "B"),       # zeta at the cutoff is not RB
+    (0.100, 0.030, 0.15, "RB"),
+])
+def test_cil_table(phi, drho, zeta, expect):
+    assert R.classify_cil(phi, drho, zeta) == expect
+
+
+def test_density_scale_moves_only_drho_cutoff():
+    s = 1 / 0.185
+    assert R.classify_cil(0.1, 0.012 * s * 0.99, 0.2, density_scale=s) == "HO"
+    assert R.classify_cil(0.1, 0.012 * s * 1.01, 0.2, density_scale=s) == "RB"
+    assert R.classify_cil(0.0239, 1.0, 1.0, density_scale=s) == "HD"
+    assert R.mips_separated(0.0431) and not R.mips_separated(0.0429)
+    assert R.mips_separated(0.0431 / 0.12, density_scale=1 / 0.12)
+
+
+def test_motionless_above_the_U0_line():
+    # App. D: B - A rho-bar^2 <= 0 is the trivial no-motion phase
+    assert R.classify_cil(0.2, 0.0, 0.0, A=2.0, B=0.3, rho_bar=0.39) == "motionless"
+    assert R.classify_cil(0.2, 0.0, 0.0, A=2.0, B=0.3, rho_bar=0.38) == "HO"
+
+
+class FakeSim:
+    def __init__(self):
+        self.log = []
+        self.rho = 0.09
+
+    def step(self, n):
+        self.log.append(("step", n))
+
+    def observables(self, lattice=0):
+        return {"rho": self.rho}
+
+    def add_density(self, delta, lattice=-1):
+        self.rho += delta
+        self.log.append(("add", round(delta, 6)))
+
+
+def test_density_sweep_follows_app_c3():
+    sim = FakeSim()
+    res = R.density_sweep(sim, 0.09, 0.1, 0.0025, 1500,
+                          t_sample_of=lambda r: 500 if r > 0.2 else 1500)
+    assert [round(r, 6) for r, _ in res] == [0.09, 0.0925, 0.095, 0.0975, 0.1]
+    assert sim.log[0] == ("step", 1500) and sim.log[1] == ("add", 0.0025)
+    sim = FakeSim()
+    down = R.density_sweep(sim, 0.35, 0.345, -0.0025, 500)
+    assert [round(r, 6) for r, _ in down] == [0.35, 0.3475, 0.345]
+    with pytest.raises(ValueError):
+        R.density_sweep(sim, 0.1, 0.2, -0.01, 10)
