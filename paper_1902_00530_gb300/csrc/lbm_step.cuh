@@ -299,19 +299,21 @@ __device__ __forceinline__ void noise_u(uint32_t x, uint32_t y, uint32_t t, uint
 }
 
 // eta_i = 2 sigma (u_i - mean u) (the sum of nine u in [1, 2) is exact in
-// FP32).  The ninth takes minus the sum of the other eight, which is the same
-// in exact arithmetic and keeps sum eta = 0 to one unbiased rounding: a shared
-// rounded factor (such as 2 sigma / 9) would bias every site the same way and
-// drift the mass.
+// FP32).  The rest population takes minus the sum of the eight moving ones,
+// which is the same in exact arithmetic and keeps sum eta = 0 to one unbiased
+// rounding.  The rounded shift -2 sigma sum(u) / 9 is shared by the eight
+// moving directions, so its rounding error cancels in sum_i eta_i e_i; the
+// absorber must be the rest population, whose e_0 = 0: a moving one would
+// turn that error into the same momentum kick at every site and step.
 template <typename V>
 __device__ __forceinline__ void eta_from_u(const V u[9], float two_sigma, V eta[9])
 {
     const V su = vdensity(u);
     const V shift = vmul(su, splat<V>(-two_sigma * (1.f / 9.f)));
 #pragma unroll
-    for (int i = 0; i < 8; ++i) eta[i] = vfma(splat<V>(two_sigma), u[i], shift);
-    eta[8] = vsub(splat<V>(0.f),
-                  vadd(vadd(vadd(eta[0], eta[1]), vadd(eta[2], eta[3])), vadd(vadd(eta[4], eta[5]), vadd(eta[6], eta[7]))));
+    for (int i = 1; i < 9; ++i) eta[i] = vfma(splat<V>(two_sigma), u[i], shift);
+    eta[0] = vsub(splat<V>(0.f),
+                  vadd(vadd(vadd(eta[1], eta[2]), vadd(eta[3], eta[4])), vadd(vadd(eta[5], eta[6]), vadd(eta[7], eta[8]))));
 }
 
 // The update of a lane's VEC sites, one site at a time.  f[i][j] holds f*_i
