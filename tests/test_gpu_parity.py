@@ -299,6 +299,10 @@ def test_observables_16bit_storage():
 @pytest.mark.parametrize("name,over,spec", [("MIPS_RHO1", dict(C=0.2), W.INIT_CONFIG1),
                                              ("CIL_RHO1", {}, W.init_ordered(U0_CIL, u_amp=0.01))])
 def test_moments_match_oracle(name, over, spec):
+    """lbm_moments against the oracle's moments after 25 steps.  The CIL
+    ordered state has a marginal mode (the common direction of u, Sec. 4), so
+    rounding differences there do not decay: the bound is 1e-5 or 4x the FP32
+    oracle's own divergence, as for the other marginal regimes."""
     model, d = split_preset(name, **over)
     nx, ny = 80, 48
     sim = gpu_sim(model, d, nx, ny, SEED, spec)
@@ -306,8 +310,15 @@ def test_moments_match_oracle(name, over, spec):
     rho, ux, uy = (a.cpu().numpy().astype(np.float64) for a in sim.moments())
     sim.close()
     rr, uxr, uyr = O.moments(oracle_run(model, d, nx, ny, 25, SEED, spec))
-    assert np.abs(rho - rr).max() < 1e-5
-    assert max(np.abs(ux - uxr).max(), np.abs(uy - uyr).max()) < 1e-5
+    e_rho = np.abs(rho - rr).max()
+    e_u = max(np.abs(ux - uxr).max(), np.abs(uy - uyr).max())
+    if max(e_rho, e_u) < 1e-5:
+        return
+    assert name == "CIL_RHO1", (e_rho, e_u)
+    r2, ux2, uy2 = O.moments(oracle_run(model, d, nx, ny, 25, SEED, spec, bits=32).astype(np.float64))
+    i_rho = np.abs(r2 - rr).max()
+    i_u = max(np.abs(ux2 - uxr).max(), np.abs(uy2 - uyr).max())
+    assert e_rho <= 4 * i_rho + 1e-6 and e_u <= 4 * i_u + 1e-6, (e_rho, e_u, i_rho, i_u)
 
 
 @pytest.mark.parametrize("name,over,spec", [("PASSIVE", dict(sigma=0.0099), W.INIT_CONFIG2),
