@@ -4,10 +4,12 @@ TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
 CPU-baseline leg of ``bench.py`` may import this package.  It shares no code
 with the CUDA path (``paper_1902_00530_gb300``) and never imports it.
 
-The arithmetic lives in ``lbm_oracle.c`` (plain C, compiled with gcc at
+The arithmetic lives in ``lbm_oracle.c`` (D2Q9) and ``lbm_oracle_d2q7.c``
+(the paper's triangular D2Q7 lattice), plain C compiled together with gcc at
 ``-O2 -ffp-contract=off`` so no fused multiply-adds change its rounding on any
-host).  This module only compiles it, loads it with ctypes and moves numpy
-arrays in and out.  Populations are numpy arrays of shape (9, ny, nx).
+host.  This module only compiles it, loads it with ctypes and moves numpy
+arrays in and out.  Populations are numpy arrays of shape (9, ny, nx), or
+(7, ny, nx) for the functions with the suffix 7.
 
 Functions and the passages they follow:
   step / run          App. A.2 (steps 1-6), Eq. (fevolution2)
@@ -18,10 +20,14 @@ Functions and the passages they follow:
   init                App. C.2 initialisation (f = f^SS of seeded rho, u)
   observables         Eq. (phi); App. D (rho_y std, zeta)
   noise_variates      Eq. (noiseDensityConservation) draws, Philox4x32-10
+  *7 (init7, run7, equilibrium7, gradient7, ...)
+                      the same on D2Q7: Sec. 2 lattice, Eq. (fssD2Q7) as
+                      printed, the Sec. 3 explicit stencils, App. A.3 pairs
 """
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 import threading
@@ -30,6 +36,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lbm_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "lbm_oracle_d2q7.c")]
 _BUILD = os.path.join(_HERE, "_build")
 _LOCK = threading.Lock()
 _LIBS: dict[int, ctypes.CDLL] = {}
@@ -58,11 +65,12 @@ def build(force: bool = False) -> None:
     os.makedirs(_BUILD, exist_ok=True)
     for bits, real in ((64, "double"), (32, "float")):
         out = _lib_path(bits)
-        if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(_SRC):
+        if not force and os.path.exists(out) and all(os.path.getmtime(out) >= os.path.getmtime(src)
+                                                     for src in _SRCS):
             continue
         tmp = out + f".tmp{os.getpid()}"
         cmd = ["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", f"-DREAL={real}",
-               "-o", tmp, _SRC, "-lm"]
+               "-o", tmp, *_SRCS, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, out)
 
@@ -99,6 +107,21 @@ def _lib(bits: int = 64) -> ctypes.CDLL:
         lib.orc_noise_variates.argtypes = [u64, u32, u32, u32, u32, dbl_p]
         lib.orc_init_uniforms.argtypes = [u64, u32, u32, u32, dbl_p]
         lib.orc_real_bytes.restype = i32
+        lib.orc7_run_window.argtypes = [real_p, i32, i32, i32, prm, u64, u32, i64, u32, i32, i32, i32, i32]
+        lib.orc7_run_window.restype = i32
+        lib.orc7_init_window.argtypes = lib.orc_init_window.argtypes
+        lib.orc7_init_window.restype = None
+        lib.orc7_from_moments.argtypes = [real_p, i32, i32, dbl_p, dbl_p, dbl_p]
+        lib.orc7_moments.argtypes = [real_p, i32, i32, dbl_p, dbl_p, dbl_p]
+        lib.orc7_observables.argtypes = [real_p, i32, i32, ctypes.c_double, dbl_p]
+        lib.orc7_observables.restype = i32
+        lib.orc7_equilibrium.argtypes = [rl] * 3 + [real_p]
+        lib.orc7_negative_correction.argtypes = [real_p, rl]
+        lib.orc7_negative_correction.restype = i32
+        lib.orc7_gradient.argtypes = [real_p, i32, i32, i32, i32, real_p]
+        lib.orc7_noise_variates.argtypes = [u64, u32, u32, u32, u32, dbl_p]
+        ip = ctypes.POINTER(ctypes.c_int)
+        lib.orc7_neighbour.argtypes = [i32, i32, i32, i32, i32, i32, ip, ip]
         assert lib.orc_real_bytes() * 8 == bits
         _LIBS[bits] = lib
         return lib
@@ -272,3 +295,128 @@ def init_uniforms(seed: int, x: int, y: int, lattice_id: int = 0) -> np.ndarray:
     u = np.empty(4)
     lib.orc_init_uniforms(seed, x, y, lattice_id, _ptr(u, ctypes.c_double))
     return u
+
+
+# ---------------------------------------------------------------- D2Q7 ----
+Q7_E = np.array([[0.0, 0.0]] + [[math.cos(k * math.pi / 3), math.sin(k * math.pi / 3)] for k in range(6)])
+Q7_W = np.array([0.5] + [1.0 / 12.0] * 6)
+
+
+def _check_f7(f: np.ndarray, bits: int) -> None:
+    if f.ndim != 3 or f.shape[0] != 7:
+        raise ValueError("D2Q7 populations must have shape (7, ny, nx)")
+    if f.shape[1] % 2:
+        raise ValueError("a periodic D2Q7 box needs an even ny (the odd rows are offset)")
+    if f.dtype != _dtype(bits) or not f.flags.c_contiguous:
+        raise ValueError(f"populations must be C-contiguous {_dtype(bits).__name__}")
+
+
+def positions7(nx: int, ny: int):
+    """Site positions (X, Y) of the D2Q7 box: X = x + (y mod 2)/2, Y = y sqrt(3)/2."""
+    y, x = np.mgrid[0:ny, 0:nx]
+    return x + 0.5 * (y % 2), y * (math.sqrt(3.0) / 2.0)
+
+
+def neighbour7(x: int, y: int, i: int, s: int, nx: int, ny: int):
+    """Index of the site at r + s e_i on the D2Q7 box."""
+    lib = _lib(64)
+    xn, yn = ctypes.c_int(), ctypes.c_int()
+    lib.orc7_neighbour(x, y, i, s, nx, ny, ctypes.byref(xn), ctypes.byref(yn))
+    return xn.value, yn.value
+
+
+def init7(nx: int, ny: int, seed: int, lattice_id: int = 0, rho_mean: float = 1.0,
+          rho_amp: float = 0.0, u_kind: int = 0, u_amp: float = 0.0, ux0: float = 0.0,
+          uy0: float = 0.0, prm: OrcParams | None = None, bits: int = 64, window=None) -> np.ndarray:
+    """Seeded D2Q7 initial populations (App. C.2), the same rho, u as init()."""
+    if ny % 2:
+        raise ValueError("a periodic D2Q7 box needs an even ny")
+    lib = _lib(bits)
+    f = np.empty((7, ny, nx), dtype=_dtype(bits))
+    xo, yo, gx, gy = window if window is not None else (0, 0, nx, ny)
+    lib.orc7_init_window(_rp(f, bits), nx, ny, seed, lattice_id, rho_mean, rho_amp, u_kind, u_amp,
+                         ux0, uy0, ctypes.byref(prm if prm is not None else params()), xo, yo, gx, gy)
+    return f
+
+
+def from_moments7(rho: np.ndarray, ux: np.ndarray, uy: np.ndarray, bits: int = 64) -> np.ndarray:
+    lib = _lib(bits)
+    rho, ux, uy = (np.ascontiguousarray(a, dtype=np.float64) for a in (rho, ux, uy))
+    ny, nx = rho.shape
+    f = np.empty((7, ny, nx), dtype=_dtype(bits))
+    lib.orc7_from_moments(_rp(f, bits), nx, ny, _ptr(rho, ctypes.c_double),
+                          _ptr(ux, ctypes.c_double), _ptr(uy, ctypes.c_double))
+    return f
+
+
+def run7(f: np.ndarray, model: str, prm: OrcParams, seed: int, t0: int, nsteps: int,
+         lattice_id: int = 0, bits: int = 64, window=None) -> np.ndarray:
+    """nsteps D2Q7 steps from t0 (App. A.2); window as in run() with an even y offset."""
+    g = np.array(f, dtype=_dtype(bits), order="C", copy=True)
+    _check_f7(g, bits)
+    lib = _lib(bits)
+    xo, yo, gx, gy = window if window is not None else (0, 0, g.shape[2], g.shape[1])
+    rc = lib.orc7_run_window(_rp(g, bits), g.shape[2], g.shape[1], MODELS[model], ctypes.byref(prm),
+                             seed, t0, nsteps, lattice_id, xo, yo, gx, gy)
+    if rc == -2:
+        raise ValueError("D2Q7 windows need even ny, y offset and box height")
+    if rc != 0:
+        raise MemoryError("oracle run failed")
+    return g
+
+
+def add_density7(f: np.ndarray, delta_rho_bar: float) -> np.ndarray:
+    """App. C.2 density step on D2Q7: delta / 7 added to every population."""
+    return f + np.asarray(delta_rho_bar / 7.0, dtype=f.dtype)
+
+
+def moments7(f: np.ndarray):
+    bits = 64 if f.dtype == np.float64 else 32
+    _check_f7(f, bits)
+    lib = _lib(bits)
+    ny, nx = f.shape[1:]
+    rho, ux, uy = (np.empty((ny, nx)) for _ in range(3))
+    lib.orc7_moments(_rp(f, bits), nx, ny, _ptr(rho, ctypes.c_double),
+                     _ptr(ux, ctypes.c_double), _ptr(uy, ctypes.c_double))
+    return rho, ux, uy
+
+
+def observables7(f: np.ndarray, B: float = 0.0) -> dict:
+    bits = 64 if f.dtype == np.float64 else 32
+    _check_f7(f, bits)
+    lib = _lib(bits)
+    out = np.zeros(6)
+    rc = lib.orc7_observables(_rp(f, bits), f.shape[2], f.shape[1], B, _ptr(out, ctypes.c_double))
+    if rc != 0:
+        raise MemoryError("oracle observables failed")
+    return dict(zip(OBS_NAMES, out.tolist()))
+
+
+def equilibrium7(rho: float, ux: float, uy: float, bits: int = 64) -> np.ndarray:
+    lib = _lib(bits)
+    out = np.empty(7, dtype=_dtype(bits))
+    lib.orc7_equilibrium(rho, ux, uy, _rp(out, bits))
+    return out
+
+
+def negative_correction7(f7, rho: float, bits: int = 64):
+    lib = _lib(bits)
+    g = np.array(f7, dtype=_dtype(bits), copy=True)
+    changed = lib.orc7_negative_correction(_rp(g, bits), rho)
+    return g, bool(changed)
+
+
+def gradient7(rho: np.ndarray, x: int, y: int, bits: int = 64) -> np.ndarray:
+    lib = _lib(bits)
+    r = np.ascontiguousarray(rho, dtype=_dtype(bits))
+    g = np.empty(2, dtype=_dtype(bits))
+    lib.orc7_gradient(_rp(r, bits), r.shape[1], r.shape[0], x, y, _rp(g, bits))
+    return g
+
+
+def noise_variates7(seed: int, x: int, y: int, t: int, lattice_id: int = 0) -> np.ndarray:
+    """The seven s_i in (-1, 1) of a D2Q7 site at step t; eta~_i = sigma s_i."""
+    lib = _lib(64)
+    s = np.empty(7)
+    lib.orc7_noise_variates(seed, x, y, t, lattice_id, _ptr(s, ctypes.c_double))
+    return s

@@ -446,19 +446,16 @@ void orc_moments(const real *f, int nx, int ny, double *rho, double *ux, double 
  *  out[3] drho_x     = the same with the axes swapped
  *  out[4] var_rho    = population variance of rho over all sites
  *  out[5] zeta       = sum rho (B - |u|) / sum rho          (App. D)       */
-int orc_observables(const real *f, int nx, int ny, double B, double out[6])
+int orc_observables_from_moments(const double *rho, const double *ux, const double *uy, int nx, int ny,
+                                 double B, double out[6])
 {
     size_t n = (size_t)nx * (size_t)ny;
-    double *rho = (double *)malloc(sizeof(double) * n);
-    double *ux = (double *)malloc(sizeof(double) * n);
-    double *uy = (double *)malloc(sizeof(double) * n);
     double *col = (double *)calloc((size_t)nx, sizeof(double));
     double *row = (double *)calloc((size_t)ny, sizeof(double));
-    if (!rho || !ux || !uy || !col || !row) {
-        free(rho); free(ux); free(uy); free(col); free(row);
+    if (!col || !row) {
+        free(col); free(row);
         return -1;
     }
-    orc_moments(f, nx, ny, rho, ux, uy);
     double m = 0, px = 0, py = 0, z = 0;
     for (size_t c = 0; c < n; ++c) {
         m += rho[c];
@@ -489,8 +486,24 @@ int orc_observables(const real *f, int nx, int ny, double B, double out[6])
     out[3] = sqrt(sx / ny);
     out[4] = v / (double)n;
     out[5] = z / m;
-    free(rho); free(ux); free(uy); free(col); free(row);
+    free(col); free(row);
     return 0;
+}
+
+int orc_observables(const real *f, int nx, int ny, double B, double out[6])
+{
+    size_t n = (size_t)nx * (size_t)ny;
+    double *rho = (double *)malloc(sizeof(double) * n);
+    double *ux = (double *)malloc(sizeof(double) * n);
+    double *uy = (double *)malloc(sizeof(double) * n);
+    if (!rho || !ux || !uy) {
+        free(rho); free(ux); free(uy);
+        return -1;
+    }
+    orc_moments(f, nx, ny, rho, ux, uy);
+    int rc = orc_observables_from_moments(rho, ux, uy, nx, ny, B, out);
+    free(rho); free(ux); free(uy);
+    return rc;
 }
 
 /* Precision tag, so a loader can tell the two builds apart. */

@@ -15,7 +15,10 @@ import pytest
 import oracle as O
 import test_oracle_pins as P
 
-SRC = os.path.join(os.path.dirname(O.__file__), "lbm_oracle.c")
+import test_oracle_d2q7_pins as P7
+
+ODIR = os.path.dirname(O.__file__)
+SRCS = {"q9": os.path.join(ODIR, "lbm_oracle.c"), "q7": os.path.join(ODIR, "lbm_oracle_d2q7.c")}
 
 # (name, text in lbm_oracle.c, replacement)
 MUTATIONS = [
@@ -44,6 +47,28 @@ MUTATIONS = [
     ("clamp_ignored", "if (mag > (real)p->u_max) {", "if (mag > (real)1e30) {"),
 ]
 
+# slips in the D2Q7 file: (name, text in lbm_oracle_d2q7.c, replacement)
+MUTATIONS7 = [
+    ("q7_row_offset_sign", "int twice_x = 2 * x + par_y + s * E2X[i];", "int twice_x = 2 * x - par_y + s * E2X[i];"),
+    ("q7_stream_reversed", "orc7_neighbour(x, y, i, -1, nx, ny, &xs, &ys);",
+     "orc7_neighbour(x, y, i, +1, nx, ny, &xs, &ys);"),
+    ("q7_opposite_table", "static const int OPP7[Q7] = {0, 4, 5, 6, 1, 2, 3};",
+     "static const int OPP7[Q7] = {0, 4, 6, 5, 1, 3, 2};"),
+    ("q7_equilibrium_quadratic", "(real)8 * eu * eu", "(real)4.5 * eu * eu"),
+    ("q7_equilibrium_velocity_square", "- (real)2 * usq)", "- (real)1.5 * usq)"),
+    ("q7_weights", "return i == 0 ? (real)1 / (real)2 : (real)1 / (real)12;",
+     "return i == 0 ? (real)4 / (real)10 : (real)1 / (real)10;"),
+    ("q7_row_spacing", "return (real)ERY[i] * (real)sqrt(3.0) / (real)2;", "return (real)ERY[i];"),
+    ("q7_gradient_dy", "((real)4 * dy)", "((real)4 * dx)"),
+    ("q7_gradient_x_terms", "(r[2] + r[6]) - (r[3] + r[5])", "(r[2] + r[3]) - (r[5] + r[6])"),
+    ("q7_noise_mean_over_nine", "mean = mean / (real)Q7;", "mean = mean / (real)9;"),
+    ("q7_init_row_spacing", "double eu = 0.5 * E2X[i] * vx + hs3 * ERY[i] * vy;",
+     "double eu = 0.5 * E2X[i] * vx + 0.5 * ERY[i] * vy;"),
+    ("q7_moments_row_spacing", "jy += fi * hs3 * ERY[i];", "jy += fi * 0.5 * ERY[i];"),
+    ("q7_noise_bits", "s[i] = (2.0 * (double)h + 1.0 - 65536.0) / 65536.0;",
+     "s[i] = (2.0 * (double)h + 1.0 - 65536.0) / 131072.0;"),
+]
+
 # the pin checks run against each planted copy (all fast)
 PINS = [
     (P.test_equilibrium_moments_textbook_d2q9, {}),
@@ -64,23 +89,49 @@ PINS = [
 ]
 
 
-def _build(tmp_path, name, old, new):
-    text = open(SRC).read()
-    assert old in text, f"mutation site of {name} not found in the oracle"
-    src = tmp_path / f"{name}.c"
-    src.write_text(text.replace(old, new, 1))
+PINS7 = [
+    (P7.test_neighbours_follow_positions, dict(nx=5, ny=4)),
+    (P7.test_streaming_moves_populations_along_e, {}),
+    (P7.test_equilibrium_moments_textbook_d2q7, {}),
+    (P7.test_equilibrium_at_rest_is_weights7, {}),
+    (P7.test_negative_correction_bruteforce7, {}),
+    (P7.test_negative_correction_examples7, {}),
+    (P7.test_gradient_stencils_on_plane_waves, dict(nx=9, ny=14, m=2, n=3)),
+    (P7.test_mass_conservation7, dict(name="MIPS_RHO1")),
+    (P7.test_passive_shear_wave_viscosity7, dict(axis="y", tau=1.0)),
+    (P7.test_passive_shear_wave_viscosity7, dict(axis="x", tau=1.0)),
+    (P7.test_mips_growth_rate_matches_chapman_enskog7, dict(axis="y", tau=1.0, C=1.0)),
+    (P7.test_noise_statistics7, {}),
+    (P7.test_init7_recipe, {}),
+]
+
+
+def _build(tmp_path, name, old, new, which):
+    srcs = []
+    for key, path in SRCS.items():
+        text = open(path).read()
+        if key == which:
+            assert old in text, f"mutation site of {name} not found in the oracle"
+            text = text.replace(old, new, 1)
+        src = tmp_path / f"{name}_{key}.c"
+        src.write_text(text)
+        srcs.append(str(src))
     libs = {}
     for bits, real in ((64, "double"), (32, "float")):
         out = tmp_path / f"{name}{bits}.so"
         subprocess.run(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", f"-DREAL={real}", "-o", str(out),
-                        str(src), "-lm"], check=True)
+                        *srcs, "-lm"], check=True)
         libs[bits] = str(out)
     return libs
 
 
-@pytest.mark.parametrize("name,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
-def test_pins_catch_planted_mistake(tmp_path, monkeypatch, name, old, new):
-    libs = _build(tmp_path, name, old, new)
+CASES = [(m, "q9") for m in MUTATIONS] + [(m, "q7") for m in MUTATIONS7]
+
+
+@pytest.mark.parametrize("mut,which", CASES, ids=[m[0] for m, _ in CASES])
+def test_pins_catch_planted_mistake(tmp_path, monkeypatch, mut, which):
+    name, old, new = mut
+    libs = _build(tmp_path, name, old, new, which)
     O._lib(64)
     O._lib(32)
     saved = dict(O._LIBS)
@@ -90,7 +141,7 @@ def test_pins_catch_planted_mistake(tmp_path, monkeypatch, name, old, new):
             O._LIBS.pop(bits, None)
         monkeypatch.setattr(O, "_lib_path", lambda bits: libs[bits])
         monkeypatch.setattr(O, "build", lambda force=False: None)
-        for fn, kw in PINS:
+        for fn, kw in (PINS if which == "q9" else PINS7):
             try:
                 fn(**kw)
             except AssertionError:
