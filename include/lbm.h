@@ -23,10 +23,11 @@
  *    Device-side conditions (non-finite observables, a barrier that timed out)
  *    are latched in a device flag and reported by the next syncing call.
  *  - Populations.  Device storage is structure-of-arrays per lattice:
- *    f[i][y][pitch] for i = 0..8, x fastest, with the D2Q9 velocities
- *    e = (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1) (-1,-1) (1,-1).
- *    Calls that exchange populations with the caller use dense FP32
- *    [9][ny][nx] arrays regardless of the storage type.
+ *    f[i][y][pitch] for i = 0..Q-1, x fastest, with the D2Q9 velocities
+ *    e = (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1) (-1,-1) (1,-1)
+ *    (Q = 9) or the D2Q7 set below (Q = 7).  Calls that exchange populations
+ *    with the caller use dense FP32 [Q][ny][nx] arrays regardless of the
+ *    storage type.
  *  - Threads.  One context per host thread; contexts are independent.
  */
 #ifndef LBM_H
@@ -61,13 +62,28 @@ typedef enum {
     LBM_BF16_SHIFTED = 2  /* stored as BF16 of f_i - w_i rho0, collided in FP32      */
 } lbm_storage;
 
+typedef enum {
+    LBM_D2Q9 = 0, /* square lattice, nine velocities (the default)                  */
+    LBM_D2Q7 = 1  /* the paper's triangular lattice (Sec. 2), seven velocities       */
+} lbm_velocity_set;
+
 /* One periodic rectangular lattice (Sec. 4: "rectangular geometry with
  * periodic boundary conditions").  id keys the lattice's random streams: two
- * lattices with the same seed, id and state evolve identically. */
+ * lattices with the same seed, id and state evolve identically.
+ *
+ * D2Q7 (Sec. 2): e_0 = 0, e_i = (cos((i-1) pi/3), sin((i-1) pi/3)), i = 1..6,
+ * w_0 = 1/2, w_i = 1/12, c_s^2 = 1/4; f^SS with the printed coefficients 4, 8,
+ * -2 (Eq. (fssD2Q7)); grad rho by the explicit Sec. 3 stencils; App. A.3
+ * pairs 1-4, 2-5, 3-6.  Site (x, y) sits at (x + (y mod 2)/2, y sqrt(3)/2):
+ * rows are sqrt(3)/2 apart and every odd row is shifted right by half a
+ * spacing, so ny must be even.  Populations are f[i][y][x], i = 0..6.  The
+ * noise of a site uses one Philox call whose 16-bit halves h_0..h_6 give
+ * s_i = (2 h_i + 1 - 2^16) / 2^16.  The TMA-staged kernel is D2Q9 only. */
 typedef struct {
-    int32_t nx, ny;   /* sites along x and y, each in [1, 65536]        */
-    int32_t storage;  /* an lbm_storage value                           */
-    int32_t id;       /* random-stream id, in [0, 2^24)                 */
+    int32_t nx, ny;        /* sites along x and y, each in [1, 65536]; D2Q7: ny even */
+    int32_t storage;       /* an lbm_storage value                                   */
+    int32_t id;            /* random-stream id, in [0, 2^24)                         */
+    int32_t velocity_set;  /* an lbm_velocity_set value (0 = D2Q9)                   */
 } lbm_lattice;
 
 /* Model parameters (App. C tables), all in lattice units dx = dt = c = 1. */
@@ -146,7 +162,7 @@ lbm_status lbm_init(lbm_ctx *ctx, uint64_t seed, const lbm_init_spec *specs);
 lbm_status lbm_step(lbm_ctx *ctx, int64_t n);
 
 /* Density and velocity of every site of lattice `lattice` in its stored
- * state (Eq. (D2Q7macroscopic) on D2Q9): rho, ux, uy are DEVICE pointers to
+ * state (Eq. (D2Q7macroscopic), on either lattice): rho, ux, uy are DEVICE pointers to
  * dense FP32 [ny][nx] arrays, written asynchronously on the bound stream. */
 lbm_status lbm_moments(lbm_ctx *ctx, int32_t lattice, float *rho, float *ux, float *uy);
 
@@ -162,20 +178,20 @@ lbm_status lbm_observables(lbm_ctx *ctx, int32_t lattice, lbm_obs *out);
 lbm_status lbm_observable_series(lbm_ctx *ctx, int32_t lattice, lbm_obs *out, int32_t cap,
                                  int32_t *n_out);
 
-/* Copy lattice `lattice`'s populations out as dense FP32 [9][ny][nx]; dst is a
+/* Copy lattice `lattice`'s populations out as dense FP32 [Q][ny][nx]; dst is a
  * host pointer if dst_is_host, else a device pointer.  16-bit storage is
  * expanded to f_i = w_i rho0 + s_i.  Syncs. */
 lbm_status lbm_get_state(lbm_ctx *ctx, int32_t lattice, float *dst, int32_t dst_is_host);
 
-/* Replace lattice `lattice`'s populations by dense FP32 [9][ny][nx] from src
+/* Replace lattice `lattice`'s populations by dense FP32 [Q][ny][nx] from src
  * (host if src_is_host, else device).  16-bit storage stores s_i = f_i -
  * w_i rho0 rounded to nearest.  Does not change t.  Syncs. */
 lbm_status lbm_set_state(lbm_ctx *ctx, int32_t lattice, const float *src, int32_t src_is_host);
 
 /* Change the mean density of lattice `lattice` (-1: every lattice) without
  * re-initialising, as in the paper's adiabatic density sweeps (App. C.2:
- * "adding delta rho-bar / 7 to every f_i"; on D2Q9 delta / 9 to each of the
- * nine populations of every site).  For 16-bit storage the shifted stored
+ * "adding delta rho-bar / 7 to every f_i": delta / Q to each of the Q
+ * populations of every site).  For 16-bit storage the shifted stored
  * values are updated and rounded to nearest.  Enqueued on the bound stream. */
 lbm_status lbm_add_density(lbm_ctx *ctx, int32_t lattice, double delta_rho_bar);
 
@@ -202,7 +218,8 @@ lbm_status lbm_load(lbm_ctx *ctx, const char *path);
  * (1..8), stages = 0 for the kernel that loads populations straight from
  * global memory, or 2..8 (MIPS: 3..8; at most 4 warps) for the kernel that
  * stages population rows in shared memory with bulk copies, that many rows
- * per warp (needs nx a multiple of 16 bytes of storage).  Host only;
+ * per warp (needs nx a multiple of 16 bytes of storage; D2Q9 only: D2Q7
+ * lattices use the direct kernel whatever stages says, and need rows even).  Host only;
  * re-uploads descriptors (syncs) when bound. */
 lbm_status lbm_set_tuning(lbm_ctx *ctx, int32_t mode, int32_t vec, int32_t rows, int32_t warps,
                           int32_t stages);
@@ -240,7 +257,7 @@ lbm_status lbm_profile_read(lbm_ctx *ctx, double *step_ms, int64_t *step_launche
  * footprint fixed.  It computes the same record as lbm_observables (Eq. (phi),
  * App. D) for a caller-supplied state instead of a context's.
  *
- * f_dev: DEVICE pointer to dense FP32 populations [9][ny][nx] (caller-owned,
+ * f_dev: DEVICE pointer to dense FP32 D2Q9 populations [9][ny][nx] (caller-owned,
  * read only); 1 <= nx, ny <= LBM_NOALLOC_MAX_SIDE.  B: the CIL constant used
  * by zeta.  out: host record (t is set to 0).  cuda_stream: the stream to run
  * on (NULL = legacy default stream); the call waits for it before returning.

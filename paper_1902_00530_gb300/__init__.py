@@ -30,8 +30,13 @@ class LBMError(RuntimeError):
 class Lattice:
     nx: int
     ny: int
-    storage: str = "f32"   # "f32", "f16s" or "bf16s"
-    id: int = 0            # random-stream id
+    storage: str = "f32"          # "f32", "f16s" or "bf16s"
+    id: int = 0                   # random-stream id
+    velocity_set: str = "d2q9"    # "d2q9", or "d2q7" (the paper's triangular lattice; ny even)
+
+    @property
+    def q(self) -> int:
+        return 7 if self.velocity_set == "d2q7" else 9
 
 
 def build(force: bool = False) -> str:
@@ -75,7 +80,8 @@ class Simulation:
             raise ValueError("lattices, models and params need the same non-zero length")
         self.lattices = list(lattices)
         self.models = [m if isinstance(m, str) else {0: "passive", 1: "mips", 2: "cil"}[m] for m in models]
-        lats = (_abi.lbm_lattice * n)(*[_abi.lbm_lattice(l.nx, l.ny, _abi.STORAGES[l.storage], l.id)
+        lats = (_abi.lbm_lattice * n)(*[_abi.lbm_lattice(l.nx, l.ny, _abi.STORAGES[l.storage], l.id,
+                                                         _abi.VELOCITY_SETS[l.velocity_set])
                                         for l in lattices])
         mods = (ctypes.c_int * n)(*[_abi.MODELS[m] for m in self.models])
         prms = (_abi.lbm_params * n)(*[_params(p) for p in params])
@@ -156,17 +162,17 @@ class Simulation:
         return [{k: getattr(buf[i], k) for k, _ in _abi.lbm_obs._fields_} for i in range(n.value)]
 
     def get_state(self, lattice: int = 0, host: bool = False, out=None):
-        """Populations as dense FP32 (9, ny, nx); a (pinned) CPU tensor if host."""
+        """Populations as dense FP32 (Q, ny, nx); a (pinned) CPU tensor if host."""
         torch = self._torch
         L = self.lattices[lattice]
         if out is not None:
-            if tuple(out.shape) != (9, L.ny, L.nx) or out.dtype != torch.float32 or not out.is_contiguous():
-                raise ValueError("out must be a contiguous float32 (9, ny, nx) tensor")
+            if tuple(out.shape) != (L.q, L.ny, L.nx) or out.dtype != torch.float32 or not out.is_contiguous():
+                raise ValueError(f"out must be a contiguous float32 ({L.q}, ny, nx) tensor")
             host = out.device.type == "cpu"
         elif host:
-            out = torch.empty((9, L.ny, L.nx), dtype=torch.float32, pin_memory=True)
+            out = torch.empty((L.q, L.ny, L.nx), dtype=torch.float32, pin_memory=True)
         else:
-            out = torch.empty((9, L.ny, L.nx), dtype=torch.float32, device=self.device)
+            out = torch.empty((L.q, L.ny, L.nx), dtype=torch.float32, device=self.device)
         self._check(self.lib.lbm_get_state(self.ctx, lattice, out.data_ptr(), 1 if host else 0))
         return out
 
@@ -174,8 +180,8 @@ class Simulation:
         torch = self._torch
         L = self.lattices[lattice]
         f = torch.as_tensor(f)
-        if tuple(f.shape) != (9, L.ny, L.nx):
-            raise ValueError(f"state must have shape (9, {L.ny}, {L.nx})")
+        if tuple(f.shape) != (L.q, L.ny, L.nx):
+            raise ValueError(f"state must have shape ({L.q}, {L.ny}, {L.nx})")
         f = f.to(torch.float32).contiguous()
         host = f.device.type == "cpu"
         if not host:

@@ -14,11 +14,12 @@ STATUS_NAMES = {0: "LBM_OK", 1: "LBM_ERR_INVALID_ARG", 2: "LBM_ERR_UNBOUND", 3: 
                 4: "LBM_ERR_TIMEOUT", 5: "LBM_ERR_NUMERIC", 6: "LBM_ERR_UNSUPPORTED"}
 MODELS = {"passive": 0, "mips": 1, "cil": 2}
 STORAGES = {"f32": 0, "f16s": 1, "bf16s": 2}
+VELOCITY_SETS = {"d2q9": 0, "d2q7": 1}
 
 
 class lbm_lattice(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("storage", ctypes.c_int32),
-                ("id", ctypes.c_int32)]
+                ("id", ctypes.c_int32), ("velocity_set", ctypes.c_int32)]
 
 
 class lbm_params(ctypes.Structure):

@@ -36,6 +36,7 @@ size_t elem_bytes(int storage) { return storage == LBM_F32 ? 4 : 2; }
 
 struct LatHost {
     lbm_lattice lat;
+    int q = 9;  // populations per site (9 for D2Q9, 7 for D2Q7)
     int model;
     lbm_params p;
     float rho0 = 1.f;
@@ -47,7 +48,7 @@ struct LatHost {
 };
 
 struct GroupHost {
-    int model = 0, storage = 0;
+    int model = 0, storage = 0, q = 9;
     std::vector<int> members;
     int vec = 1, rows = 32, warps = 4, blocks = 0;
     int stages = 0;  // 0: direct-load kernel; >= 2: TMA-staged kernel with that many row buffers
@@ -122,6 +123,8 @@ std::string validate(const lbm_lattice &l, int model, const lbm_params &p)
     if (l.nx < 1 || l.ny < 1 || l.nx > 65536 || l.ny > 65536) return "nx, ny must be in [1, 65536]";
     if (l.storage < LBM_F32 || l.storage > LBM_BF16_SHIFTED) return "unknown storage type";
     if (l.id < 0 || l.id >= (1 << 24)) return "lattice id must be in [0, 2^24)";
+    if (l.velocity_set != LBM_D2Q9 && l.velocity_set != LBM_D2Q7) return "unknown velocity set";
+    if (l.velocity_set == LBM_D2Q7 && l.ny % 2) return "a periodic D2Q7 box needs an even ny (odd rows are offset)";
     if (model < LBM_PASSIVE || model > LBM_CIL) return "unknown model";
     if (!finite_all(p)) return "parameters must be finite";
     if (!(p.tau > 0.5)) return "tau must exceed 1/2";
@@ -133,8 +136,10 @@ std::string validate(const lbm_lattice &l, int model, const lbm_params &p)
 }
 
 // The staged kernel copies 16-byte halos: nx must be a multiple of that width.
+// It exists for D2Q9 only.
 bool staged_ok(const lbm_ctx *c, const GroupHost &g)
 {
+    if (g.q != 9) return false;
     const int halo = g.storage == LBM_F32 ? 4 : 8;
     for (int m : g.members)
         if (c->lats[m].lat.nx % halo != 0 || c->lats[m].lat.nx < halo) return false;
@@ -169,7 +174,7 @@ void layout(lbm_ctx *c)
         const size_t eb = elem_bytes(L.lat.storage);
         const size_t align_elems = 128 / eb;
         L.pitch = ((size_t)L.lat.nx + align_elems - 1) / align_elems * align_elems;
-        L.buf_bytes = align256(9 * (size_t)L.lat.ny * L.pitch * eb);
+        L.buf_bytes = align256((size_t)L.q * L.lat.ny * L.pitch * eb);
         L.state_off = so;
         so += 2 * L.buf_bytes;
     }
@@ -234,6 +239,7 @@ LatDesc make_desc(const lbm_ctx *c, const LatHost &L, int block_begin, const Gro
     d.rows = g.rows;
     d.block_begin = block_begin;
     d.ring_cap = std::max(c->ring_cap, 1);
+    d.q = L.q;
     const long long nstrip = (long long)d.nsx * d.nsy;
     d.nchunk = std::min(L.nchunk_max, std::max(1, ceil_div(std::max<long long>({L.lat.nx, L.lat.ny, nstrip}), CHUNK_COLS)));
     d.omega = (float)(1.0 / L.p.tau);
@@ -306,6 +312,7 @@ cudaError_t launch_group_step(const lbm_ctx *c, const GroupHost &g, int src, uin
         a.rk[2 * r] = a.key0 + (uint32_t)r * 0x9E3779B9u;
         a.rk[2 * r + 1] = a.key1 + (uint32_t)r * 0xBB67AE85u;
     }
+    if (g.q == 7) return launch_step_q7(g.storage, g.model, g.vec, sample, a, g.blocks, g.warps, c->stream);
     const int kind = g.stages > 0 ? 1 : 0;
     if (g.storage == LBM_F32)
         return launch_step_f32(g.model, kind, g.vec, sample, a, g.blocks, g.warps, c->stream);
@@ -326,6 +333,7 @@ cudaError_t launch_group_observe(const lbm_ctx *c, const GroupHost &g, int src)
     a.stages = 0;
     a.err = err_dev(c);
     for (int r = 0; r < 20; ++r) a.rk[r] = 0;
+    if (g.q == 7) return launch_observe_q7(g.storage, g.vec, a, g.blocks, g.warps, c->stream);
     if (g.storage == LBM_F32) return launch_observe_f32(g.vec, a, g.blocks, g.warps, c->stream);
     if (g.storage == LBM_F16_SHIFTED) return launch_observe_f16(g.vec, a, g.blocks, g.warps, c->stream);
     return launch_observe_bf16(g.vec, a, g.blocks, g.warps, c->stream);
@@ -419,7 +427,7 @@ lbm_status tune_group(lbm_ctx *c, GroupHost &g)
     long long max_ny = 1;
     for (int m : g.members) max_ny = std::max<long long>(max_ny, c->lats[m].lat.ny);
     const int all_v[] = {1, 2, 4, 8};
-    const bool staged = staged_ok(c, g);
+    const bool staged = staged_ok(c, g);  // false for D2Q7
     const int base_stages = g.model == LBM_MIPS ? 4 : 3;
     for (int v : all_v) {
         if (!allowed_vec(g.storage, v)) continue;
@@ -504,18 +512,21 @@ lbm_status create_common(int32_t n, const lbm_lattice *lats, const lbm_model *mo
         L.model = (int)models[k];
         L.p = ps[k];
         L.rho0 = ps[k].rho0 > 0 ? (float)ps[k].rho0 : 1.f;
+        L.q = lats[k].velocity_set == LBM_D2Q7 ? 7 : 9;
         c->lats.push_back(L);
     }
-    // launch groups: one per (model, storage)
+    // launch groups: one per (model, storage, velocity set)
     for (int32_t k = 0; k < n; ++k) {
         LatHost &L = c->lats[k];
         int gi = -1;
         for (size_t q = 0; q < c->groups.size(); ++q)
-            if (c->groups[q].model == L.model && c->groups[q].storage == L.lat.storage) gi = (int)q;
+            if (c->groups[q].model == L.model && c->groups[q].storage == L.lat.storage && c->groups[q].q == L.q)
+                gi = (int)q;
         if (gi < 0) {
             GroupHost g;
             g.model = L.model;
             g.storage = L.lat.storage;
+            g.q = L.q;
             c->groups.push_back(g);
             gi = (int)c->groups.size() - 1;
         }
@@ -774,19 +785,19 @@ lbm_status lbm_get_state(lbm_ctx *c, int32_t lattice, float *dst, int32_t dst_is
     const size_t eb = elem_bytes(L.lat.storage);
     const long long cells = (long long)L.lat.nx * L.lat.ny;
     if (L.lat.storage == LBM_F32) {
-        CK(cudaMemcpy2DAsync(dst, L.lat.nx * 4, src, L.pitch * 4, L.lat.nx * 4, 9 * (size_t)L.lat.ny,
+        CK(cudaMemcpy2DAsync(dst, L.lat.nx * 4, src, L.pitch * 4, L.lat.nx * 4, (size_t)L.q * L.lat.ny,
                              dst_is_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c->stream),
            "copy populations");
     } else if (!dst_is_host) {
         CK(launch_export(L.lat.storage, all_desc(c), lattice, cells, c->parity, dst, c->stream), "launch export");
     } else {
-        std::vector<uint16_t> raw((size_t)9 * cells);
-        CK(cudaMemcpy2DAsync(raw.data(), L.lat.nx * eb, src, L.pitch * eb, L.lat.nx * eb, 9 * (size_t)L.lat.ny,
+        std::vector<uint16_t> raw((size_t)L.q * cells);
+        CK(cudaMemcpy2DAsync(raw.data(), L.lat.nx * eb, src, L.pitch * eb, L.lat.nx * eb, (size_t)L.q * L.lat.ny,
                              cudaMemcpyDeviceToHost, c->stream),
            "copy populations");
         CK(cudaStreamSynchronize(c->stream), "synchronise");
-        for (int i = 0; i < 9; ++i) {
-            const float shift = wq(i) * L.rho0;
+        for (int i = 0; i < L.q; ++i) {
+            const float shift = pop_shift(L.q, i, L.rho0);
             for (long long q = 0; q < cells; ++q) {
                 const uint16_t bits = raw[(size_t)i * cells + q];
                 float v;
@@ -823,15 +834,15 @@ lbm_status lbm_set_state(lbm_ctx *c, int32_t lattice, const float *src, int32_t 
     const size_t eb = elem_bytes(L.lat.storage);
     const long long cells = (long long)L.lat.nx * L.lat.ny;
     if (L.lat.storage == LBM_F32) {
-        CK(cudaMemcpy2DAsync(dstp, L.pitch * 4, src, L.lat.nx * 4, L.lat.nx * 4, 9 * (size_t)L.lat.ny,
+        CK(cudaMemcpy2DAsync(dstp, L.pitch * 4, src, L.lat.nx * 4, L.lat.nx * 4, (size_t)L.q * L.lat.ny,
                              src_is_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, c->stream),
            "copy populations");
     } else if (!src_is_host) {
         CK(launch_import(L.lat.storage, all_desc(c), lattice, cells, c->parity, src, c->stream), "launch import");
     } else {
-        std::vector<uint16_t> raw((size_t)9 * cells);
-        for (int i = 0; i < 9; ++i) {
-            const float shift = wq(i) * L.rho0;
+        std::vector<uint16_t> raw((size_t)L.q * cells);
+        for (int i = 0; i < L.q; ++i) {
+            const float shift = pop_shift(L.q, i, L.rho0);
             for (long long q = 0; q < cells; ++q) {
                 const float v = src[(size_t)i * cells + q] - shift;
                 uint16_t bits;
@@ -845,7 +856,7 @@ lbm_status lbm_set_state(lbm_ctx *c, int32_t lattice, const float *src, int32_t 
                 raw[(size_t)i * cells + q] = bits;
             }
         }
-        CK(cudaMemcpy2DAsync(dstp, L.pitch * eb, raw.data(), L.lat.nx * eb, L.lat.nx * eb, 9 * (size_t)L.lat.ny,
+        CK(cudaMemcpy2DAsync(dstp, L.pitch * eb, raw.data(), L.lat.nx * eb, L.lat.nx * eb, (size_t)L.q * L.lat.ny,
                              cudaMemcpyHostToDevice, c->stream),
            "copy populations");
     }
@@ -863,7 +874,7 @@ lbm_status lbm_add_density(lbm_ctx *c, int32_t lattice, double delta_rho_bar)
         if (lattice != -1 && k != lattice) continue;
         const LatHost &L = c->lats[k];
         CK(launch_add_density(L.lat.storage, all_desc(c), k, (long long)L.lat.nx * L.lat.ny, c->parity,
-                              (float)(delta_rho_bar / 9.0), c->stream),
+                              (float)(delta_rho_bar / (double)L.q), c->stream),
            "launch density step");
     }
     return LBM_OK;
@@ -896,7 +907,7 @@ lbm_status lbm_get_time(const lbm_ctx *c, int64_t *t)
     return LBM_OK;
 }
 
-static const char kMagic[8] = {'L', 'B', 'M', 'S', 'T', 'A', 'T', '1'};
+static const char kMagic[8] = {'L', 'B', 'M', 'S', 'T', 'A', 'T', '2'};
 
 lbm_status lbm_save(lbm_ctx *c, const char *path)
 {
@@ -910,14 +921,14 @@ lbm_status lbm_save(lbm_ctx *c, const char *path)
     ok = ok && std::fwrite(hdr, sizeof(hdr), 1, f) == 1;
     for (size_t k = 0; ok && k < c->lats.size(); ++k) {
         const LatHost &L = c->lats[k];
-        const int32_t meta[5] = {L.lat.nx, L.lat.ny, L.lat.storage, L.model, L.lat.id};
+        const int32_t meta[6] = {L.lat.nx, L.lat.ny, L.lat.storage, L.model, L.lat.id, L.lat.velocity_set};
         ok = ok && std::fwrite(meta, sizeof(meta), 1, f) == 1;
         ok = ok && std::fwrite(&L.rho0, sizeof(float), 1, f) == 1;
         const size_t eb = elem_bytes(L.lat.storage);
-        std::vector<char> raw((size_t)9 * L.lat.ny * L.lat.nx * eb);
+        std::vector<char> raw((size_t)L.q * L.lat.ny * L.lat.nx * eb);
         const char *src = c->state + L.state_off + (c->parity ? L.buf_bytes : 0);
         cudaError_t e = cudaMemcpy2DAsync(raw.data(), L.lat.nx * eb, src, L.pitch * eb, L.lat.nx * eb,
-                                          9 * (size_t)L.lat.ny, cudaMemcpyDeviceToHost, c->stream);
+                                          (size_t)L.q * L.lat.ny, cudaMemcpyDeviceToHost, c->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
         if (e != cudaSuccess) {
             std::fclose(f);
@@ -946,14 +957,14 @@ lbm_status lbm_load(lbm_ctx *c, const char *path)
     std::vector<float> rho0s;
     for (size_t k = 0; ok && k < c->lats.size(); ++k) {
         const LatHost &L = c->lats[k];
-        int32_t meta[5];
+        int32_t meta[6];
         float r0 = 0.f;
         ok = ok && std::fread(meta, sizeof(meta), 1, f) == 1 && std::fread(&r0, sizeof(float), 1, f) == 1;
         ok = ok && meta[0] == L.lat.nx && meta[1] == L.lat.ny && meta[2] == L.lat.storage && meta[3] == L.model &&
-             meta[4] == L.lat.id;
+             meta[4] == L.lat.id && meta[5] == L.lat.velocity_set;
         if (!ok) break;
         const size_t eb = elem_bytes(L.lat.storage);
-        std::vector<char> raw((size_t)9 * L.lat.ny * L.lat.nx * eb);
+        std::vector<char> raw((size_t)L.q * L.lat.ny * L.lat.nx * eb);
         ok = std::fread(raw.data(), 1, raw.size(), f) == raw.size();
         raws.push_back(std::move(raw));
         rho0s.push_back(r0);
@@ -967,7 +978,7 @@ lbm_status lbm_load(lbm_ctx *c, const char *path)
         const LatHost &L = c->lats[k];
         const size_t eb = elem_bytes(L.lat.storage);
         CK(cudaMemcpy2DAsync(c->state + L.state_off, L.pitch * eb, raws[k].data(), L.lat.nx * eb, L.lat.nx * eb,
-                             9 * (size_t)L.lat.ny, cudaMemcpyHostToDevice, c->stream),
+                             (size_t)L.q * L.lat.ny, cudaMemcpyHostToDevice, c->stream),
            "upload populations");
         c->lats[k].consumed = 0;
     }
@@ -995,11 +1006,16 @@ lbm_status lbm_set_tuning(lbm_ctx *c, int32_t mode, int32_t vec, int32_t rows, i
     if (warps < 1 || warps > 8) return fail(c, LBM_ERR_INVALID_ARG, "warps must be in [1, 8]");
     if (stages != 0 && (stages < 2 || stages > 8 || warps > 4))
         return fail(c, LBM_ERR_INVALID_ARG, "stages must be 0 (direct) or 2..8 with at most 4 warps");
-    if (stages != 0 && c->groups.size() && c->groups[0].model == LBM_MIPS && stages < 3)
-        return fail(c, LBM_ERR_INVALID_ARG, "MIPS needs at least 3 stages");
     if (stages != 0)
         for (auto &g : c->groups)
-            if (!staged_ok(c, g)) return fail(c, LBM_ERR_INVALID_ARG, "staged kernel needs nx a multiple of 16 bytes");
+            if (g.q == 9 && g.model == LBM_MIPS && stages < 3)
+                return fail(c, LBM_ERR_INVALID_ARG, "MIPS needs at least 3 stages");
+    if (stages != 0)
+        for (auto &g : c->groups)
+            if (g.q == 9 && !staged_ok(c, g))
+                return fail(c, LBM_ERR_INVALID_ARG, "staged kernel needs nx a multiple of 16 bytes");
+    for (auto &g : c->groups)
+        if (g.q == 7 && rows % 2) return fail(c, LBM_ERR_INVALID_ARG, "D2Q7 strips need an even number of rows");
     for (auto &g : c->groups) {
         if (!allowed_vec(g.storage, vec)) return fail(c, LBM_ERR_INVALID_ARG, "vec not available for this storage");
         for (int m : g.members)
@@ -1009,7 +1025,7 @@ lbm_status lbm_set_tuning(lbm_ctx *c, int32_t mode, int32_t vec, int32_t rows, i
         g.vec = vec;
         g.rows = rows;
         g.warps = warps;
-        g.stages = stages;
+        g.stages = g.q == 9 ? stages : 0;  // D2Q7 has the direct kernel only
     }
     c->tune_mode = 1;
     c->tuned = true;

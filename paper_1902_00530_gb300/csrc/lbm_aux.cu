@@ -52,15 +52,29 @@ __global__ void init_kernel(const LatDesc *desc, const InitSpecDev *specs, int d
         const double usq = ux * ux + uy * uy;
         T *base = reinterpret_cast<T *>(d.f[dst]);
         const size_t plane = (size_t)d.ny * d.pitch;
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            const double eu = vx(i) * ux + vy(i) * uy;
-            const double feq = wq_d(i) * rho * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * usq);
+        auto put = [&](int i, double feq, float shift) {
             T v;
             if constexpr (ST == ST_F32) v = (float)feq;
-            else if constexpr (ST == ST_F16) v = __double2half(feq - (double)(wq(i) * d.rho0));
-            else v = __double2bfloat16(feq - (double)(wq(i) * d.rho0));
+            else if constexpr (ST == ST_F16) v = __double2half(feq - (double)shift);
+            else v = __double2bfloat16(feq - (double)shift);
             base[i * plane + (size_t)y * d.pitch + x] = v;
+        };
+        if (d.q == 7) {
+            // Eq. (fssD2Q7): w_i rho [1 + 4 e.u + 8 (e.u)^2 - 2 u^2], e_i at (i-1) pi/3
+            const double hs3 = 0.86602540378443864676;
+            const double ex[7] = {0.0, 1.0, 0.5, -0.5, -1.0, -0.5, 0.5};
+            const double ey[7] = {0.0, 0.0, hs3, hs3, 0.0, -hs3, -hs3};
+#pragma unroll
+            for (int i = 0; i < 7; ++i) {
+                const double eu = ex[i] * ux + ey[i] * uy;
+                put(i, wq7_d(i) * rho * (1.0 + 4.0 * eu + 8.0 * eu * eu - 2.0 * usq), wq7(i) * d.rho0);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const double eu = vx(i) * ux + vy(i) * uy;
+                put(i, wq_d(i) * rho * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * usq), wq(i) * d.rho0);
+            }
         }
     }
 }
@@ -78,18 +92,29 @@ __global__ void moments_kernel(const LatDesc *desc, int lat, int src, float *rho
          c += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(c % d.nx), y = (int)(c / d.nx);
         float f[9];
+        float r, jx, jy;
+        if (d.q == 7) {
 #pragma unroll
-        for (int i = 0; i < 9; ++i) f[i] = load_one<ST>(base + i * plane + (size_t)y * d.pitch + x, wq(i) * d.rho0);
-        const float r = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
-        const float jx = (f[1] + f[5] + f[8]) - (f[3] + f[6] + f[7]);
-        const float jy = (f[2] + f[5] + f[6]) - (f[4] + f[7] + f[8]);
+            for (int i = 0; i < 7; ++i)
+                f[i] = load_one<ST>(base + i * plane + (size_t)y * d.pitch + x, wq7(i) * d.rho0);
+            r = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + f[6]);
+            jx = (f[1] - f[4]) + 0.5f * ((f[2] + f[6]) - (f[3] + f[5]));
+            jy = 0.86602540378443865f * ((f[2] + f[3]) - (f[5] + f[6]));
+        } else {
+#pragma unroll
+            for (int i = 0; i < 9; ++i)
+                f[i] = load_one<ST>(base + i * plane + (size_t)y * d.pitch + x, wq(i) * d.rho0);
+            r = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+            jx = (f[1] + f[5] + f[8]) - (f[3] + f[6] + f[7]);
+            jy = (f[2] + f[5] + f[6]) - (f[4] + f[7] + f[8]);
+        }
         rho[c] = r;
         ux[c] = r > 0.f ? jx / r : 0.f;
         uy[c] = r > 0.f ? jy / r : 0.f;
     }
 }
 
-// Stored state <-> dense FP32 populations [9][ny][nx].
+// Stored state <-> dense FP32 populations [q][ny][nx].
 template <int ST>
 __global__ void export_kernel(const LatDesc *desc, int lat, int src, float *out)
 {
@@ -98,12 +123,12 @@ __global__ void export_kernel(const LatDesc *desc, int lat, int src, float *out)
     const T *base = reinterpret_cast<const T *>(d.f[src]);
     const size_t plane = (size_t)d.ny * d.pitch;
     const long long n = (long long)d.nx * d.ny;
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < 9 * n;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < (long long)d.q * n;
          c += (long long)gridDim.x * blockDim.x) {
         const int i = (int)(c / n);
         const long long r = c % n;
         const int x = (int)(r % d.nx), y = (int)(r / d.nx);
-        out[c] = Store<ST>::get(base[i * plane + (size_t)y * d.pitch + x], wq(i) * d.rho0);
+        out[c] = Store<ST>::get(base[i * plane + (size_t)y * d.pitch + x], pop_shift(d.q, i, d.rho0));
     }
 }
 
@@ -115,12 +140,12 @@ __global__ void import_kernel(const LatDesc *desc, int lat, int dst, const float
     T *base = reinterpret_cast<T *>(d.f[dst]);
     const size_t plane = (size_t)d.ny * d.pitch;
     const long long n = (long long)d.nx * d.ny;
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < 9 * n;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < (long long)d.q * n;
          c += (long long)gridDim.x * blockDim.x) {
         const int i = (int)(c / n);
         const long long r = c % n;
         const int x = (int)(r % d.nx), y = (int)(r / d.nx);
-        base[i * plane + (size_t)y * d.pitch + x] = Store<ST>::put(in[c], wq(i) * d.rho0);
+        base[i * plane + (size_t)y * d.pitch + x] = Store<ST>::put(in[c], pop_shift(d.q, i, d.rho0));
     }
 }
 
@@ -133,13 +158,13 @@ __global__ void add_density_kernel(const LatDesc *desc, int lat, int buf, float 
     T *base = reinterpret_cast<T *>(d.f[buf]);
     const size_t plane = (size_t)d.ny * d.pitch;
     const long long n = (long long)d.nx * d.ny;
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < 9 * n;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < (long long)d.q * n;
          c += (long long)gridDim.x * blockDim.x) {
         const int i = (int)(c / n);
         const long long r = c % n;
         const int x = (int)(r % d.nx), y = (int)(r / d.nx);
         T *p = base + i * plane + (size_t)y * d.pitch + x;
-        const float shift = wq(i) * d.rho0;
+        const float shift = pop_shift(d.q, i, d.rho0);
         *p = Store<ST>::put(__fadd_rn(Store<ST>::get(*p, shift), per_population), shift);
     }
 }
@@ -306,7 +331,7 @@ cudaError_t launch_moments(int storage, const LatDesc *desc, int lat, long long 
 cudaError_t launch_export(int storage, const LatDesc *desc, int lat, long long cells, int src, float *out,
                           cudaStream_t s)
 {
-    const int g = grid_for(9 * cells, 256);
+    const int g = grid_for(9 * cells, 256);  // enough for q <= 9
     if (storage == ST_F32) export_kernel<ST_F32><<<g, 256, 0, s>>>(desc, lat, src, out);
     else if (storage == ST_F16) export_kernel<ST_F16><<<g, 256, 0, s>>>(desc, lat, src, out);
     else export_kernel<ST_BF16><<<g, 256, 0, s>>>(desc, lat, src, out);
@@ -316,7 +341,7 @@ cudaError_t launch_export(int storage, const LatDesc *desc, int lat, long long c
 cudaError_t launch_import(int storage, const LatDesc *desc, int lat, long long cells, int dst, const float *in,
                           cudaStream_t s)
 {
-    const int g = grid_for(9 * cells, 256);
+    const int g = grid_for(9 * cells, 256);  // enough for q <= 9
     if (storage == ST_F32) import_kernel<ST_F32><<<g, 256, 0, s>>>(desc, lat, dst, in);
     else if (storage == ST_F16) import_kernel<ST_F16><<<g, 256, 0, s>>>(desc, lat, dst, in);
     else import_kernel<ST_BF16><<<g, 256, 0, s>>>(desc, lat, dst, in);
@@ -326,7 +351,7 @@ cudaError_t launch_import(int storage, const LatDesc *desc, int lat, long long c
 cudaError_t launch_add_density(int storage, const LatDesc *desc, int lat, long long cells, int buf, float per_pop,
                                cudaStream_t s)
 {
-    const int g = grid_for(9 * cells, 256);
+    const int g = grid_for(9 * cells, 256);  // enough for q <= 9
     if (storage == ST_F32) add_density_kernel<ST_F32><<<g, 256, 0, s>>>(desc, lat, buf, per_pop);
     else if (storage == ST_F16) add_density_kernel<ST_F16><<<g, 256, 0, s>>>(desc, lat, buf, per_pop);
     else add_density_kernel<ST_BF16><<<g, 256, 0, s>>>(desc, lat, buf, per_pop);

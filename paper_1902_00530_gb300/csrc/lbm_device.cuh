@@ -43,13 +43,21 @@ static_assert(reverse_of(1) == 3 && reverse_of(2) == 4 && reverse_of(3) == 1 &&
                   reverse_of(7) == 5 && reverse_of(8) == 6,
               "D2Q9 reverse directions");
 
+// D2Q7 weights (Sec. 2): 1/2 for the rest population, 1/12 for the six moving
+// ones; velocities e_i = (cos((i-1) pi/3), sin((i-1) pi/3)).
+__host__ __device__ constexpr float wq7(int i) { return i == 0 ? 0.5f : 1.0f / 12.0f; }
+__host__ __device__ constexpr double wq7_d(int i) { return i == 0 ? 0.5 : 1.0 / 12.0; }
+
+// Storage shift w_i rho0 of population i on a lattice with q populations.
+__host__ __device__ inline float pop_shift(int q, int i, float rho0) { return (q == 7 ? wq7(i) : wq(i)) * rho0; }
+
 enum { MODEL_PASSIVE = 0, MODEL_MIPS = 1, MODEL_CIL = 2 };
 enum { ST_F32 = 0, ST_F16 = 1, ST_BF16 = 2 };
 enum { DEVERR_NUMERIC = 1u, DEVERR_TIMEOUT = 2u };
 
 // Per-lattice descriptor, resident in device memory for the whole run.
 struct LatDesc {
-    void *f[2];          // the two population buffers, [9][ny][pitch] of the storage type
+    void *f[2];          // the two population buffers, [q][ny][pitch] of the storage type
     double *scal;        // [nstrips][5] per-strip sums: rho, jx, jy, rho^2, |j|
     double *colp;        // [nsy][nx] per-strip-row column sums of rho
     double *rowp;        // [nsx][ny] per-strip-column row sums of rho
@@ -59,7 +67,9 @@ struct LatDesc {
     unsigned *counters;  // [2]: samples written, finaliser arrivals
     int nx, ny, pitch, id;
     int nsx, nsy, rows, block_begin;
-    int ring_cap, nchunk, pad0, pad1;
+    int ring_cap, nchunk;
+    int q;               // populations per site: 9 (D2Q9) or 7 (D2Q7)
+    int pad1;
     float omega;         // 1/tau
     float sigma_q;       // 2 sigma: noise scale of u in [1, 2) (0 = no noise)
     float C, inv_rho_star, rho_star, u_max, u_max2, A, B;

@@ -16,7 +16,13 @@ cudaError_t launch_observe_f32(int vec, const StepArgs &a, int blocks, int warps
 cudaError_t launch_observe_f16(int vec, const StepArgs &a, int blocks, int warps, cudaStream_t stream);
 cudaError_t launch_observe_bf16(int vec, const StepArgs &a, int blocks, int warps, cudaStream_t stream);
 
-// auxiliary kernels (lbm_aux.cu)
+// the D2Q7 step / observe kernels (lbm_step_q7.cu; storage an ST_* value)
+cudaError_t launch_step_q7(int storage, int model, int vec, bool sample, const StepArgs &a, int blocks, int warps,
+                           cudaStream_t stream);
+cudaError_t launch_observe_q7(int storage, int vec, const StepArgs &a, int blocks, int warps, cudaStream_t stream);
+
+// auxiliary kernels (lbm_aux.cu); the lattice's q comes from its descriptor,
+// so `cells` counts sites and q * cells elements are touched
 size_t init_spec_bytes();
 void pack_init_spec(void *dst, double rho_mean, double rho_amp, int u_kind, double u_amp, double ux0,
                     double uy0, double A, double B);

@@ -168,20 +168,11 @@ __device__ __forceinline__ V vdensity(const V f[9])
     return vadd(vadd(vadd(vadd(f[0], f[1]), vadd(f[2], f[3])), vadd(vadd(f[4], f[5]), vadd(f[6], f[7]))), f[8]);
 }
 
-// Steps 2-5: moments of f*, u*, f^SS, BGK, noise.  Returns rho (for step 6).
+// Step 3: the steady-state velocity u* of the model from rho, u and (MIPS)
+// grad rho; independent of the lattice.
 template <int MODEL, typename V>
-__device__ __forceinline__ V collide_v(V f[9], V gx, V gy, const SiteParams &d, bool noise, const V eta[9],
-                                       const V *rho_known = nullptr)
+__device__ __forceinline__ void ustar_v(V rho, V ux, V uy, V gx, V gy, const SiteParams &d, V &sx, V &sy)
 {
-    // step 2: moments of f* (rho may come precomputed, bitwise equal: the MIPS
-    // density window sums the same nine values in the same order)
-    const V rho = rho_known ? *rho_known : vdensity(f);
-    const V jx = vsub(vadd(vadd(f[1], f[5]), f[8]), vadd(vadd(f[3], f[6]), f[7]));
-    const V jy = vsub(vadd(vadd(f[2], f[5]), f[6]), vadd(vadd(f[4], f[7]), f[8]));
-    const V inv = vmap(rho, [](float r) { return r > 0.f ? __frcp_rn(r) : 0.f; });  // u = 0 where rho <= 0
-    const V ux = vmul(jx, inv), uy = vmul(jy, inv);
-    // step 3: u* of the model
-    V sx, sy;
     if constexpr (MODEL == MODEL_PASSIVE) {
         sx = ux;
         sy = uy;
@@ -207,6 +198,23 @@ __device__ __forceinline__ V collide_v(V f[9], V gx, V gy, const SiteParams &d, 
         sx = vmul(ux, sc);
         sy = vmul(uy, sc);
     }
+}
+
+// Steps 2-5: moments of f*, u*, f^SS, BGK, noise.  Returns rho (for step 6).
+template <int MODEL, typename V>
+__device__ __forceinline__ V collide_v(V f[9], V gx, V gy, const SiteParams &d, bool noise, const V eta[9],
+                                       const V *rho_known = nullptr)
+{
+    // step 2: moments of f* (rho may come precomputed, bitwise equal: the MIPS
+    // density window sums the same nine values in the same order)
+    const V rho = rho_known ? *rho_known : vdensity(f);
+    const V jx = vsub(vadd(vadd(f[1], f[5]), f[8]), vadd(vadd(f[3], f[6]), f[7]));
+    const V jy = vsub(vadd(vadd(f[2], f[5]), f[6]), vadd(vadd(f[4], f[7]), f[8]));
+    const V inv = vmap(rho, [](float r) { return r > 0.f ? __frcp_rn(r) : 0.f; });  // u = 0 where rho <= 0
+    const V ux = vmul(jx, inv), uy = vmul(jy, inv);
+    // step 3: u* of the model
+    V sx, sy;
+    ustar_v<MODEL, V>(rho, ux, uy, gx, gy, d, sx, sy);
     // step 3 (cont.): f^SS = w rho [1 + 3 e.u* + 9/2 (e.u*)^2 - 3/2 |u*|^2].  The
     // rest population takes rho minus the moving ones: identical in exact
     // arithmetic, but the FP32 weights sum to 1 + 7.5e-9, which would otherwise
@@ -361,20 +369,20 @@ __device__ __forceinline__ void mips_gradients(const float rm[VEC + 2], const fl
     }
 }
 
-// Observable sums of one stored row (sites x0..x0+VEC-1): per-thread FP64
-// accumulators for the strip's column sums and five scalar sums, and the
-// row's density total reduced over the warp.
+// Observable sums of one stored row (sites x0..x0+VEC-1) from its moments
+// rho and j = rho u: per-thread FP64 accumulators for the strip's column sums
+// and five scalar sums, and the row's density total reduced over the warp.
+// Lattice-independent.
 template <int VEC>
-__device__ __forceinline__ void observe_row(const float g[9][VEC], bool valid, double col[VEC],
-                                            double acc[5], double *row_out, int lane)
+__device__ __forceinline__ void observe_moments(const float rv[VEC], const float jxv[VEC], const float jyv[VEC],
+                                                bool valid, double col[VEC], double acc[5], double *row_out,
+                                                int lane)
 {
     float rs = 0.f, js = 0.f, jxs = 0.f, jys = 0.f, r2s = 0.f;
     if (valid) {
 #pragma unroll
         for (int j = 0; j < VEC; ++j) {
-            const float r = density<VEC>(g, j);
-            const float jx = (g[1][j] + g[5][j] + g[8][j]) - (g[3][j] + g[6][j] + g[7][j]);
-            const float jy = (g[2][j] + g[5][j] + g[6][j]) - (g[4][j] + g[7][j] + g[8][j]);
+            const float r = rv[j], jx = jxv[j], jy = jyv[j];
             col[j] += (double)r;
             rs += r;
             jxs += jx;
@@ -392,6 +400,21 @@ __device__ __forceinline__ void observe_row(const float g[9][VEC], bool valid, d
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(FULL, t, o);
     if (lane == 0) *row_out = t;
+}
+
+// The same for a stored D2Q9 row.
+template <int VEC>
+__device__ __forceinline__ void observe_row(const float g[9][VEC], bool valid, double col[VEC],
+                                            double acc[5], double *row_out, int lane)
+{
+    float rv[VEC], jxv[VEC], jyv[VEC];
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) {
+        rv[j] = density<VEC>(g, j);
+        jxv[j] = (g[1][j] + g[5][j] + g[8][j]) - (g[3][j] + g[6][j] + g[7][j]);
+        jyv[j] = (g[2][j] + g[5][j] + g[6][j]) - (g[4][j] + g[7][j] + g[8][j]);
+    }
+    observe_moments<VEC>(rv, jxv, jyv, valid, col, acc, row_out, lane);
 }
 
 template <int VEC>

@@ -15,9 +15,10 @@ def split_preset(name: str, **overrides):
 
 
 def gpu_sim(model, d, nx, ny, seed, spec, storage="f32", lattice_id=0, tuning=None,
-            sample_every=0, ring=0, graphs=True):
+            sample_every=0, ring=0, graphs=True, q=9):
     from paper_1902_00530_gb300 import Lattice, Simulation
-    sim = Simulation([Lattice(nx, ny, storage, lattice_id)], [model], [d], sample_every=sample_every,
+    vs = "d2q7" if q == 7 else "d2q9"
+    sim = Simulation([Lattice(nx, ny, storage, lattice_id, vs)], [model], [d], sample_every=sample_every,
                      ring_capacity=ring)
     if tuning is not None:
         sim.set_tuning(1, *tuning)
@@ -34,16 +35,28 @@ def gpu_run(model, d, nx, ny, steps, seed, spec, **kw):
     return f
 
 
-def oracle_run(model, d, nx, ny, steps, seed, spec, bits=64, lattice_id=0):
+def oracle_run(model, d, nx, ny, steps, seed, spec, bits=64, lattice_id=0, q=9):
     p = O.params(**d)
-    f = O.init(nx, ny, seed, lattice_id=lattice_id, **spec, prm=p, bits=bits)
-    return O.run(f, model, p, seed, 0, steps, lattice_id=lattice_id, bits=bits)
+    init, run = (O.init7, O.run7) if q == 7 else (O.init, O.run)
+    f = init(nx, ny, seed, lattice_id=lattice_id, **spec, prm=p, bits=bits)
+    return run(f, model, p, seed, 0, steps, lattice_id=lattice_id, bits=bits)
+
+
+def moments(f):
+    """(rho, ux, uy) of a D2Q9 or D2Q7 population array, in FP64."""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    return O.moments7(f) if f.shape[0] == 7 else O.moments(f)
+
+
+def observables(f, B=0.0):
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    return O.observables7(f, B=B) if f.shape[0] == 7 else O.observables(f, B=B)
 
 
 def errors(f, ref):
     """e_rho = max|rho - rho_ref| / mean rho_ref; e_u = max|u - u_ref| / max(max|u_ref|, 1e-3)."""
-    r, ux, uy = O.moments(np.ascontiguousarray(f, dtype=np.float64))
-    rr, uxr, uyr = O.moments(np.ascontiguousarray(ref, dtype=np.float64))
+    r, ux, uy = moments(f)
+    rr, uxr, uyr = moments(ref)
     e_rho = np.abs(r - rr).max() / rr.mean()
     du = max(np.abs(ux - uxr).max(), np.abs(uy - uyr).max())
     e_u = du / max(np.hypot(uxr, uyr).max(), 1e-3)
@@ -53,12 +66,14 @@ def errors(f, ref):
 def assert_parity(got, model, d, nx, ny, steps, seed, spec, strict=1e-5, lattice_id=0):
     """Pass if the GPU result is within `strict` of the FP64 oracle, or, where
     rounding differences grow (linearly unstable or marginal regimes), within
-    4x the oracle's own FP32-vs-FP64 divergence (+1e-6)."""
-    ref = oracle_run(model, d, nx, ny, steps, seed, spec, lattice_id=lattice_id)
+    4x the oracle's own FP32-vs-FP64 divergence (+1e-6).  The lattice (D2Q9 or
+    D2Q7) follows from the shape of `got`."""
+    q = got.shape[0]
+    ref = oracle_run(model, d, nx, ny, steps, seed, spec, lattice_id=lattice_id, q=q)
     e = errors(got, ref)
     if max(e) <= strict:
         return e, None
-    f32 = oracle_run(model, d, nx, ny, steps, seed, spec, bits=32, lattice_id=lattice_id).astype(np.float64)
+    f32 = oracle_run(model, d, nx, ny, steps, seed, spec, bits=32, lattice_id=lattice_id, q=q).astype(np.float64)
     ei = errors(f32, ref)
     assert e[0] <= 4 * ei[0] + 1e-6 and e[1] <= 4 * ei[1] + 1e-6, (e, ei)
     return e, ei

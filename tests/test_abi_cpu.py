@@ -37,9 +37,9 @@ def test_library_exports_every_declared_symbol(lib):
         assert name in _abi.SIGNATURES, f"binding lacks {name}"
 
 
-def _lat(nx=8, ny=8, storage=0, id_=0):
+def _lat(nx=8, ny=8, storage=0, id_=0, vs=0):
     from paper_1902_00530_gb300 import _abi
-    return _abi.lbm_lattice(nx, ny, storage, id_)
+    return _abi.lbm_lattice(nx, ny, storage, id_, vs)
 
 
 def _prm(**kw):
@@ -52,6 +52,7 @@ def _prm(**kw):
     dict(prm=dict(tau=0.5)), dict(prm=dict(sigma=-1.0)), dict(prm=dict(tau=float("nan"))),
     dict(model=7), dict(model=1, prm=dict(rho_star=0.0)), dict(prm=dict(rho0=-1.0)),
     dict(prm=dict(A=float("inf")), model=2),
+    dict(lat=dict(vs=2)), dict(lat=dict(vs=1, ny=7)),  # unknown velocity set; D2Q7 with odd ny
 ])
 def test_create_rejects_bad_arguments(lib, bad):
     ctx = ctypes.c_void_p(123)
@@ -120,3 +121,26 @@ def test_python_binding_refuses_without_library(tmp_path):
             _abi.load(str(tmp_path / "missing.so"))
         finally:
             _abi._lib = _abi._lib_saved
+
+
+def test_d2q7_buffers_and_tuning(lib):
+    """A D2Q7 lattice holds seven planes per buffer; its strips need an even
+    number of rows; the staged kernel (D2Q9 only) is not required of it."""
+    from paper_1902_00530_gb300 import _abi
+    lats = (_abi.lbm_lattice * 2)(_abi.lbm_lattice(64, 30, 0, 0, 1), _abi.lbm_lattice(64, 30, 0, 1, 0))
+    mods = (ctypes.c_int * 2)(2, 2)
+    prms = (_abi.lbm_params * 2)(*[_prm(tau=1.0, A=0.06845, B=0.3) for _ in range(2)])
+    ctx = ctypes.c_void_p()
+    assert lib.lbm_create_batch(2, lats, mods, prms, ctypes.byref(ctx)) == 0
+    sb = ctypes.c_size_t(); cb = ctypes.c_size_t()
+    assert lib.lbm_buffer_bytes(ctx, ctypes.byref(sb), ctypes.byref(cb)) == 0
+    plane = 30 * 64 * 4
+    assert 2 * (7 + 9) * plane <= sb.value < 2 * (7 + 9) * plane + 4 * 256
+    assert lib.lbm_set_tuning(ctx, 1, 2, 17, 4, 0) == 1   # odd rows: D2Q7 needs even
+    assert lib.lbm_set_tuning(ctx, 1, 2, 32, 2, 3) == 0   # stages apply to the D2Q9 member only
+    v, r, w, st = (ctypes.c_int32() for _ in range(4))
+    assert lib.lbm_get_tuning(ctx, 0, *[ctypes.byref(x) for x in (v, r, w, st)]) == 0
+    assert (v.value, r.value, st.value) == (2, 32, 0)
+    assert lib.lbm_get_tuning(ctx, 1, *[ctypes.byref(x) for x in (v, r, w, st)]) == 0
+    assert st.value == 3
+    lib.lbm_destroy(ctx)

@@ -218,11 +218,13 @@ def test_staged_kernel_small_and_ragged(nx, ny):
 
 # ---------------------------------------------------------- noise stream ---
 def _write_state_file(path, f, t, seed, lattice_id, model, storage=0, rho0=1.0):
-    nine, ny, nx = f.shape
+    """A state file as lbm_save writes it (one lattice): magic, (count, t,
+    seed), (nx, ny, storage, model, id, velocity set), rho0, raw populations."""
+    q, ny, nx = f.shape
     with open(path, "wb") as fh:
-        fh.write(b"LBMSTAT1")
+        fh.write(b"LBMSTAT2")
         fh.write(struct.pack("<2qQ", 1, t, seed))
-        fh.write(struct.pack("<5i", nx, ny, storage, model, lattice_id))
+        fh.write(struct.pack("<6i", nx, ny, storage, model, lattice_id, 1 if q == 7 else 0))
         fh.write(struct.pack("<f", rho0))
         fh.write(np.ascontiguousarray(f, dtype=np.float32).tobytes())
 

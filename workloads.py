@@ -17,6 +17,10 @@ about 1, so each paper preset appears twice:
 Noise amplitude on D2Q9.  The paper's noise gives <h_x^2> = c^2 sigma^2 on D2Q7
 (Sec. 7); with the same uniform eta~ on D2Q9 the momentum noise is 2 sigma^2,
 so a paper sigma is carried over as sigma / sqrt(2).
+
+D2Q7 presets (``*_Q7_*``) are for the paper's own triangular lattice, where
+its numbers apply unchanged: ``*_Q7_PAPER`` as printed (run at the paper's
+mean densities) and ``*_Q7_RHO1`` rescaled to rho ~ 1 as above.
 """
 from __future__ import annotations
 
@@ -49,7 +53,22 @@ PRESETS = {
                      rho_star=1.0, u_max=1.0, A=_CIL_A * _CIL_RHOBAR ** 2, B=_CIL_B),
     "PASSIVE": dict(model="passive", tau=1.0, sigma=0.0, C=0.0, rho_star=1.0, u_max=1.0,
                     A=0.0, B=0.0),
+    # D2Q7: the paper's lattice, its sigma as printed
+    "MIPS_Q7_PAPER": dict(model="mips", tau=1.0, sigma=_MIPS_SIGMA, C=_MIPS_C, rho_star=_MIPS_RHO_STAR,
+                          u_max=_MIPS_UMAX, A=0.0, B=0.0),
+    "MIPS_Q7_RHO1": dict(model="mips", tau=1.0, sigma=_MIPS_SIGMA / _MIPS_RHOBAR, C=_MIPS_C * _MIPS_RHOBAR,
+                         rho_star=_MIPS_RHO_STAR / _MIPS_RHOBAR, u_max=_MIPS_UMAX, A=0.0, B=0.0),
+    "CIL_Q7_PAPER": dict(model="cil", tau=1.0, sigma=_CIL_SIGMA, C=0.0, rho_star=1.0, u_max=1.0,
+                         A=_CIL_A, B=_CIL_B),
+    "CIL_Q7_RHO1": dict(model="cil", tau=1.0, sigma=_CIL_SIGMA / _CIL_RHOBAR, C=0.0, rho_star=1.0,
+                        u_max=1.0, A=_CIL_A * _CIL_RHOBAR ** 2, B=_CIL_B),
 }
+
+# the paper's mean densities for its D2Q7 runs (App. C.1 MIPS phase diagram;
+# App. C.2 CIL homogeneous-ordered snapshot) and boxes (App. C)
+MIPS_RHOBAR_PAPER, CIL_RHOBAR_PAPER = _MIPS_RHOBAR, _CIL_RHOBAR
+BOX_CIL_PAPER = (180, 60)
+BOX_MIPS_PHASE_PAPER = (90, 30)
 
 
 def preset(name: str, **overrides) -> dict:
