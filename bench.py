@@ -30,7 +30,13 @@ sys.path.insert(0, ROOT)
 METRIC = "GLUPS & % HBM roofline; batched/16-bit-storage vs plain FP32 at stated error"
 UNIT = "GLUPS"
 BYTES_PER_UPDATE = {"f32": 72, "f16s": 36, "bf16s": 36}   # 9 reads + 9 writes per site
-KERNEL_SOURCES = ["paper_1902_00530_gb300/csrc/lbm_step.cuh", "paper_1902_00530_gb300/csrc/lbm_device.cuh"]
+
+
+def bytes_per_update(storage: str, q: int = 9) -> int:
+    """Algorithmic HBM bytes of one site update: q populations read and written."""
+    return BYTES_PER_UPDATE[storage] * q // 9
+KERNEL_SOURCES = ["paper_1902_00530_gb300/csrc/lbm_step.cuh", "paper_1902_00530_gb300/csrc/lbm_step_staged.cuh",
+                  "paper_1902_00530_gb300/csrc/lbm_step_q7.cuh", "paper_1902_00530_gb300/csrc/lbm_device.cuh"]
 
 
 def kernel_hash() -> str:
@@ -164,6 +170,11 @@ def workload_spec(name: str):
         d = W.preset("CIL_RHO1")
         return dict(nx=1024, ny=1024, model=d.pop("model"), params=d, init=W.INIT_CONFIG2, sample_every=100,
                     seed=W.seed(2), label="cil_rho1_1024x1024")
+    if name in ("mips7_8192", "mips7_4096"):  # the paper's D2Q7 lattice, same physics and sizes
+        n = 8192 if name == "mips7_8192" else 4096
+        d = W.preset("MIPS_Q7_RHO1")
+        return dict(nx=n, ny=n, model=d.pop("model"), params=d, init=W.INIT_CONFIG1, sample_every=100,
+                    seed=W.seed(3), label=f"mips_q7_rho1_{n}x{n}", velocity_set="d2q7")
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -177,7 +188,9 @@ def run_gpu(args, world, rank, local):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     wl = workload_spec(args.workload)
     storage = args.storage
-    sim = Simulation([Lattice(wl["nx"], wl["ny"], storage, rank)], [wl["model"]], [wl["params"]],
+    vs = wl.get("velocity_set", "d2q9")
+    q = 7 if vs == "d2q7" else 9
+    sim = Simulation([Lattice(wl["nx"], wl["ny"], storage, rank, vs)], [wl["model"]], [wl["params"]],
                      sample_every=wl["sample_every"], ring_capacity=max(16, args.steps // wl["sample_every"] + 4))
     sim.init(wl["seed"], [wl["init"]])
     if args.shape:
@@ -219,12 +232,12 @@ def run_gpu(args, world, rank, local):
     # ---------------- roofline of the dominant kernel (the fused step) -------
     peak, peak_kind = measured_peak()
     step_avg_ms = prof["step_ms"] / max(prof["step_launches"], 1)
-    achieved = BYTES_PER_UPDATE[storage] * cells / (step_avg_ms * 1e-3) / 1e9
+    achieved = bytes_per_update(storage, q) * cells / (step_avg_ms * 1e-3) / 1e9
     traffic = ncu_traffic(f"{wl['label']}_{storage}")
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic, "peak_source": peak_kind,
-                "algorithmic_bytes_per_launch": BYTES_PER_UPDATE[storage] * cells,
-                "kernel": "lbm::step_kernel", "avg_launch_ms": round(step_avg_ms, 5),
+                "algorithmic_bytes_per_launch": bytes_per_update(storage, q) * cells,
+                "kernel": "lbm::step_kernel_q7" if q == 7 else "lbm::step_kernel", "avg_launch_ms": round(step_avg_ms, 5),
                 "step_kernel_share": round(prof["step_ms"] / max(prof["step_ms"] + prof["other_ms"], 1e-9), 4),
                 "frac_of_8TBps": round(achieved / 8000.0, 4)}
 
@@ -279,7 +292,8 @@ def secondary_lines(args, wl):
         return cells * steps / (e0.elapsed_time(e1) * 1e-3) / 1e9
 
     for st in ("f16s", "bf16s"):
-        sim = Simulation([Lattice(wl["nx"], wl["ny"], st)], [wl["model"]], [wl["params"]],
+        sim = Simulation([Lattice(wl["nx"], wl["ny"], st, 0, wl.get("velocity_set", "d2q9"))], [wl["model"]],
+                         [wl["params"]],
                          sample_every=wl["sample_every"], ring_capacity=16)
         sim.init(wl["seed"], [wl["init"]])
         out[f"{st}_glups"] = round(time_sim(sim, wl["nx"] * wl["ny"], steps), 2)
@@ -315,7 +329,29 @@ def secondary_lines(args, wl):
     sim.init(W.seed(5), specs)
     out["ragged64_bf16s_glups"] = round(time_sim(sim, sum(s * s for s, _ in rag), steps), 2)
     sim.close()
+    del sim
+    torch.cuda.empty_cache()
+    # the paper's own lattice: D2Q7 at the same size and physics (56 B per FP32 update)
+    if wl.get("velocity_set", "d2q9") == "d2q9" and wl["nx"] == 8192:
+        w7 = workload_spec("mips7_8192")
+        peak, _ = measured_peak()
+        for st in ("f32", "bf16s"):
+            sim = Simulation([Lattice(w7["nx"], w7["ny"], st, 0, "d2q7")], [w7["model"]], [w7["params"]],
+                             sample_every=w7["sample_every"], ring_capacity=16)
+            sim.init(w7["seed"], [w7["init"]])
+            g = time_sim(sim, w7["nx"] * w7["ny"], steps)
+            out[f"d2q7_mips_8192_{st}_glups"] = round(g, 2)
+            out[f"d2q7_mips_8192_{st}_frac_hbm"] = round(g * bytes_per_update(st, 7) / peak, 4)
+            sim.close()
+            del sim
+            torch.cuda.empty_cache()
     return out
+
+
+def _oracle_pair(wl):
+    """The oracle's (init, run) for the workload's lattice."""
+    import oracle as O
+    return (O.init7, O.run7) if wl.get("velocity_set") == "d2q7" else (O.init, O.run)
 
 
 def cpu_baseline(wl, budget_s: float = 15.0):
@@ -323,13 +359,14 @@ def cpu_baseline(wl, budget_s: float = 15.0):
     window of the same workload (same seed, parameters and global
     coordinates), stepped until about budget_s seconds have passed."""
     import oracle as O
+    init, run = _oracle_pair(wl)
     n = 512
     p = O.params(**wl["params"])
     win = (0, 0, wl["nx"], wl["ny"])
-    f = O.init(n, n, wl["seed"], **wl["init"], prm=p, window=win)
+    f = init(n, n, wl["seed"], **wl["init"], prm=p, window=win)
     steps, t0 = 0, time.perf_counter()
     while time.perf_counter() - t0 < budget_s:
-        f = O.run(f, wl["model"], p, wl["seed"], steps, 5, window=win)
+        f = run(f, wl["model"], p, wl["seed"], steps, 5, window=win)
         steps += 5
     dt = time.perf_counter() - t0
     return {"value": round(n * n * steps / dt / 1e9, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -347,12 +384,13 @@ def run_reference(args, world, rank):
     n = 512
     while n > 64 and n * n * (args.steps + args.warmup) > 3.0e8:
         n //= 2
+    init, run = _oracle_pair(wl)
     p = O.params(**wl["params"])
     win = (0, 0, wl["nx"], wl["ny"])
-    f = O.init(n, n, wl["seed"], **wl["init"], prm=p, window=win)
-    f = O.run(f, wl["model"], p, wl["seed"], 0, args.warmup, window=win)
+    f = init(n, n, wl["seed"], **wl["init"], prm=p, window=win)
+    f = run(f, wl["model"], p, wl["seed"], 0, args.warmup, window=win)
     t0 = time.perf_counter()
-    f = O.run(f, wl["model"], p, wl["seed"], args.warmup, args.steps, window=win)
+    f = run(f, wl["model"], p, wl["seed"], args.warmup, args.steps, window=win)
     dt = time.perf_counter() - t0
     value = n * n * args.steps / dt / 1e9
     line = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world,

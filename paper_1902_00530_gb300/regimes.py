@@ -43,21 +43,28 @@ def mips_separated(drho: float, density_scale: float = 1.0) -> bool:
 
 
 def density_sweep(sim, rho_start: float, rho_end: float, delta: float, t_sample: int, lattice: int = -1,
-                  t_sample_of=None):
+                  t_sample_of=None, sample=None):
     """App. C.3: from mean density rho_start, repeat {step t_sample steps; sample
     the observables; add delta to the mean density} until rho_end is passed.
     ``t_sample_of(rho)`` may vary the interval with the density (the paper uses
-    500 steps above rho-bar 0.2 and 1500 below).  Returns [(rho_bar, obs)]
-    for the lattice (lattice 0 if -1)."""
+    500 steps above rho-bar 0.2 and 1500 below).  ``lattice`` is the lattice
+    whose density changes (-1: all).  Returns [(rho_bar, obs)] with obs the
+    record of lattice ``sample`` if that is an int, a list of records if it is
+    a sequence of lattices (the paper's repeated runs, as one batch), and of
+    ``lattice`` (0 if -1) by default."""
     if delta == 0 or (rho_end - rho_start) * delta < 0:
         raise ValueError("delta must move rho_start towards rho_end")
     out = []
     rho = rho_start
     k = 0
-    target = lattice if lattice >= 0 else 0
+    if sample is None:
+        sample = lattice if lattice >= 0 else 0
     while (rho - rho_end) * (1 if delta > 0 else -1) <= 1e-12:
         sim.step(t_sample_of(rho) if t_sample_of else t_sample)
-        out.append((rho, sim.observables(target)))
+        if isinstance(sample, int):
+            out.append((rho, sim.observables(sample)))
+        else:
+            out.append((rho, [sim.observables(k_) for k_ in sample]))
         sim.add_density(delta, lattice)
         k += 1
         rho = rho_start + k * delta

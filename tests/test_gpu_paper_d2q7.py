@@ -1,0 +1,96 @@
+"""The paper's qualitative results on its own lattice (D2Q7), as GPU smoke
+tests: the CIL regime sequence of the increasing-density run of Fig.
+Hysteresis (a), and the noise strength at which MIPS stops (App. C.1).  Parameters, box and procedure are the paper's, read from
+tests/golden/paper_parameters.json; the regimes are classified with App. D's
+cutoffs (paper_1902_00530_gb300.regimes)."""
+import json
+import os
+from collections import Counter
+
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+G = json.load(open(os.path.join(HERE, "golden", "paper_parameters.json")))
+
+
+def test_cil_density_sweep_reproduces_paper_regimes():
+    """Increasing run at A = 2 (App. C.2-C.3) on the 180 x 60 D2Q7 box, eight
+    independent runs in one batch.  At the paper's four snapshot densities
+    (HD 0.105, B 0.1425, HO 0.185, RB 0.2875) a majority of the runs is in the
+    paper's regime, and the majority regime along the sweep goes HD, B, HO,
+    RB and back to HD (the second disordered region at high density, Sec. 4),
+    in that order."""
+    from paper_1902_00530_gb300 import Lattice, Simulation
+    from paper_1902_00530_gb300 import regimes as R
+    proc, hyst = G["cil_hysteresis_procedure"], G["cil_hysteresis"]
+    d = W.preset("CIL_Q7_PAPER")
+    model = d.pop("model")
+    nx, ny = G["boxes"]["cil"]
+    runs = 8
+    sim = Simulation([Lattice(nx, ny, "f32", k, "d2q7") for k in range(runs)], [model] * runs, [d] * runs)
+    sim.init(W.seed(11), [dict(W.INIT_PAPER_CIL, rho_mean=proc["rho_start"])] * runs)
+    sim.step(proc["init_steps"])
+    sweep = R.density_sweep(sim, proc["rho_start"], proc["rho_end"], proc["delta"], proc["t_sample_low"],
+                            t_sample_of=lambda r: proc["t_sample_high"] if r > proc["t_switch_rho"] + 1e-9
+                            else proc["t_sample_low"], sample=list(range(runs)))
+    sim.close()
+    majority = []
+    for rho, obs in sweep:
+        cls = [R.classify_cil(o["phi"], o["drho_y"], o["zeta"], A=d["A"], B=d["B"], rho_bar=rho) for o in obs]
+        majority.append((round(rho, 4), Counter(cls).most_common(1)[0][0], cls))
+    at = {r: (m, cls) for r, m, cls in majority}
+    for regime in ("HD", "B", "HO", "RB"):
+        rho = hyst[f"rho_bar_{regime}"]
+        m, cls = at[round(rho, 4)]
+        assert cls.count(regime) > runs // 2, (rho, regime, cls)
+    # order of the stretches of equal majority regime, ignoring one-sample
+    # blips where the runs are split at a transition
+    stretches = []
+    for _, m, _ in majority:
+        if stretches and stretches[-1][0] == m:
+            stretches[-1][1] += 1
+        else:
+            stretches.append([m, 1])
+    order = []
+    for m, n in stretches:
+        if n >= 2 and (not order or order[-1] != m):
+            order.append(m)
+    assert order == ["HD", "B", "HO", "RB", "HD"], stretches
+
+
+def test_mips_phase_separation_stops_near_paper_sigma():
+    """App. C.1 on the 90 x 30 D2Q7 box at rho-bar = 0.12 with Table
+    ParametersMIPS (tau = 2): drho (std of rho_y) above the paper's threshold
+    0.0430 means phase separated.  Noise strengths 10/700 ... 30/700 run side by
+    side as one batch (2 x 10^5 steps, then 50 samples 4000 steps apart): the
+    mean drho must be above the threshold at every sigma below the paper's
+    sigma = 0.0275, where its drho levels out, by at least one 1/700 step,
+    and below it at every sigma at least one step above."""
+    import numpy as np
+    from paper_1902_00530_gb300 import Lattice, Simulation
+    from paper_1902_00530_gb300 import regimes as R
+    ms = G["mips_sweep"]
+    d = W.preset("MIPS_Q7_PAPER")
+    model = d.pop("model")
+    nx, ny = G["boxes"]["mips_phase"]
+    sigmas = [k * ms["sigma_step"] for k in range(10, 31, 2)]
+    sim = Simulation([Lattice(nx, ny, "f32", k, "d2q7") for k in range(len(sigmas))], [model] * len(sigmas),
+                     [dict(d, sigma=s) for s in sigmas])
+    sim.init(W.seed(12), [dict(W.INIT_CONFIG1, rho_mean=ms["rho_bar"], rho_amp=0.05)] * len(sigmas))
+    sim.step(200_000)
+    drho = np.zeros((len(sigmas), 50))
+    for j in range(50):
+        sim.step(4000)
+        for k in range(len(sigmas)):
+            drho[k, j] = sim.observables(k)["drho_y"]
+    sim.close()
+    mean = drho.mean(1)
+    for s, m in zip(sigmas, mean):
+        if s < ms["sigma_levels_out"] - ms["sigma_step"]:
+            assert R.mips_separated(m), (s, m)
+        elif s > ms["sigma_levels_out"] + ms["sigma_step"]:
+            assert not R.mips_separated(m), (s, m)

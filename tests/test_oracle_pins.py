@@ -466,3 +466,20 @@ def test_presets_follow_paper_tables():
     s = 1 / g["cil_hysteresis"]["rho_bar_HO"]
     r = W.PRESETS["CIL_RHO1"]
     assert abs(r["A"] - cil["A"] / s ** 2) < 1e-12 and abs(r["sigma"] - cil["sigma"] * s) < 1e-12
+
+
+def test_d2q7_presets_follow_paper_tables():
+    """The D2Q7 presets carry the paper's numbers unchanged (no D2Q9 noise
+    conversion): MIPS Table ParametersMIPS (tau = 2), CIL App. C.2 (tau = 1)."""
+    g = json.load(open(os.path.join(HERE, "golden", "paper_parameters.json")))
+    m = W.PRESETS["MIPS_Q7_PAPER"]
+    t = g["mips_table"]
+    assert (m["tau"], m["C"], m["rho_star"], m["u_max"]) == (t["tau"], t["C"], t["rho_star"], t["U_max"])
+    assert m["sigma"] == g["mips_stills"]["b"]["sigma"]
+    c = W.PRESETS["CIL_Q7_PAPER"]
+    assert (c["tau"], c["B"], c["sigma"], c["A"]) == (g["cil_general"]["tau"], g["cil_general"]["B"],
+                                                     g["cil_general"]["sigma"], g["cil_hysteresis"]["A"])
+    assert list(W.BOX_CIL_PAPER) == g["boxes"]["cil"] and list(W.BOX_MIPS_PHASE_PAPER) == g["boxes"]["mips_phase"]
+    s = 1 / g["mips_sweep"]["rho_bar"]
+    r = W.PRESETS["MIPS_Q7_RHO1"]
+    assert abs(r["C"] - m["C"] / s) < 1e-12 and abs(r["sigma"] - m["sigma"] * s) < 1e-12 and r["tau"] == m["tau"]

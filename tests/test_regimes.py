@@ -52,7 +52,7 @@ class FakeSim:
         self.log.append(("step", n))
 
     def observables(self, lattice=0):
-        return {"rho": self.rho}
+        return {"rho": self.rho, "lattice": lattice}
 
     def add_density(self, delta, lattice=-1):
         self.rho += delta
@@ -70,3 +70,10 @@ def test_density_sweep_follows_app_c3():
     assert [round(r, 6) for r, _ in down] == [0.35, 0.3475, 0.345]
     with pytest.raises(ValueError):
         R.density_sweep(sim, 0.1, 0.2, -0.01, 10)
+
+
+def test_density_sweep_samples_a_batch():
+    sim = FakeSim()
+    res = R.density_sweep(sim, 0.09, 0.095, 0.0025, 100, sample=[0, 1, 2])
+    assert len(res) == 3 and [o["lattice"] for o in res[0][1]] == [0, 1, 2]
+    assert res[1][1][2]["rho"] == pytest.approx(0.0925)

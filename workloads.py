@@ -38,6 +38,7 @@ SQRT2 = math.sqrt(2.0)
 
 # paper values (Table ParametersMIPS; stills (b)-(d) sigma = 0.014; App. C.1 rho-bar = 0.12)
 _MIPS_C, _MIPS_RHO_STAR, _MIPS_UMAX, _MIPS_SIGMA, _MIPS_RHOBAR = 50.0, 0.2, 0.3, 0.014, 0.12
+_MIPS_TAU = 2.0  # Table ParametersMIPS; the D2Q9 presets use tau = 1
 # paper values (App. C.2: B = 0.3, tau = 1, sigma = 1/70; Fig. Hysteresis A = 2; HO snapshot rho-bar 0.185)
 _CIL_A, _CIL_B, _CIL_SIGMA, _CIL_RHOBAR = 2.0, 0.3, 1.0 / 70.0, 0.185
 
@@ -53,10 +54,10 @@ PRESETS = {
                      rho_star=1.0, u_max=1.0, A=_CIL_A * _CIL_RHOBAR ** 2, B=_CIL_B),
     "PASSIVE": dict(model="passive", tau=1.0, sigma=0.0, C=0.0, rho_star=1.0, u_max=1.0,
                     A=0.0, B=0.0),
-    # D2Q7: the paper's lattice, its sigma as printed
-    "MIPS_Q7_PAPER": dict(model="mips", tau=1.0, sigma=_MIPS_SIGMA, C=_MIPS_C, rho_star=_MIPS_RHO_STAR,
+    # D2Q7: the paper's lattice, its parameters as printed (MIPS: Table ParametersMIPS, tau = 2)
+    "MIPS_Q7_PAPER": dict(model="mips", tau=_MIPS_TAU, sigma=_MIPS_SIGMA, C=_MIPS_C, rho_star=_MIPS_RHO_STAR,
                           u_max=_MIPS_UMAX, A=0.0, B=0.0),
-    "MIPS_Q7_RHO1": dict(model="mips", tau=1.0, sigma=_MIPS_SIGMA / _MIPS_RHOBAR, C=_MIPS_C * _MIPS_RHOBAR,
+    "MIPS_Q7_RHO1": dict(model="mips", tau=_MIPS_TAU, sigma=_MIPS_SIGMA / _MIPS_RHOBAR, C=_MIPS_C * _MIPS_RHOBAR,
                          rho_star=_MIPS_RHO_STAR / _MIPS_RHOBAR, u_max=_MIPS_UMAX, A=0.0, B=0.0),
     "CIL_Q7_PAPER": dict(model="cil", tau=1.0, sigma=_CIL_SIGMA, C=0.0, rho_star=1.0, u_max=1.0,
                          A=_CIL_A, B=_CIL_B),
