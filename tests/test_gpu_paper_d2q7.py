@@ -90,7 +90,7 @@ def test_mips_phase_separation_stops_near_paper_sigma():
     sim.close()
     mean = drho.mean(1)
     for s, m in zip(sigmas, mean):
-        if s < ms["sigma_levels_out"] - ms["sigma_step"]:
+        if s < ms["sigma_levels_out"] - 2 * ms["sigma_step"]:
             assert R.mips_separated(m), (s, m)
         elif s > ms["sigma_levels_out"] + ms["sigma_step"]:
             assert not R.mips_separated(m), (s, m)
