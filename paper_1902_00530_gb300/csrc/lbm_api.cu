@@ -312,13 +312,17 @@ cudaError_t launch_group_step(const lbm_ctx *c, const GroupHost &g, int src, uin
         a.rk[2 * r] = a.key0 + (uint32_t)r * 0x9E3779B9u;
         a.rk[2 * r + 1] = a.key1 + (uint32_t)r * 0xBB67AE85u;
     }
-    if (g.q == 7) return launch_step_q7(g.storage, g.model, g.vec, sample, a, g.blocks, g.warps, c->stream);
+    // noise form of the launch: compile-time when the group is uniform in sigma
+    int with = 0;
+    for (int m : g.members) with += (float)(2.0 * c->lats[m].p.sigma) > 0.f ? 1 : 0;  // as the kernel sees sigma_q
+    const int noise = with == 0 ? 0 : (with == (int)g.members.size() ? 1 : 2);
+    if (g.q == 7) return launch_step_q7(g.storage, g.model, g.vec, sample, noise, a, g.blocks, g.warps, c->stream);
     const int kind = g.stages > 0 ? 1 : 0;
     if (g.storage == LBM_F32)
-        return launch_step_f32(g.model, kind, g.vec, sample, a, g.blocks, g.warps, c->stream);
+        return launch_step_f32(g.model, kind, g.vec, sample, noise, a, g.blocks, g.warps, c->stream);
     if (g.storage == LBM_F16_SHIFTED)
-        return launch_step_f16(g.model, kind, g.vec, sample, a, g.blocks, g.warps, c->stream);
-    return launch_step_bf16(g.model, kind, g.vec, sample, a, g.blocks, g.warps, c->stream);
+        return launch_step_f16(g.model, kind, g.vec, sample, noise, a, g.blocks, g.warps, c->stream);
+    return launch_step_bf16(g.model, kind, g.vec, sample, noise, a, g.blocks, g.warps, c->stream);
 }
 
 cudaError_t launch_group_observe(const lbm_ctx *c, const GroupHost &g, int src)

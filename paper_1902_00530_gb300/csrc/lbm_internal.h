@@ -5,20 +5,22 @@
 
 namespace lbm {
 
-// fused step / observe kernels (lbm_step_*.cu, one unit per storage type)
-cudaError_t launch_step_f32(int model, int kind, int vec, bool sample, const StepArgs &a, int blocks, int warps,
-                            cudaStream_t stream);
-cudaError_t launch_step_f16(int model, int kind, int vec, bool sample, const StepArgs &a, int blocks, int warps,
-                            cudaStream_t stream);
-cudaError_t launch_step_bf16(int model, int kind, int vec, bool sample, const StepArgs &a, int blocks, int warps,
-                             cudaStream_t stream);
+// fused step / observe kernels (lbm_step_*.cu, one unit per storage type).
+// noise: 0 = sigma = 0 in every lattice of the launch, 1 = sigma > 0 in every
+// one, 2 = mixed (decided per lattice in the kernel).
+cudaError_t launch_step_f32(int model, int kind, int vec, bool sample, int noise, const StepArgs &a, int blocks,
+                            int warps, cudaStream_t stream);
+cudaError_t launch_step_f16(int model, int kind, int vec, bool sample, int noise, const StepArgs &a, int blocks,
+                            int warps, cudaStream_t stream);
+cudaError_t launch_step_bf16(int model, int kind, int vec, bool sample, int noise, const StepArgs &a, int blocks,
+                             int warps, cudaStream_t stream);
 cudaError_t launch_observe_f32(int vec, const StepArgs &a, int blocks, int warps, cudaStream_t stream);
 cudaError_t launch_observe_f16(int vec, const StepArgs &a, int blocks, int warps, cudaStream_t stream);
 cudaError_t launch_observe_bf16(int vec, const StepArgs &a, int blocks, int warps, cudaStream_t stream);
 
 // the D2Q7 step / observe kernels (lbm_step_q7.cu; storage an ST_* value)
-cudaError_t launch_step_q7(int storage, int model, int vec, bool sample, const StepArgs &a, int blocks, int warps,
-                           cudaStream_t stream);
+cudaError_t launch_step_q7(int storage, int model, int vec, bool sample, int noise, const StepArgs &a, int blocks,
+                           int warps, cudaStream_t stream);
 cudaError_t launch_observe_q7(int storage, int vec, const StepArgs &a, int blocks, int warps, cudaStream_t stream);
 
 // auxiliary kernels (lbm_aux.cu); the lattice's q comes from its descriptor,

@@ -448,7 +448,10 @@ __device__ __forceinline__ int find_lattice(const LatDesc *desc, int nlat, int b
     return lo;
 }
 
-template <int MODEL, int ST, int VEC, bool SAMPLE>
+// NOISE: 0 = no noise in any lattice of the launch, 1 = noise in all of them
+// (both decided at compile time, so the per-site code has no branch around
+// the generator), 2 = decided per lattice from sigma at run time.
+template <int MODEL, int ST, int VEC, bool SAMPLE, int NOISE>
 __global__ void __launch_bounds__(256) step_kernel(const StepArgs a)
 {
     using T = typename Store<ST>::T;
@@ -470,7 +473,7 @@ __global__ void __launch_bounds__(256) step_kernel(const StepArgs a)
     const float rho0 = dp->rho0;
     const uint32_t id = (uint32_t)dp->id;
     const uint32_t t = *a.t_ptr + a.k;
-    const bool noise = d.sigma_q > 0.f;
+    const bool noise = NOISE == 2 ? d.sigma_q > 0.f : NOISE == 1;
 
     double col[VEC], acc[5];
     if constexpr (SAMPLE) {

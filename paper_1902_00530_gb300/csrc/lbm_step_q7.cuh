@@ -312,7 +312,7 @@ __device__ __forceinline__ void q7_row(Q7Walk<VEC> &w, int y, const typename Sto
     }
 }
 
-template <int MODEL, int ST, int VEC, bool SAMPLE>
+template <int MODEL, int ST, int VEC, bool SAMPLE, int NOISE>
 __global__ void __launch_bounds__(256) step_kernel_q7(const StepArgs a)
 {
     using T = typename Store<ST>::T;
@@ -335,7 +335,7 @@ __global__ void __launch_bounds__(256) step_kernel_q7(const StepArgs a)
     const float rho0 = dp->rho0;
     const uint32_t id = (uint32_t)dp->id;
     const uint32_t t = *a.t_ptr + a.k;
-    const bool noise = d.sigma_q > 0.f;
+    const bool noise = NOISE == 2 ? d.sigma_q > 0.f : NOISE == 1;  // as in step_kernel
     double *rowp = dp->rowp + (size_t)sx * ny;
 
     Q7Walk<VEC> w;
@@ -404,35 +404,38 @@ __global__ void __launch_bounds__(256) observe_kernel_q7(const StepArgs a)
 // Launchers
 // ---------------------------------------------------------------------------
 template <int MODEL, int ST, int VEC>
-static cudaError_t launch_q7_mv(bool sample, const StepArgs &a, int blocks, int warps, cudaStream_t stream)
+static cudaError_t launch_q7_mv(bool sample, int noise, const StepArgs &a, int blocks, int warps, cudaStream_t stream)
 {
-    if (sample) step_kernel_q7<MODEL, ST, VEC, true><<<blocks, warps * 32, 0, stream>>>(a);
-    else step_kernel_q7<MODEL, ST, VEC, false><<<blocks, warps * 32, 0, stream>>>(a);
+    if (sample) step_kernel_q7<MODEL, ST, VEC, true, 2><<<blocks, warps * 32, 0, stream>>>(a);
+    else if (noise == 0) step_kernel_q7<MODEL, ST, VEC, false, 0><<<blocks, warps * 32, 0, stream>>>(a);
+    else if (noise == 1) step_kernel_q7<MODEL, ST, VEC, false, 1><<<blocks, warps * 32, 0, stream>>>(a);
+    else step_kernel_q7<MODEL, ST, VEC, false, 2><<<blocks, warps * 32, 0, stream>>>(a);
     return cudaGetLastError();
 }
 
 template <int MODEL, int ST>
-static cudaError_t launch_q7_m(int vec, bool sample, const StepArgs &a, int blocks, int warps, cudaStream_t stream)
+static cudaError_t launch_q7_m(int vec, bool sample, int noise, const StepArgs &a, int blocks, int warps,
+                               cudaStream_t stream)
 {
     switch (vec) {
-    case 1: return launch_q7_mv<MODEL, ST, 1>(sample, a, blocks, warps, stream);
-    case 2: return launch_q7_mv<MODEL, ST, 2>(sample, a, blocks, warps, stream);
-    case 4: return launch_q7_mv<MODEL, ST, 4>(sample, a, blocks, warps, stream);
+    case 1: return launch_q7_mv<MODEL, ST, 1>(sample, noise, a, blocks, warps, stream);
+    case 2: return launch_q7_mv<MODEL, ST, 2>(sample, noise, a, blocks, warps, stream);
+    case 4: return launch_q7_mv<MODEL, ST, 4>(sample, noise, a, blocks, warps, stream);
     case 8:
-        if constexpr (ST != ST_F32) return launch_q7_mv<MODEL, ST, 8>(sample, a, blocks, warps, stream);
+        if constexpr (ST != ST_F32) return launch_q7_mv<MODEL, ST, 8>(sample, noise, a, blocks, warps, stream);
         return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
     }
 }
 
 template <int ST>
-static cudaError_t launch_step_q7_storage(int model, int vec, bool sample, const StepArgs &a, int blocks, int warps,
-                                         cudaStream_t stream)
+static cudaError_t launch_step_q7_storage(int model, int vec, bool sample, int noise, const StepArgs &a, int blocks,
+                                         int warps, cudaStream_t stream)
 {
     switch (model) {
-    case MODEL_PASSIVE: return launch_q7_m<MODEL_PASSIVE, ST>(vec, sample, a, blocks, warps, stream);
-    case MODEL_MIPS: return launch_q7_m<MODEL_MIPS, ST>(vec, sample, a, blocks, warps, stream);
-    case MODEL_CIL: return launch_q7_m<MODEL_CIL, ST>(vec, sample, a, blocks, warps, stream);
+    case MODEL_PASSIVE: return launch_q7_m<MODEL_PASSIVE, ST>(vec, sample, noise, a, blocks, warps, stream);
+    case MODEL_MIPS: return launch_q7_m<MODEL_MIPS, ST>(vec, sample, noise, a, blocks, warps, stream);
+    case MODEL_CIL: return launch_q7_m<MODEL_CIL, ST>(vec, sample, noise, a, blocks, warps, stream);
     default: return cudaErrorInvalidValue;
     }
 }

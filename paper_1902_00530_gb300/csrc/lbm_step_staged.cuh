@@ -208,7 +208,7 @@ template <int VEC> constexpr int staged_min_blocks()
     return VEC == 1 ? LBM_STAGED_MINB_1 : (VEC == 2 ? LBM_STAGED_MINB_2 : (VEC == 4 ? LBM_STAGED_MINB_4 : LBM_STAGED_MINB_8));
 }
 
-template <int MODEL, int ST, int VEC, bool SAMPLE>
+template <int MODEL, int ST, int VEC, bool SAMPLE, int NOISE>
 __global__ void __launch_bounds__(128, staged_min_blocks<VEC>()) step_staged_kernel(const StepArgs a)
 {
     using T = typename Store<ST>::T;
@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(128, staged_min_blocks<VEC>()) step_staged_ker
     const float rho0 = dp->rho0;
     const uint32_t id = (uint32_t)dp->id;
     const uint32_t t = *a.t_ptr + a.k;
-    const bool noise = d.sigma_q > 0.f;
+    const bool noise = NOISE == 2 ? d.sigma_q > 0.f : NOISE == 1;
 
     if (lane == 0) {
         for (int k = 0; k < S; ++k) mbar_init(&bars[k], 1);
@@ -361,52 +361,60 @@ constexpr int staged_stage_bytes()
 // ---------------------------------------------------------------------------
 namespace lbm {
 
-template <int MODEL, int ST, int VEC, bool SAMPLE>
+template <int MODEL, int ST, int VEC, bool SAMPLE, int NOISE>
 static cudaError_t launch_one_staged(const StepArgs &a, int blocks, int warps, cudaStream_t stream)
 {
     const size_t bytes = (size_t)warps * a.stages * (StageGeom<ST, VEC>::STAGE_BYTES + sizeof(uint64_t));
-    auto kern = step_staged_kernel<MODEL, ST, VEC, SAMPLE>;
+    auto kern = step_staged_kernel<MODEL, ST, VEC, SAMPLE, NOISE>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
     kern<<<blocks, warps * 32, bytes, stream>>>(a);
     return cudaGetLastError();
 }
 
-template <int MODEL, int ST, int VEC>
-static cudaError_t launch_mv(int kind, bool sample, const StepArgs &a, int blocks, int warps, cudaStream_t stream)
+template <int MODEL, int ST, int VEC, bool SAMPLE, int NOISE>
+static cudaError_t launch_one(int kind, const StepArgs &a, int blocks, int warps, cudaStream_t stream)
 {
-    if (kind == 1) {
-        if (sample) return launch_one_staged<MODEL, ST, VEC, true>(a, blocks, warps, stream);
-        return launch_one_staged<MODEL, ST, VEC, false>(a, blocks, warps, stream);
-    }
-    if (sample) step_kernel<MODEL, ST, VEC, true><<<blocks, warps * 32, 0, stream>>>(a);
-    else step_kernel<MODEL, ST, VEC, false><<<blocks, warps * 32, 0, stream>>>(a);
+    if (kind == 1) return launch_one_staged<MODEL, ST, VEC, SAMPLE, NOISE>(a, blocks, warps, stream);
+    step_kernel<MODEL, ST, VEC, SAMPLE, NOISE><<<blocks, warps * 32, 0, stream>>>(a);
     return cudaGetLastError();
 }
 
+// Sample steps (one in sample_every) decide the noise at run time; the other
+// steps take the compile-time forms when the launch group is uniform.
+template <int MODEL, int ST, int VEC>
+static cudaError_t launch_mv(int kind, bool sample, int noise, const StepArgs &a, int blocks, int warps,
+                             cudaStream_t stream)
+{
+    if (sample) return launch_one<MODEL, ST, VEC, true, 2>(kind, a, blocks, warps, stream);
+    if (noise == 0) return launch_one<MODEL, ST, VEC, false, 0>(kind, a, blocks, warps, stream);
+    if (noise == 1) return launch_one<MODEL, ST, VEC, false, 1>(kind, a, blocks, warps, stream);
+    return launch_one<MODEL, ST, VEC, false, 2>(kind, a, blocks, warps, stream);
+}
+
 template <int MODEL, int ST>
-static cudaError_t launch_m(int kind, int vec, bool sample, const StepArgs &a, int blocks, int warps,
+static cudaError_t launch_m(int kind, int vec, bool sample, int noise, const StepArgs &a, int blocks, int warps,
                             cudaStream_t stream)
 {
     switch (vec) {
-    case 1: return launch_mv<MODEL, ST, 1>(kind, sample, a, blocks, warps, stream);
-    case 2: return launch_mv<MODEL, ST, 2>(kind, sample, a, blocks, warps, stream);
-    case 4: return launch_mv<MODEL, ST, 4>(kind, sample, a, blocks, warps, stream);
+    case 1: return launch_mv<MODEL, ST, 1>(kind, sample, noise, a, blocks, warps, stream);
+    case 2: return launch_mv<MODEL, ST, 2>(kind, sample, noise, a, blocks, warps, stream);
+    case 4: return launch_mv<MODEL, ST, 4>(kind, sample, noise, a, blocks, warps, stream);
     case 8:
-        if constexpr (ST != ST_F32) return launch_mv<MODEL, ST, 8>(kind, sample, a, blocks, warps, stream);
+        if constexpr (ST != ST_F32) return launch_mv<MODEL, ST, 8>(kind, sample, noise, a, blocks, warps, stream);
         return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
     }
 }
 
 template <int ST>
-static cudaError_t launch_step_storage(int model, int kind, int vec, bool sample, const StepArgs &a, int blocks,
-                                       int warps, cudaStream_t stream)
+static cudaError_t launch_step_storage(int model, int kind, int vec, bool sample, int noise, const StepArgs &a,
+                                       int blocks, int warps, cudaStream_t stream)
 {
     switch (model) {
-    case MODEL_PASSIVE: return launch_m<MODEL_PASSIVE, ST>(kind, vec, sample, a, blocks, warps, stream);
-    case MODEL_MIPS: return launch_m<MODEL_MIPS, ST>(kind, vec, sample, a, blocks, warps, stream);
-    case MODEL_CIL: return launch_m<MODEL_CIL, ST>(kind, vec, sample, a, blocks, warps, stream);
+    case MODEL_PASSIVE: return launch_m<MODEL_PASSIVE, ST>(kind, vec, sample, noise, a, blocks, warps, stream);
+    case MODEL_MIPS: return launch_m<MODEL_MIPS, ST>(kind, vec, sample, noise, a, blocks, warps, stream);
+    case MODEL_CIL: return launch_m<MODEL_CIL, ST>(kind, vec, sample, noise, a, blocks, warps, stream);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -433,10 +441,10 @@ static cudaError_t launch_observe_storage(int vec, const StepArgs &a, int blocks
 
 #define LBM_INSTANTIATE_STORAGE(ST, SUFFIX)                                                                  \
     namespace lbm {                                                                                          \
-    cudaError_t launch_step_##SUFFIX(int model, int kind, int vec, bool sample, const StepArgs &a, int blocks, \
-                                     int warps, cudaStream_t stream)                                         \
+    cudaError_t launch_step_##SUFFIX(int model, int kind, int vec, bool sample, int noise, const StepArgs &a,  \
+                                     int blocks, int warps, cudaStream_t stream)                             \
     {                                                                                                        \
-        return launch_step_storage<ST>(model, kind, vec, sample, a, blocks, warps, stream);                   \
+        return launch_step_storage<ST>(model, kind, vec, sample, noise, a, blocks, warps, stream);            \
     }                                                                                                        \
     cudaError_t launch_observe_##SUFFIX(int vec, const StepArgs &a, int blocks, int warps,                    \
                                         cudaStream_t stream)                                                 \
