@@ -36,7 +36,8 @@ def bytes_per_update(storage: str, q: int = 9) -> int:
     """Algorithmic HBM bytes of one site update: q populations read and written."""
     return BYTES_PER_UPDATE[storage] * q // 9
 KERNEL_SOURCES = ["paper_1902_00530_gb300/csrc/lbm_step.cuh", "paper_1902_00530_gb300/csrc/lbm_step_staged.cuh",
-                  "paper_1902_00530_gb300/csrc/lbm_step_q7.cuh", "paper_1902_00530_gb300/csrc/lbm_device.cuh"]
+                  "paper_1902_00530_gb300/csrc/lbm_step_q7.cuh", "paper_1902_00530_gb300/csrc/lbm_step_q7_staged.cuh",
+                  "paper_1902_00530_gb300/csrc/lbm_device.cuh"]
 
 
 def kernel_hash() -> str:

@@ -78,7 +78,7 @@ typedef enum {
  * rows are sqrt(3)/2 apart and every odd row is shifted right by half a
  * spacing, so ny must be even.  Populations are f[i][y][x], i = 0..6.  The
  * noise of a site uses one Philox call whose 16-bit halves h_0..h_6 give
- * s_i = (2 h_i + 1 - 2^16) / 2^16.  The TMA-staged kernel is D2Q9 only. */
+ * s_i = (2 h_i + 1 - 2^16) / 2^16. */
 typedef struct {
     int32_t nx, ny;        /* sites along x and y, each in [1, 65536]; D2Q7: ny even */
     int32_t storage;       /* an lbm_storage value                                   */
@@ -218,8 +218,8 @@ lbm_status lbm_load(lbm_ctx *ctx, const char *path);
  * (1..8), stages = 0 for the kernel that loads populations straight from
  * global memory, or 2..8 (MIPS: 3..8; at most 4 warps) for the kernel that
  * stages population rows in shared memory with bulk copies, that many rows
- * per warp (needs nx a multiple of 16 bytes of storage; D2Q9 only: D2Q7
- * lattices use the direct kernel whatever stages says, and need rows even).  Host only;
+ * per warp (needs nx a multiple of 16 bytes of storage; D2Q7 lattices also
+ * need rows even).  Host only;
  * re-uploads descriptors (syncs) when bound. */
 lbm_status lbm_set_tuning(lbm_ctx *ctx, int32_t mode, int32_t vec, int32_t rows, int32_t warps,
                           int32_t stages);

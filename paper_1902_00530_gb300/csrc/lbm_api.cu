@@ -135,11 +135,9 @@ std::string validate(const lbm_lattice &l, int model, const lbm_params &p)
     return "";
 }
 
-// The staged kernel copies 16-byte halos: nx must be a multiple of that width.
-// It exists for D2Q9 only.
+// The staged kernels copy 16-byte halos: nx must be a multiple of that width.
 bool staged_ok(const lbm_ctx *c, const GroupHost &g)
 {
-    if (g.q != 9) return false;
     const int halo = g.storage == LBM_F32 ? 4 : 8;
     for (int m : g.members)
         if (c->lats[m].lat.nx % halo != 0 || c->lats[m].lat.nx < halo) return false;
@@ -316,8 +314,14 @@ cudaError_t launch_group_step(const lbm_ctx *c, const GroupHost &g, int src, uin
     int with = 0;
     for (int m : g.members) with += (float)(2.0 * c->lats[m].p.sigma) > 0.f ? 1 : 0;  // as the kernel sees sigma_q
     const int noise = with == 0 ? 0 : (with == (int)g.members.size() ? 1 : 2);
-    if (g.q == 7) return launch_step_q7(g.storage, g.model, g.vec, sample, noise, a, g.blocks, g.warps, c->stream);
     const int kind = g.stages > 0 ? 1 : 0;
+    if (g.q == 7) {
+        if (g.storage == LBM_F32)
+            return launch_step_q7_f32(g.model, kind, g.vec, sample, noise, a, g.blocks, g.warps, c->stream);
+        if (g.storage == LBM_F16_SHIFTED)
+            return launch_step_q7_f16(g.model, kind, g.vec, sample, noise, a, g.blocks, g.warps, c->stream);
+        return launch_step_q7_bf16(g.model, kind, g.vec, sample, noise, a, g.blocks, g.warps, c->stream);
+    }
     if (g.storage == LBM_F32)
         return launch_step_f32(g.model, kind, g.vec, sample, noise, a, g.blocks, g.warps, c->stream);
     if (g.storage == LBM_F16_SHIFTED)
@@ -337,7 +341,11 @@ cudaError_t launch_group_observe(const lbm_ctx *c, const GroupHost &g, int src)
     a.stages = 0;
     a.err = err_dev(c);
     for (int r = 0; r < 20; ++r) a.rk[r] = 0;
-    if (g.q == 7) return launch_observe_q7(g.storage, g.vec, a, g.blocks, g.warps, c->stream);
+    if (g.q == 7) {
+        if (g.storage == LBM_F32) return launch_observe_q7_f32(g.vec, a, g.blocks, g.warps, c->stream);
+        if (g.storage == LBM_F16_SHIFTED) return launch_observe_q7_f16(g.vec, a, g.blocks, g.warps, c->stream);
+        return launch_observe_q7_bf16(g.vec, a, g.blocks, g.warps, c->stream);
+    }
     if (g.storage == LBM_F32) return launch_observe_f32(g.vec, a, g.blocks, g.warps, c->stream);
     if (g.storage == LBM_F16_SHIFTED) return launch_observe_f16(g.vec, a, g.blocks, g.warps, c->stream);
     return launch_observe_bf16(g.vec, a, g.blocks, g.warps, c->stream);
@@ -431,7 +439,7 @@ lbm_status tune_group(lbm_ctx *c, GroupHost &g)
     long long max_ny = 1;
     for (int m : g.members) max_ny = std::max<long long>(max_ny, c->lats[m].lat.ny);
     const int all_v[] = {1, 2, 4, 8};
-    const bool staged = staged_ok(c, g);  // false for D2Q7
+    const bool staged = staged_ok(c, g);
     const int base_stages = g.model == LBM_MIPS ? 4 : 3;
     for (int v : all_v) {
         if (!allowed_vec(g.storage, v)) continue;
@@ -1012,12 +1020,10 @@ lbm_status lbm_set_tuning(lbm_ctx *c, int32_t mode, int32_t vec, int32_t rows, i
         return fail(c, LBM_ERR_INVALID_ARG, "stages must be 0 (direct) or 2..8 with at most 4 warps");
     if (stages != 0)
         for (auto &g : c->groups)
-            if (g.q == 9 && g.model == LBM_MIPS && stages < 3)
-                return fail(c, LBM_ERR_INVALID_ARG, "MIPS needs at least 3 stages");
+            if (g.model == LBM_MIPS && stages < 3) return fail(c, LBM_ERR_INVALID_ARG, "MIPS needs at least 3 stages");
     if (stages != 0)
         for (auto &g : c->groups)
-            if (g.q == 9 && !staged_ok(c, g))
-                return fail(c, LBM_ERR_INVALID_ARG, "staged kernel needs nx a multiple of 16 bytes");
+            if (!staged_ok(c, g)) return fail(c, LBM_ERR_INVALID_ARG, "staged kernel needs nx a multiple of 16 bytes");
     for (auto &g : c->groups)
         if (g.q == 7 && rows % 2) return fail(c, LBM_ERR_INVALID_ARG, "D2Q7 strips need an even number of rows");
     for (auto &g : c->groups) {
@@ -1029,7 +1035,7 @@ lbm_status lbm_set_tuning(lbm_ctx *c, int32_t mode, int32_t vec, int32_t rows, i
         g.vec = vec;
         g.rows = rows;
         g.warps = warps;
-        g.stages = g.q == 9 ? stages : 0;  // D2Q7 has the direct kernel only
+        g.stages = stages;
     }
     c->tune_mode = 1;
     c->tuned = true;

@@ -18,10 +18,17 @@ cudaError_t launch_observe_f32(int vec, const StepArgs &a, int blocks, int warps
 cudaError_t launch_observe_f16(int vec, const StepArgs &a, int blocks, int warps, cudaStream_t stream);
 cudaError_t launch_observe_bf16(int vec, const StepArgs &a, int blocks, int warps, cudaStream_t stream);
 
-// the D2Q7 step / observe kernels (lbm_step_q7.cu; storage an ST_* value)
-cudaError_t launch_step_q7(int storage, int model, int vec, bool sample, int noise, const StepArgs &a, int blocks,
-                           int warps, cudaStream_t stream);
-cudaError_t launch_observe_q7(int storage, int vec, const StepArgs &a, int blocks, int warps, cudaStream_t stream);
+// the D2Q7 step / observe kernels (lbm_step_q7_*.cu, one unit per storage
+// type); kind 0 = direct loads, 1 = bulk-copy staged rows
+cudaError_t launch_step_q7_f32(int model, int kind, int vec, bool sample, int noise, const StepArgs &a, int blocks,
+                               int warps, cudaStream_t stream);
+cudaError_t launch_step_q7_f16(int model, int kind, int vec, bool sample, int noise, const StepArgs &a, int blocks,
+                               int warps, cudaStream_t stream);
+cudaError_t launch_step_q7_bf16(int model, int kind, int vec, bool sample, int noise, const StepArgs &a, int blocks,
+                                int warps, cudaStream_t stream);
+cudaError_t launch_observe_q7_f32(int vec, const StepArgs &a, int blocks, int warps, cudaStream_t stream);
+cudaError_t launch_observe_q7_f16(int vec, const StepArgs &a, int blocks, int warps, cudaStream_t stream);
+cudaError_t launch_observe_q7_bf16(int vec, const StepArgs &a, int blocks, int warps, cudaStream_t stream);
 
 // auxiliary kernels (lbm_aux.cu); the lattice's q comes from its descriptor,
 // so `cells` counts sites and q * cells elements are touched

@@ -400,62 +400,4 @@ __global__ void __launch_bounds__(256) observe_kernel_q7(const StepArgs a)
     observe_flush<VEC>(dp->colp, dp->scal, nx, s, sy, x0, valid, col, acc, lane);
 }
 
-// ---------------------------------------------------------------------------
-// Launchers
-// ---------------------------------------------------------------------------
-template <int MODEL, int ST, int VEC>
-static cudaError_t launch_q7_mv(bool sample, int noise, const StepArgs &a, int blocks, int warps, cudaStream_t stream)
-{
-    if (sample) step_kernel_q7<MODEL, ST, VEC, true, 2><<<blocks, warps * 32, 0, stream>>>(a);
-    else if (noise == 0) step_kernel_q7<MODEL, ST, VEC, false, 0><<<blocks, warps * 32, 0, stream>>>(a);
-    else if (noise == 1) step_kernel_q7<MODEL, ST, VEC, false, 1><<<blocks, warps * 32, 0, stream>>>(a);
-    else step_kernel_q7<MODEL, ST, VEC, false, 2><<<blocks, warps * 32, 0, stream>>>(a);
-    return cudaGetLastError();
-}
-
-template <int MODEL, int ST>
-static cudaError_t launch_q7_m(int vec, bool sample, int noise, const StepArgs &a, int blocks, int warps,
-                               cudaStream_t stream)
-{
-    switch (vec) {
-    case 1: return launch_q7_mv<MODEL, ST, 1>(sample, noise, a, blocks, warps, stream);
-    case 2: return launch_q7_mv<MODEL, ST, 2>(sample, noise, a, blocks, warps, stream);
-    case 4: return launch_q7_mv<MODEL, ST, 4>(sample, noise, a, blocks, warps, stream);
-    case 8:
-        if constexpr (ST != ST_F32) return launch_q7_mv<MODEL, ST, 8>(sample, noise, a, blocks, warps, stream);
-        return cudaErrorInvalidValue;
-    default: return cudaErrorInvalidValue;
-    }
-}
-
-template <int ST>
-static cudaError_t launch_step_q7_storage(int model, int vec, bool sample, int noise, const StepArgs &a, int blocks,
-                                         int warps, cudaStream_t stream)
-{
-    switch (model) {
-    case MODEL_PASSIVE: return launch_q7_m<MODEL_PASSIVE, ST>(vec, sample, noise, a, blocks, warps, stream);
-    case MODEL_MIPS: return launch_q7_m<MODEL_MIPS, ST>(vec, sample, noise, a, blocks, warps, stream);
-    case MODEL_CIL: return launch_q7_m<MODEL_CIL, ST>(vec, sample, noise, a, blocks, warps, stream);
-    default: return cudaErrorInvalidValue;
-    }
-}
-
-template <int ST>
-static cudaError_t launch_observe_q7_storage(int vec, const StepArgs &a, int blocks, int warps, cudaStream_t stream)
-{
-    switch (vec) {
-    case 1: observe_kernel_q7<ST, 1><<<blocks, warps * 32, 0, stream>>>(a); break;
-    case 2: observe_kernel_q7<ST, 2><<<blocks, warps * 32, 0, stream>>>(a); break;
-    case 4: observe_kernel_q7<ST, 4><<<blocks, warps * 32, 0, stream>>>(a); break;
-    case 8:
-        if constexpr (ST != ST_F32) {
-            observe_kernel_q7<ST, 8><<<blocks, warps * 32, 0, stream>>>(a);
-            break;
-        }
-        return cudaErrorInvalidValue;
-    default: return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
-}
-
 }  // namespace lbm

@@ -17,6 +17,8 @@
 // staged kernel (DEVERR_TIMEOUT, bounded drain, return).
 #pragma once
 
+#include <type_traits>
+
 #include "lbm_step_q7.cuh"
 #include "lbm_step_staged.cuh"
 
@@ -286,4 +288,84 @@ static cudaError_t launch_one_staged7(const StepArgs &a, int blocks, int warps, 
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Launchers (instantiated once per storage type by LBM_INSTANTIATE_Q7).
+// ---------------------------------------------------------------------------
+template <int MODEL, int ST, int VEC, bool SAMPLE, int NOISE>
+static cudaError_t launch_one_q7(int kind, const StepArgs &a, int blocks, int warps, cudaStream_t stream)
+{
+    if (kind == 1) return launch_one_staged7<MODEL, ST, VEC, SAMPLE, NOISE>(a, blocks, warps, stream);
+    step_kernel_q7<MODEL, ST, VEC, SAMPLE, NOISE><<<blocks, warps * 32, 0, stream>>>(a);
+    return cudaGetLastError();
+}
+
+template <int MODEL, int ST, int VEC>
+static cudaError_t launch_q7_mv(int kind, bool sample, int noise, const StepArgs &a, int blocks, int warps,
+                                cudaStream_t stream)
+{
+    if (sample) return launch_one_q7<MODEL, ST, VEC, true, 2>(kind, a, blocks, warps, stream);
+    if (noise == 0) return launch_one_q7<MODEL, ST, VEC, false, 0>(kind, a, blocks, warps, stream);
+    if (noise == 1) return launch_one_q7<MODEL, ST, VEC, false, 1>(kind, a, blocks, warps, stream);
+    return launch_one_q7<MODEL, ST, VEC, false, 2>(kind, a, blocks, warps, stream);
+}
+
+template <int MODEL, int ST>
+static cudaError_t launch_q7_m(int kind, int vec, bool sample, int noise, const StepArgs &a, int blocks, int warps,
+                               cudaStream_t stream)
+{
+    switch (vec) {
+    case 1: return launch_q7_mv<MODEL, ST, 1>(kind, sample, noise, a, blocks, warps, stream);
+    case 2: return launch_q7_mv<MODEL, ST, 2>(kind, sample, noise, a, blocks, warps, stream);
+    case 4: return launch_q7_mv<MODEL, ST, 4>(kind, sample, noise, a, blocks, warps, stream);
+    case 8:
+        if constexpr (ST != ST_F32) return launch_q7_mv<MODEL, ST, 8>(kind, sample, noise, a, blocks, warps, stream);
+        return cudaErrorInvalidValue;
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int ST>
+static cudaError_t launch_step_q7_storage(int model, int kind, int vec, bool sample, int noise, const StepArgs &a,
+                                         int blocks, int warps, cudaStream_t stream)
+{
+    switch (model) {
+    case MODEL_PASSIVE: return launch_q7_m<MODEL_PASSIVE, ST>(kind, vec, sample, noise, a, blocks, warps, stream);
+    case MODEL_MIPS: return launch_q7_m<MODEL_MIPS, ST>(kind, vec, sample, noise, a, blocks, warps, stream);
+    case MODEL_CIL: return launch_q7_m<MODEL_CIL, ST>(kind, vec, sample, noise, a, blocks, warps, stream);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int ST>
+static cudaError_t launch_observe_q7_storage(int vec, const StepArgs &a, int blocks, int warps, cudaStream_t stream)
+{
+    switch (vec) {
+    case 1: observe_kernel_q7<ST, 1><<<blocks, warps * 32, 0, stream>>>(a); break;
+    case 2: observe_kernel_q7<ST, 2><<<blocks, warps * 32, 0, stream>>>(a); break;
+    case 4: observe_kernel_q7<ST, 4><<<blocks, warps * 32, 0, stream>>>(a); break;
+    case 8:
+        if constexpr (ST != ST_F32) {
+            observe_kernel_q7<ST, 8><<<blocks, warps * 32, 0, stream>>>(a);
+            break;
+        }
+        return cudaErrorInvalidValue;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 }  // namespace lbm
+
+#define LBM_INSTANTIATE_Q7(ST, SUFFIX)                                                                        \
+    namespace lbm {                                                                                          \
+    cudaError_t launch_step_q7_##SUFFIX(int model, int kind, int vec, bool sample, int noise, const StepArgs &a, \
+                                        int blocks, int warps, cudaStream_t stream)                          \
+    {                                                                                                        \
+        return launch_step_q7_storage<ST>(model, kind, vec, sample, noise, a, blocks, warps, stream);         \
+    }                                                                                                        \
+    cudaError_t launch_observe_q7_##SUFFIX(int vec, const StepArgs &a, int blocks, int warps,                 \
+                                           cudaStream_t stream)                                              \
+    {                                                                                                        \
+        return launch_observe_q7_storage<ST>(vec, a, blocks, warps, stream);                                  \
+    }                                                                                                        \
+    }

@@ -125,7 +125,7 @@ def test_python_binding_refuses_without_library(tmp_path):
 
 def test_d2q7_buffers_and_tuning(lib):
     """A D2Q7 lattice holds seven planes per buffer; its strips need an even
-    number of rows; the staged kernel (D2Q9 only) is not required of it."""
+    number of rows; staged shapes apply to both lattices."""
     from paper_1902_00530_gb300 import _abi
     lats = (_abi.lbm_lattice * 2)(_abi.lbm_lattice(64, 30, 0, 0, 1), _abi.lbm_lattice(64, 30, 0, 1, 0))
     mods = (ctypes.c_int * 2)(2, 2)
@@ -137,10 +137,10 @@ def test_d2q7_buffers_and_tuning(lib):
     plane = 30 * 64 * 4
     assert 2 * (7 + 9) * plane <= sb.value < 2 * (7 + 9) * plane + 4 * 256
     assert lib.lbm_set_tuning(ctx, 1, 2, 17, 4, 0) == 1   # odd rows: D2Q7 needs even
-    assert lib.lbm_set_tuning(ctx, 1, 2, 32, 2, 3) == 0   # stages apply to the D2Q9 member only
+    assert lib.lbm_set_tuning(ctx, 1, 2, 32, 2, 3) == 0
     v, r, w, st = (ctypes.c_int32() for _ in range(4))
     assert lib.lbm_get_tuning(ctx, 0, *[ctypes.byref(x) for x in (v, r, w, st)]) == 0
-    assert (v.value, r.value, st.value) == (2, 32, 0)
+    assert (v.value, r.value, st.value) == (2, 32, 3)
     assert lib.lbm_get_tuning(ctx, 1, *[ctypes.byref(x) for x in (v, r, w, st)]) == 0
     assert st.value == 3
     lib.lbm_destroy(ctx)

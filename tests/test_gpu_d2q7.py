@@ -113,15 +113,18 @@ def test_ragged_sizes_default_shape7(nx, ny):
         assert_parity(got, model, d, nx, ny, steps, SEED, spec)
 
 
-SHAPES_FIXED7 = [(1, 16), (2, 16), (4, 16), (4, 48), (2, 128), (8, 32), (1, 16, 2), (2, 32, 8)]
+SHAPES_FIXED7 = [(1, 16), (2, 16), (4, 16), (4, 48), (2, 128), (8, 32), (1, 16, 2), (2, 32, 8),
+                 (1, 16, 4, 3), (2, 32, 2, 4), (4, 64, 4, 6), (2, 48, 4, 3), (8, 32, 2, 4)]
 
 
 @pytest.mark.parametrize("shape", SHAPES_FIXED7, ids=lambda s: "x".join(map(str, s)))
 @pytest.mark.parametrize("storage", ["f32", "bf16s"])
 @pytest.mark.parametrize("name", ["MIPS_Q7_RHO1", "CIL_Q7_RHO1", "PASSIVE"])
 def test_launch_shapes_give_identical_states7(shape, storage, name):
-    """Every launch shape performs the same per-site arithmetic: bitwise equal
-    to the (vec 1, rows 16) shape, and within parity of the oracle."""
+    """Every launch shape -- direct loads (vec, rows, warps) or bulk-copy
+    staged rows (vec, rows, warps, stages) -- performs the same per-site
+    arithmetic: bitwise equal to the (vec 1, rows 16) shape, and within parity
+    of the oracle."""
     if storage == "f32" and shape[0] == 8:
         pytest.skip("vec 8 is a 16-bit storage shape")
     model, d = split_preset(name, **(dict(sigma=0.01) if name == "PASSIVE" else {}))
@@ -132,6 +135,22 @@ def test_launch_shapes_give_identical_states7(shape, storage, name):
     np.testing.assert_array_equal(got, base)
     if storage == "f32":
         assert_parity(got, model, d, nx, ny, 9, SEED, spec)
+
+
+@pytest.mark.parametrize("nx,ny", [(4, 4), (8, 2), (36, 6), (64, 64), (96, 34), (520, 18)])
+def test_staged_kernel_small_and_ragged7(nx, ny):
+    """Staged D2Q7 shapes on lattices narrower than a strip, with a ragged last
+    strip, and with the periodic halo wrapping onto the strip itself."""
+    for name, over, steps, spec in (("MIPS_Q7_RHO1", {}, 3, W.INIT_CONFIG1),
+                                    ("CIL_Q7_RHO1", {}, 20, W.init_ordered(U0_CIL7))):
+        model, d = split_preset(name, **over)
+        for shape in ((1, 16, 4, 3), (4, 32, 2, 4)):
+            if nx % shape[0]:
+                continue
+            got = gpu_run(model, d, nx, ny, steps, SEED, spec, tuning=shape, **Q7)
+            base = gpu_run(model, d, nx, ny, steps, SEED, spec, tuning=(1, 16), **Q7)
+            np.testing.assert_array_equal(got, base)
+            assert_parity(got, model, d, nx, ny, steps, SEED, spec)
 
 
 # ---------------------------------------------------------- noise stream ---
