@@ -449,9 +449,12 @@ lbm_status tune_group(lbm_ctx *c, GroupHost &g)
         for (int r : {16, 32, 64, 128}) {
             if (r > 16 && r > 2 * max_ny) continue;
             for (int w : {4, 8}) cands.push_back({v, r, w, 0});
-            if (staged && v >= 2)
+            if (staged && v >= 2) {
+                // MIPS also tries 3, the least its ring needs (less shared memory, more warps)
+                const int sts[3] = {base_stages, base_stages + 2, 3};
                 for (int w : {2, 4})
-                    for (int st : {base_stages, base_stages + 2}) cands.push_back({v, r, w, st});
+                    for (int k = 0; k < (base_stages > 3 ? 3 : 2); ++k) cands.push_back({v, r, w, sts[k]});
+            }
         }
     }
     cudaEvent_t e0, e1;

@@ -13,9 +13,10 @@
 // MIPS needs grad rho of the post-stream density at the eight neighbours
 // (Sec. 3 stencil, App. A.2 steps 2-3).  The warp keeps the post-stream
 // density of rows y-1, y, y+1 in registers (a 3-row window that slides with
-// the row loop, the populations of row y+1 pulled one row ahead) and obtains
-// the x-neighbours by shuffles; only the two strip-edge sites of each row are
-// recomputed by scalar pulls.
+// the row loop; row y+1 is pulled one row ahead for its densities, and pulled
+// again from cache when it is updated) and obtains the x-neighbours by
+// shuffles; only the two strip-edge sites of each row are recomputed by
+// scalar pulls.
 #pragma once
 
 #include "lbm_device.cuh"
@@ -451,8 +452,20 @@ __device__ __forceinline__ int find_lattice(const LatDesc *desc, int nlat, int b
 // NOISE: 0 = no noise in any lattice of the launch, 1 = noise in all of them
 // (both decided at compile time, so the per-site code has no branch around
 // the generator), 2 = decided per lattice from sigma at run time.
+// Minimum resident 256-thread blocks per SM the compiler must allow for,
+// which caps registers per thread at 65536 / (256 * blocks): 128 for MIPS
+// (its density window needs them), 85 for the other closures, where the
+// extra occupancy hides more load latency (measured at 8192^2 FP32).  No cap
+// where one would spill: sample steps (observables), 16-bit vec 8, 16-bit MIPS.
+template <int MODEL, int ST, int VEC, bool SAMPLE> constexpr int direct_min_blocks()
+{
+    if (SAMPLE) return 1;
+    if (ST != ST_F32 && (VEC == 8 || MODEL == MODEL_MIPS)) return 1;
+    return MODEL == MODEL_MIPS ? 2 : 3;
+}
+
 template <int MODEL, int ST, int VEC, bool SAMPLE, int NOISE>
-__global__ void __launch_bounds__(256) step_kernel(const StepArgs a)
+__global__ void __launch_bounds__(256, direct_min_blocks<MODEL, ST, VEC, SAMPLE>()) step_kernel(const StepArgs a)
 {
     using T = typename Store<ST>::T;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -483,26 +496,30 @@ __global__ void __launch_bounds__(256) step_kernel(const StepArgs a)
         for (int q = 0; q < 5; ++q) acc[q] = 0.0;
     }
 
-    float fc[9][VEC];
+    // MIPS: the densities of rows y-1 and y slide along in registers; the
+    // populations of row y are pulled again when row y is updated (they were
+    // pulled one row earlier for its densities, so the loads hit L1 / L2)
+    // rather than held across the collide of the row before: fewer registers,
+    // more resident warps.
     float rm[VEC + 2], rc[VEC + 2], rn[VEC + 2];
     if constexpr (MODEL == MODEL_MIPS) {
         float tmp[9][VEC];
         const int yp = wrap_once(y_begin - 1, ny);
         pull_row<ST, VEC>(src, plane, yp, ny, nx, pitch, x0, valid, last, lane, rho0, tmp);
         density_window<ST, VEC>(tmp, src, plane, yp, nx, ny, pitch, x0, valid, last, lane, rho0, rm);
-        pull_row<ST, VEC>(src, plane, y_begin, ny, nx, pitch, x0, valid, last, lane, rho0, fc);
-        density_window<ST, VEC>(fc, src, plane, y_begin, nx, ny, pitch, x0, valid, last, lane, rho0, rc);
+        pull_row<ST, VEC>(src, plane, y_begin, ny, nx, pitch, x0, valid, last, lane, rho0, tmp);
+        density_window<ST, VEC>(tmp, src, plane, y_begin, nx, ny, pitch, x0, valid, last, lane, rho0, rc);
     }
 
     for (int y = y_begin; y < y_end; ++y) {
-        float fn[9][VEC];
+        float fc[9][VEC];
         if constexpr (MODEL == MODEL_MIPS) {
+            float fn[9][VEC];
             const int yn = wrap_once(y + 1, ny);
             pull_row<ST, VEC>(src, plane, yn, ny, nx, pitch, x0, valid, last, lane, rho0, fn);
             density_window<ST, VEC>(fn, src, plane, yn, nx, ny, pitch, x0, valid, last, lane, rho0, rn);
-        } else {
-            pull_row<ST, VEC>(src, plane, y, ny, nx, pitch, x0, valid, last, lane, rho0, fc);
         }
+        pull_row<ST, VEC>(src, plane, y, ny, nx, pitch, x0, valid, last, lane, rho0, fc);
         float gx[VEC], gy[VEC];
         if constexpr (MODEL == MODEL_MIPS) {
             mips_gradients<VEC>(rm, rc, rn, gx, gy);
@@ -533,10 +550,6 @@ __global__ void __launch_bounds__(256) step_kernel(const StepArgs a)
             observe_row<VEC>(g, valid, col, acc, dp->rowp + (size_t)sx * ny + y, lane);
         }
         if constexpr (MODEL == MODEL_MIPS) {
-#pragma unroll
-            for (int i = 0; i < 9; ++i)
-#pragma unroll
-                for (int j = 0; j < VEC; ++j) fc[i][j] = fn[i][j];
 #pragma unroll
             for (int j = 0; j < VEC + 2; ++j) {
                 rm[j] = rc[j];
