@@ -15,8 +15,8 @@
 // density of rows y-1, y, y+1 in registers (a 3-row window that slides with
 // the row loop; row y+1 is pulled one row ahead for its densities, and pulled
 // again from cache when it is updated) and obtains the x-neighbours by
-// shuffles; only the two strip-edge sites of each row are recomputed by
-// scalar pulls.
+// shuffles; the two sites just outside the strip are pulled by 18 lanes at
+// once, one population each.
 #pragma once
 
 #include "lbm_device.cuh"
@@ -81,23 +81,13 @@ __device__ __forceinline__ float density(const float f[9][VEC], int j)
                      f[8][j]);
 }
 
-// Post-stream density of one site by nine scalar pulls (strip-edge halo),
-// summed in the same order as density() so the result does not depend on
-// where the strip edges fall.
-template <int ST>
-__device__ __forceinline__ float pulled_density(const typename Store<ST>::T *base, size_t plane,
-                                                int x, int y, int nx, int ny, int pitch, float rho0)
-{
-    float v[9][1];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        const int xs = wrap_once(x - vx(i), nx), ys = wrap_once(y - vy(i), ny);
-        v[i][0] = load_one<ST>(base + i * plane + (size_t)ys * pitch + xs, wq(i) * rho0);
-    }
-    return density<1>(v, 0);
-}
-
 // Density of this lane's VEC sites plus the two x-neighbours, for one row.
+// Inside the strip the neighbours come by shuffle.  The two sites just outside
+// it (left of lane 0, right of the last lane) are pulled cooperatively: lanes
+// 0..8 load one population each of the left site and lanes 16..24 of the right
+// one, and a shuffle tree adds them in density()'s order (((f0+f1)+(f2+f3)) +
+// ((f4+f5)+(f6+f7))) + f8, so the sums are bitwise those of a single-lane
+// pull without its nine serial loads.
 template <int ST, int VEC>
 __device__ __forceinline__ void density_window(const float f[9][VEC], const typename Store<ST>::T *base,
                                                size_t plane, int y, int nx, int ny, int pitch, int x0,
@@ -108,10 +98,21 @@ __device__ __forceinline__ void density_window(const float f[9][VEC], const type
     for (int j = 0; j < VEC; ++j) r[j + 1] = density<VEC>(f, j);
     float left = __shfl_up_sync(FULL, r[VEC], 1);
     float right = __shfl_down_sync(FULL, r[1], 1);
-    if (lane == 0 && valid)
-        left = pulled_density<ST>(base, plane, x0 == 0 ? nx - 1 : x0 - 1, y, nx, ny, pitch, rho0);
-    if (last && valid)
-        right = pulled_density<ST>(base, plane, x0 + VEC >= nx ? 0 : x0 + VEC, y, nx, ny, pitch, rho0);
+    const int xs = x0 - lane * VEC, xe = min(xs + 32 * VEC, nx);  // the strip's columns
+    const int i = lane & 15;
+    float v = 0.f;
+    if (i < 9) {
+        const int xh = lane >= 16 ? (xe >= nx ? 0 : xe) : (xs == 0 ? nx - 1 : xs - 1);
+        const int xsrc = wrap_once(xh - vx(i), nx), ysrc = wrap_once(y - vy(i), ny);
+        v = load_one<ST>(base + i * plane + (size_t)ysrc * pitch + xsrc, wq(i) * rho0);
+    }
+    const float s01 = __fadd_rn(v, __shfl_down_sync(FULL, v, 1));         // lanes 0, 2, 4, 6
+    const float s03 = __fadd_rn(s01, __shfl_down_sync(FULL, s01, 2));     // lanes 0, 4
+    const float s07 = __fadd_rn(s03, __shfl_down_sync(FULL, s03, 4));     // lane 0
+    const float s08 = __fadd_rn(s07, __shfl_down_sync(FULL, v, 8));       // + f8
+    const float halo_left = __shfl_sync(FULL, s08, 0), halo_right = __shfl_sync(FULL, s08, 16);
+    if (lane == 0) left = halo_left;
+    if (last) right = halo_right;
     r[0] = left;
     r[VEC + 1] = right;
 }

@@ -96,21 +96,6 @@ __device__ __forceinline__ float density7_at(const float f[7][VEC], int j)
     return density7(v);
 }
 
-// Post-stream density of one site of a row of parity P by scalar pulls
-// (strip-edge halo), summed in density7's order.
-template <int ST, int P>
-__device__ __forceinline__ float pulled_density7(const typename Store<ST>::T *base, size_t plane, int x, int y,
-                                                 int nx, int ny, int pitch, float rho0)
-{
-    float v[7];
-#pragma unroll
-    for (int i = 0; i < 7; ++i) {
-        const int xs = wrap_once(x + q7_src_dx(i, P), nx), ys = wrap_once(y + q7_src_dy(i), ny);
-        v[i] = load_one<ST>(base + i * plane + (size_t)ys * pitch + xs, wq7(i) * rho0);
-    }
-    return density7(v);
-}
-
 template <int ST, int VEC, int P>
 __device__ __forceinline__ void density_window7(const float f[7][VEC], const typename Store<ST>::T *base,
                                                 size_t plane, int y, int nx, int ny, int pitch, int x0, bool valid,
@@ -120,8 +105,23 @@ __device__ __forceinline__ void density_window7(const float f[7][VEC], const typ
     for (int j = 0; j < VEC; ++j) r[j + 1] = density7_at<VEC>(f, j);
     float left = __shfl_up_sync(FULL, r[VEC], 1);
     float right = __shfl_down_sync(FULL, r[1], 1);
-    if (lane == 0 && valid) left = pulled_density7<ST, P>(base, plane, x0 == 0 ? nx - 1 : x0 - 1, y, nx, ny, pitch, rho0);
-    if (last && valid) right = pulled_density7<ST, P>(base, plane, x0 + VEC >= nx ? 0 : x0 + VEC, y, nx, ny, pitch, rho0);
+    // the sites just outside the strip: lanes 0..6 (left) and 16..22 (right)
+    // pull one population each, summed by a shuffle tree in density7's order
+    const int xs = x0 - lane * VEC, xe = min(xs + 32 * VEC, nx);
+    const int i = lane & 15;
+    float v = 0.f;
+    if (i < 7) {
+        const int xh = lane >= 16 ? (xe >= nx ? 0 : xe) : (xs == 0 ? nx - 1 : xs - 1);
+        const int xsrc = wrap_once(xh + q7_src_dx(i, P), nx), ysrc = wrap_once(y + q7_src_dy(i), ny);
+        v = load_one<ST>(base + i * plane + (size_t)ysrc * pitch + xsrc, wq7(i) * rho0);
+    }
+    const float n1 = __shfl_down_sync(FULL, v, 1);
+    const float s01 = i == 6 ? v : __fadd_rn(v, n1);                 // lanes 0, 2, 4: pairs; lane 6: f6
+    const float s03 = __fadd_rn(s01, __shfl_down_sync(FULL, s01, 2)); // lanes 0, 4
+    const float s06 = __fadd_rn(s03, __shfl_down_sync(FULL, s03, 4)); // lane 0
+    const float halo_left = __shfl_sync(FULL, s06, 0), halo_right = __shfl_sync(FULL, s06, 16);
+    if (lane == 0) left = halo_left;
+    if (last) right = halo_right;
     r[0] = left;
     r[VEC + 1] = right;
 }
