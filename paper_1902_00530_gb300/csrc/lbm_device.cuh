@@ -143,10 +143,24 @@ template <> struct Store<ST_F32> {
     __device__ static __forceinline__ float get(T v, float) { return v; }
     __device__ static __forceinline__ T put(float f, float) { return f; }
 };
+// The 16-bit forms also convert two values at a time (packed conversions,
+// the same round-to-nearest per element): put2 packs (a, b) into one word, a
+// in the low half, and get2 unpacks it.
 template <> struct Store<ST_F16> {
     using T = __half;
     __device__ static __forceinline__ float get(T v, float shift) { return __half2float(v) + shift; }
     __device__ static __forceinline__ T put(float f, float shift) { return __float2half_rn(f - shift); }
+    __device__ static __forceinline__ uint32_t put2(float a, float b, float shift)
+    {
+        const __half2 h = __floats2half2_rn(a - shift, b - shift);
+        return *reinterpret_cast<const uint32_t *>(&h);
+    }
+    __device__ static __forceinline__ void get2(uint32_t w, float shift, float &a, float &b)
+    {
+        const float2 v = __half22float2(*reinterpret_cast<const __half2 *>(&w));
+        a = v.x + shift;
+        b = v.y + shift;
+    }
 };
 template <> struct Store<ST_BF16> {
     using T = __nv_bfloat16;
@@ -158,7 +172,32 @@ template <> struct Store<ST_BF16> {
     {
         return __float2bfloat16_rn(f - shift);
     }
+    __device__ static __forceinline__ uint32_t put2(float a, float b, float shift)
+    {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(a - shift, b - shift);
+        return *reinterpret_cast<const uint32_t *>(&h);
+    }
+    __device__ static __forceinline__ void get2(uint32_t w, float shift, float &a, float &b)
+    {
+        const float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w));
+        a = v.x + shift;
+        b = v.y + shift;
+    }
 };
+
+// Expand / pack the 32-bit words of a vector of VEC 16-bit values (VEC even).
+template <int ST, int VEC>
+__device__ __forceinline__ void unpack_words(const uint32_t *w, float shift, float out[VEC])
+{
+#pragma unroll
+    for (int k = 0; k < VEC / 2; ++k) Store<ST>::get2(w[k], shift, out[2 * k], out[2 * k + 1]);
+}
+template <int ST, int VEC>
+__device__ __forceinline__ void pack_words(const float in[VEC], float shift, uint32_t *w)
+{
+#pragma unroll
+    for (int k = 0; k < VEC / 2; ++k) w[k] = Store<ST>::put2(in[2 * k], in[2 * k + 1], shift);
+}
 
 template <int BYTES> struct VecWord;
 template <> struct VecWord<2> { using T = unsigned short; };
@@ -176,18 +215,26 @@ __device__ __forceinline__ void load_vec(const typename Store<ST>::T *p, float s
     if constexpr (BYTES <= 16) {
         using W = typename VecWord<BYTES>::T;
         W w = __ldg(reinterpret_cast<const W *>(p));
-        const T *e = reinterpret_cast<const T *>(&w);
+        if constexpr (sizeof(T) == 2 && VEC % 2 == 0) {
+            unpack_words<ST, VEC>(reinterpret_cast<const uint32_t *>(&w), shift, out);
+        } else {
+            const T *e = reinterpret_cast<const T *>(&w);
 #pragma unroll
-        for (int j = 0; j < VEC; ++j) out[j] = Store<ST>::get(e[j], shift);
+            for (int j = 0; j < VEC; ++j) out[j] = Store<ST>::get(e[j], shift);
+        }
     } else {
         const uint4 *q = reinterpret_cast<const uint4 *>(p);
 #pragma unroll
         for (int h = 0; h < BYTES / 16; ++h) {
             uint4 w = __ldg(q + h);
-            const T *e = reinterpret_cast<const T *>(&w);
+            constexpr int PER = 16 / (int)sizeof(T);
+            if constexpr (sizeof(T) == 2) {
+                unpack_words<ST, PER>(reinterpret_cast<const uint32_t *>(&w), shift, out + h * PER);
+            } else {
+                const T *e = reinterpret_cast<const T *>(&w);
 #pragma unroll
-            for (int j = 0; j < 16 / (int)sizeof(T); ++j)
-                out[h * (16 / (int)sizeof(T)) + j] = Store<ST>::get(e[j], shift);
+                for (int j = 0; j < PER; ++j) out[h * PER + j] = Store<ST>::get(e[j], shift);
+            }
         }
     }
 }
@@ -201,9 +248,13 @@ __device__ __forceinline__ void load_vec_plain(const typename Store<ST>::T *p, f
     static_assert(BYTES <= 16, "vector wider than 16 bytes");
     using W = typename VecWord<BYTES>::T;
     const W w = *reinterpret_cast<const W *>(p);
-    const T *e = reinterpret_cast<const T *>(&w);
+    if constexpr (sizeof(T) == 2 && VEC % 2 == 0) {
+        unpack_words<ST, VEC>(reinterpret_cast<const uint32_t *>(&w), shift, out);
+    } else {
+        const T *e = reinterpret_cast<const T *>(&w);
 #pragma unroll
-    for (int j = 0; j < VEC; ++j) out[j] = Store<ST>::get(e[j], shift);
+        for (int j = 0; j < VEC; ++j) out[j] = Store<ST>::get(e[j], shift);
+    }
 }
 
 template <int ST, int VEC>
@@ -214,19 +265,27 @@ __device__ __forceinline__ void store_vec(typename Store<ST>::T *p, float shift,
     if constexpr (BYTES <= 16) {
         using W = typename VecWord<BYTES>::T;
         W w;
-        T *e = reinterpret_cast<T *>(&w);
+        if constexpr (sizeof(T) == 2 && VEC % 2 == 0) {
+            pack_words<ST, VEC>(in, shift, reinterpret_cast<uint32_t *>(&w));
+        } else {
+            T *e = reinterpret_cast<T *>(&w);
 #pragma unroll
-        for (int j = 0; j < VEC; ++j) e[j] = Store<ST>::put(in[j], shift);
+            for (int j = 0; j < VEC; ++j) e[j] = Store<ST>::put(in[j], shift);
+        }
         *reinterpret_cast<W *>(p) = w;
     } else {
         uint4 *q = reinterpret_cast<uint4 *>(p);
 #pragma unroll
         for (int h = 0; h < BYTES / 16; ++h) {
             uint4 w;
-            T *e = reinterpret_cast<T *>(&w);
+            constexpr int PER = 16 / (int)sizeof(T);
+            if constexpr (sizeof(T) == 2) {
+                pack_words<ST, PER>(in + h * PER, shift, reinterpret_cast<uint32_t *>(&w));
+            } else {
+                T *e = reinterpret_cast<T *>(&w);
 #pragma unroll
-            for (int j = 0; j < 16 / (int)sizeof(T); ++j)
-                e[j] = Store<ST>::put(in[h * (16 / (int)sizeof(T)) + j], shift);
+                for (int j = 0; j < PER; ++j) e[j] = Store<ST>::put(in[h * PER + j], shift);
+            }
             q[h] = w;
         }
     }

@@ -457,11 +457,11 @@ __device__ __forceinline__ int find_lattice(const LatDesc *desc, int nlat, int b
 // which caps registers per thread at 65536 / (256 * blocks): 128 for MIPS
 // (its density window needs them), 85 for the other closures, where the
 // extra occupancy hides more load latency (measured at 8192^2 FP32).  No cap
-// where one would spill: sample steps (observables), 16-bit vec 8, 16-bit MIPS.
+// where one would spill: sample steps (observables), 16-bit vec 8.
 template <int MODEL, int ST, int VEC, bool SAMPLE> constexpr int direct_min_blocks()
 {
     if (SAMPLE) return 1;
-    if (ST != ST_F32 && (VEC == 8 || MODEL == MODEL_MIPS)) return 1;
+    if (ST != ST_F32 && VEC == 8) return 1;
     return MODEL == MODEL_MIPS ? 2 : 3;
 }
 
