@@ -47,7 +47,7 @@ typedef enum {
     LBM_ERR_CUDA = 3,        /* a CUDA runtime call failed                      */
     LBM_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up              */
     LBM_ERR_NUMERIC = 5,     /* non-finite observables were detected            */
-    LBM_ERR_UNSUPPORTED = 6  /* valid request this build does not provide       */
+    LBM_ERR_UNSUPPORTED = 6  /* a valid request the library does not provide    */
 } lbm_status;
 
 typedef enum {

@@ -79,7 +79,7 @@ def test_step_parity_16bit_1000_steps(storage, case):
     """Low-noise, linearly stable regimes (sigma ~ 0.01).  At the rescaled
     presets' noise (sigma ~ 0.05-0.08) the shifted populations carry
     deviations of the order of sigma, the 16-bit store rounds them to 2^-11
-    (FP16) or 2^-8 (BF16) of that, and the error is judged on steady-state
+    (FP16) or 2^-8 (BF16) of that, and the error is measured on steady-state
     observables instead (test_16bit_steady_state_observables); so is the
     passive model, whose conserved momentum accumulates rounding."""
     name, over, spec = STABLE[case]
