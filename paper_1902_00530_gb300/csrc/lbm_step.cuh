@@ -513,15 +513,14 @@ __global__ void __launch_bounds__(256, direct_min_blocks<MODEL, ST, VEC, SAMPLE>
     }
 
     for (int y = y_begin; y < y_end; ++y) {
-        // prefetch into L2 the nine source-row segments the next iteration
-        // pulls first (row y+2 for MIPS, whose loop pulls one row ahead; else
-        // row y+1): one instruction per population and no registers, and the
-        // row's work covers the DRAM latency
-        if (valid) {
-            const int ahead = MODEL == MODEL_MIPS ? 2 : 1;
+        // MIPS: prefetch into L2 the nine source-row segments of row y+2, which
+        // the next iteration pulls first (one instruction per population, no
+        // registers; the row's work covers the DRAM latency).  The lighter
+        // closures run at the copy bandwidth, where the extra requests cost.
+        if (MODEL == MODEL_MIPS && valid) {
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
-                const T *pp = src + i * plane + (size_t)wrap_once(wrap_once(y + ahead, ny) - vy(i), ny) * pitch + x0;
+                const T *pp = src + i * plane + (size_t)wrap_once(wrap_once(y + 2, ny) - vy(i), ny) * pitch + x0;
                 asm volatile("prefetch.global.L2 [%0];" ::"l"(pp));
             }
         }
