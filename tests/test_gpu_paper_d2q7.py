@@ -94,3 +94,51 @@ def test_mips_phase_separation_stops_near_paper_sigma():
             assert R.mips_separated(m), (s, m)
         elif s > ms["sigma_levels_out"] + ms["sigma_step"]:
             assert not R.mips_separated(m), (s, m)
+
+
+def _cil_sweep(direction, runs, seed):
+    """phi of every run at every density of one App. C.3 sweep (increasing or decreasing)."""
+    from paper_1902_00530_gb300 import Lattice, Simulation
+    from paper_1902_00530_gb300 import regimes as R
+    proc = G["cil_hysteresis_procedure"]
+    d = W.preset("CIL_Q7_PAPER")
+    model = d.pop("model")
+    nx, ny = G["boxes"]["cil"]
+    if direction > 0:
+        r0, r1, delta = proc["rho_start"], proc["rho_end"], proc["delta"]
+    else:
+        r0, r1, delta = proc["rho_start_down"], proc["rho_start"], -proc["delta"]
+    sim = Simulation([Lattice(nx, ny, "f32", k, "d2q7") for k in range(runs)], [model] * runs, [d] * runs)
+    sim.init(seed, [dict(W.INIT_PAPER_CIL, rho_mean=r0)] * runs)
+    sim.step(proc["init_steps"])
+    sweep = R.density_sweep(sim, r0, r1, delta, proc["t_sample_low"],
+                            t_sample_of=lambda r: proc["t_sample_high"] if r > proc["t_switch_rho"] + 1e-9
+                            else proc["t_sample_low"], sample=list(range(runs)))
+    sim.close()
+    return {round(r, 4): [o["phi"] for o in obs] for r, obs in sweep}
+
+
+def test_cil_hysteresis_loops_at_the_transitions():
+    """Fig. Hysteresis (a): increasing and decreasing runs at A = 2 (App. C.3;
+    the runs reinitialised between directions), sixteen runs per direction as
+    one batch.  The mean phi of the two directions must coincide across the
+    homogeneous ordered range well inside the paper's B and RB snapshot densities
+    (every point within 4.5 standard errors), and must split by more than 5
+    standard errors somewhere between the HD and B snapshot densities and
+    somewhere above the RB one: the loops at the HD-B transition and at the
+    return to disorder at high density."""
+    import numpy as np
+    hyst = G["cil_hysteresis"]
+    up = _cil_sweep(+1, 16, W.seed(21))
+    down = _cil_sweep(-1, 16, W.seed(22))
+    z = {}
+    for r in up:
+        if r in down:
+            a, b = np.array(up[r]), np.array(down[r])
+            z[r] = (a.mean() - b.mean()) / max(np.sqrt(a.var() / len(a) + b.var() / len(b)), 1e-12)
+    ho = [abs(z[r]) for r in z if hyst["rho_bar_B"] + 0.025 <= r <= hyst["rho_bar_RB"] - 0.04]
+    assert len(ho) > 20 and max(ho) < 4.5, max(ho)
+    low = [abs(z[r]) for r in z if hyst["rho_bar_HD"] < r < hyst["rho_bar_B"]]
+    high = [abs(z[r]) for r in z if r > hyst["rho_bar_RB"]]
+    assert max(low) > 5.0, low
+    assert max(high) > 5.0, high
