@@ -106,27 +106,25 @@ static void draw(uint64_t seed, uint32_t x, uint32_t y, uint32_t t, uint32_t id,
 }
 
 /* The nine noise variates s_i in (-1, 1) of one site and step, from one
- * Philox call (call index 0): split the four words into eight 16-bit halves
- * h_0..h_7 (h_2j = low half of word j, h_2j+1 = high half); variate i < 8
- * takes the top 14 bits of h_i, variate 8 the low 2 bits of h_0..h_6 (h_0's
- * lowest).  s = (2m + 1 - 2^14) / 2^14 for the 14-bit integer m: an odd
- * multiple of 2^-14, exact in FP32 and FP64 and symmetric about 0, so
- * eta~_i = sigma * s_i is uniform on [-sigma, sigma] (Sec. 2, below Eq.
- * (noiseDensityConservation)) to 14 bits. */
+ * Philox call (call index 0): each of the four 32-bit words w_j gives two
+ * 14-bit integers, its top bits 18..31 (variate 2j) and its bits 4..17
+ * (variate 2j+1); variate 8 gathers the words' low bits, bits 0..3 of w_0,
+ * w_1, w_2 (in that order from its lowest bit) and bits 0..1 of w_3.
+ * s = (2m + 1 - 2^14) / 2^14 for the 14-bit integer m: an odd multiple of
+ * 2^-14, exact in FP32 and FP64 and symmetric about 0, so eta~_i = sigma * s_i
+ * is uniform on [-sigma, sigma] (Sec. 2, below Eq. (noiseDensityConservation))
+ * to 14 bits. */
 void orc_noise_variates(uint64_t seed, uint32_t x, uint32_t y, uint32_t t, uint32_t id,
                         double s[Q])
 {
     uint32_t w[4];
     draw(seed, x, y, t, id, 0u, 0u, w);
-    uint32_t h[8];
-    for (int j = 0; j < 4; ++j) {
-        h[2 * j] = w[j] & 0xFFFFu;
-        h[2 * j + 1] = w[j] >> 16;
-    }
     uint32_t m[Q];
-    for (int i = 0; i < 8; ++i) m[i] = h[i] >> 2;
-    m[8] = 0;
-    for (int i = 0; i < 7; ++i) m[8] |= (h[i] & 3u) << (2 * i);
+    for (int j = 0; j < 4; ++j) {
+        m[2 * j] = w[j] >> 18;
+        m[2 * j + 1] = (w[j] >> 4) & 0x3FFFu;
+    }
+    m[8] = (w[0] & 0xFu) | ((w[1] & 0xFu) << 4) | ((w[2] & 0xFu) << 8) | ((w[3] & 0x3u) << 12);
     for (int i = 0; i < Q; ++i) s[i] = (2.0 * (double)m[i] + 1.0 - 16384.0) / 16384.0;
 }
 
