@@ -121,10 +121,10 @@ __device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const uint32_t *rk)
 }
 
 // Noise counter: (x, y, t, id | purpose << 24 | call << 28), purpose 0 and
-// call 0 for the collision noise.  One Philox call gives 128 bits: the eight
-// 16-bit halves h_0..h_7 (h_2j = low half of word j) each give a 14-bit
-// integer m_i = h_i >> 2 (i < 8), and m_8 gathers the low 2 bits of h_0..h_6
-// (h_0's lowest).  The variate s_i = (2 m_i + 1 - 2^14) 2^-14 is built without
+// call 0 for the collision noise.  One Philox call gives four 32-bit words
+// w_j: each gives two 14-bit integers, m_2j = bits 18..31 and m_2j+1 = bits
+// 4..17, and m_8 gathers bits 0..3 of w_0, w_1, w_2 and bits 0..1 of w_3 (w_0's
+// lowest first).  The variate s_i = (2 m_i + 1 - 2^14) 2^-14 is built without
 // an integer conversion: u_i = 1 + (m_i + 1/2) 2^-14 is assembled directly as
 // FP32 bits (exponent of 1, m_i in the top 14 mantissa bits, then a 1), and
 // s_i = 2 u_i - 3 exactly.  The zero-sum noise is then eta_i = sigma (s_i -

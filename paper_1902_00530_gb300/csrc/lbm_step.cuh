@@ -300,11 +300,10 @@ __device__ __forceinline__ void noise_u(uint32_t x, uint32_t y, uint32_t t, uint
     const uint32_t w[4] = {a.x, a.y, a.z, a.w};
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        u[2 * j] = u_from_bits((w[j] << 7) & 0x007FFE00u);
-        u[2 * j + 1] = u_from_bits((w[j] >> 9) & 0x007FFE00u);
+        u[2 * j] = u_from_bits((w[j] >> 9) & 0x007FFE00u);      // bits 18..31
+        u[2 * j + 1] = u_from_bits((w[j] << 5) & 0x007FFE00u);  // bits 4..17
     }
-    const uint32_t m8 = (w[0] & 3u) | ((w[0] >> 14) & 0xCu) | ((w[1] & 3u) << 4) | ((w[1] >> 10) & 0xC0u) |
-                        ((w[2] & 3u) << 8) | ((w[2] >> 6) & 0xC00u) | ((w[3] & 3u) << 12);
+    const uint32_t m8 = (w[0] & 0xFu) | ((w[1] & 0xFu) << 4) | ((w[2] & 0xFu) << 8) | ((w[3] & 0x3u) << 12);
     u[8] = u_from_bits(m8 << 9);
 }
 
