@@ -164,21 +164,23 @@ __device__ __forceinline__ float collide7(float f[7], float gx, float gy, const 
     float sx, sy;
     ustar_v<MODEL, float>(rho, ux, uy, gx, gy, d, sx, sy);
     // e_1.u* = sx, e_2.u* = sx/2 + (sqrt3/2) sy, e_3.u* = (sqrt3/2) sy - sx/2;
-    // e_4..e_6 are their negatives, sharing t = 1 - 2|u*|^2 + 8 (e.u*)^2
+    // e_4..e_6 are their negatives.  With r = rho/12 folded into the constants,
+    // each opposite pair is t = r (1 - 2|u*|^2) + 8 r (e.u*)^2 and t +- 4 r e.u*,
+    // one multiply and three fused multiply-adds
     const float base = __fmaf_rn(-2.f, __fmaf_rn(sx, sx, __fmul_rn(sy, sy)), 1.f);
     const float r12 = __fmul_rn(1.f / 12.f, rho);
     const float hy = __fmul_rn(Q7_HALF_SQRT3, sy), hx = __fmul_rn(0.5f, sx);
     const float a1 = sx, a2 = __fadd_rn(hy, hx), a3 = __fsub_rn(hy, hx);
-    const float t1 = __fmaf_rn(__fmul_rn(8.f, a1), a1, base), t2 = __fmaf_rn(__fmul_rn(8.f, a2), a2, base),
-                t3 = __fmaf_rn(__fmul_rn(8.f, a3), a3, base);
-    const float h1 = __fmul_rn(4.f, a1), h2 = __fmul_rn(4.f, a2), h3 = __fmul_rn(4.f, a3);
+    const float b = __fmul_rn(r12, base), q = __fmul_rn(8.f, r12), k = __fmul_rn(4.f, r12);
+    const float t1 = __fmaf_rn(__fmul_rn(q, a1), a1, b), t2 = __fmaf_rn(__fmul_rn(q, a2), a2, b),
+                t3 = __fmaf_rn(__fmul_rn(q, a3), a3, b);
     float eq[7];
-    eq[1] = __fmul_rn(r12, __fadd_rn(t1, h1));
-    eq[4] = __fmul_rn(r12, __fsub_rn(t1, h1));
-    eq[2] = __fmul_rn(r12, __fadd_rn(t2, h2));
-    eq[5] = __fmul_rn(r12, __fsub_rn(t2, h2));
-    eq[3] = __fmul_rn(r12, __fadd_rn(t3, h3));
-    eq[6] = __fmul_rn(r12, __fsub_rn(t3, h3));
+    eq[1] = __fmaf_rn(k, a1, t1);
+    eq[4] = __fmaf_rn(-k, a1, t1);
+    eq[2] = __fmaf_rn(k, a2, t2);
+    eq[5] = __fmaf_rn(-k, a2, t2);
+    eq[3] = __fmaf_rn(k, a3, t3);
+    eq[6] = __fmaf_rn(-k, a3, t3);
     eq[0] = __fsub_rn(rho, __fadd_rn(__fadd_rn(__fadd_rn(eq[1], eq[4]), __fadd_rn(eq[2], eq[5])),
                                      __fadd_rn(eq[3], eq[6])));
     const float om = d.omega;
