@@ -10,6 +10,10 @@ Host-side logic on top of the observables the library reduces on the GPU:
 * ``mips_separated``: App. C.1's phase-separation criterion drho > 0.0430.
 * ``density_sweep``: App. C.3's adiabatic procedure -- step t_sample steps,
   take a sample, change the mean density by delta (App. C.2), repeat.
+* ``phase_densities``: App. C.1's liquid and gas densities of a phase-separated
+  state -- the column profile rho_y(x) averaged over a window 20 columns wide,
+  slid along the periodic box; the highest window is the liquid, the lowest
+  the gas.
 
 The paper's cutoffs are in its units (mean densities 0.1-0.35).  Under the
 model's density-rescaling symmetry (rho -> s rho with C/s, s rho*, A/s^2,
@@ -23,6 +27,7 @@ PHI_CUT = 0.024           # App. D: phi < 0.024 is HD (CIL)
 DRHO_CUT_CIL = 0.012      # App. D: drho > 0.012 is B or RB
 ZETA_CUT = 0.1            # App. D: zeta > 0.1 is RB
 DRHO_CUT_MIPS = 0.0430    # App. C.1: drho > 0.0430 is phase separated
+PHASE_WINDOW = 20         # App. C.1: the averaging window is 20 dx wide
 
 
 def classify_cil(phi: float, drho: float, zeta: float, density_scale: float = 1.0,
@@ -69,3 +74,23 @@ def density_sweep(sim, rho_start: float, rho_end: float, delta: float, t_sample:
         k += 1
         rho = rho_start + k * delta
     return out
+
+
+def phase_densities(rho, width: int = PHASE_WINDOW):
+    """App. C.1: (liquid, gas) densities of a phase-separated state from its
+    density field rho (ny, nx) -- or from its column profile rho_y(x) -- by
+    averaging rho_y over `width` consecutive columns (periodic) at every
+    offset and taking the highest and the lowest window.  Accepts numpy
+    arrays and (CPU or CUDA) torch tensors."""
+    import numpy as np
+    if hasattr(rho, "detach"):
+        rho = rho.detach().double().cpu().numpy()
+    a = np.asarray(rho, dtype=np.float64)
+    prof = a.mean(axis=0) if a.ndim == 2 else a
+    nx = prof.shape[0]
+    if not 1 <= width <= nx:
+        raise ValueError("window width must be in [1, nx]")
+    ext = np.concatenate([prof, prof[:width - 1]])
+    c = np.concatenate([[0.0], np.cumsum(ext)])
+    windows = (c[width:width + nx] - c[:nx]) / width
+    return float(windows.max()), float(windows.min())

@@ -87,13 +87,18 @@ def test_mips_phase_separation_stops_near_paper_sigma():
         sim.step(4000)
         for k in range(len(sigmas)):
             drho[k, j] = sim.observables(k)["drho_y"]
+    phases = [R.phase_densities(sim.moments(k)[0]) for k in range(len(sigmas))]
     sim.close()
     mean = drho.mean(1)
-    for s, m in zip(sigmas, mean):
+    gaps = []
+    for s, m, (liquid, gas) in zip(sigmas, mean, phases):
         if s < ms["sigma_levels_out"] - 2 * ms["sigma_step"]:
             assert R.mips_separated(m), (s, m)
+            assert gas < ms["rho_bar"] < liquid, (s, liquid, gas)  # App. C.1 phase densities
+            gaps.append(liquid - gas)
         elif s > ms["sigma_levels_out"] + ms["sigma_step"]:
             assert not R.mips_separated(m), (s, m)
+    assert gaps[-1] < gaps[0], gaps  # liquid and gas approach each other towards the critical noise
 
 
 def _cil_sweep(direction, runs, seed):

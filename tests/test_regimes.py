@@ -77,3 +77,23 @@ def test_density_sweep_samples_a_batch():
     res = R.density_sweep(sim, 0.09, 0.095, 0.0025, 100, sample=[0, 1, 2])
     assert len(res) == 3 and [o["lattice"] for o in res[0][1]] == [0, 1, 2]
     assert res[1][1][2]["rho"] == pytest.approx(0.0925)
+
+
+def test_phase_densities_window():
+    """App. C.1: a liquid strip of 40 columns at 0.19 in a 0.05 gas, crossing
+    the periodic edge: the 20-column windows find both densities exactly; a
+    smooth profile matches a brute-force loop over window offsets."""
+    import numpy as np
+    nx, ny = 90, 30
+    prof = np.full(nx, 0.05)
+    prof[np.r_[70:90, 0:20]] = 0.19
+    rho = np.tile(prof, (ny, 1))
+    liq, gas = R.phase_densities(rho)
+    assert abs(liq - 0.19) < 1e-14 and abs(gas - 0.05) < 1e-14
+    x = np.arange(nx)
+    prof = 0.12 + 0.07 * np.sin(2 * np.pi * x / nx) + 0.01 * np.cos(6 * np.pi * x / nx)
+    w = [np.mean([prof[(s + k) % nx] for k in range(20)]) for s in range(nx)]
+    liq, gas = R.phase_densities(prof)
+    assert abs(liq - max(w)) < 1e-14 and abs(gas - min(w)) < 1e-14
+    with pytest.raises(ValueError):
+        R.phase_densities(prof, width=0)
