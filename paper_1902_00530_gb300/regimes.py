@@ -10,6 +10,9 @@ Host-side logic on top of the observables the library reduces on the GPU:
 * ``mips_separated``: App. C.1's phase-separation criterion drho > 0.0430.
 * ``density_sweep``: App. C.3's adiabatic procedure -- step t_sample steps,
   take a sample, change the mean density by delta (App. C.2), repeat.
+* ``density_sweeps``: several such sweeps with their own schedules (start,
+  end, step, sampling interval) on the lattices of one batch -- the paper's
+  increasing and decreasing runs side by side.
 * ``phase_densities``: App. C.1's liquid and gas densities of a phase-separated
   state -- the column profile rho_y(x) averaged over a window 20 columns wide,
   slid along the periodic box; the highest window is the liquid, the lowest
@@ -74,6 +77,46 @@ def density_sweep(sim, rho_start: float, rho_end: float, delta: float, t_sample:
         k += 1
         rho = rho_start + k * delta
     return out
+
+
+def density_sweeps(sim, schedules):
+    """App. C.3 sweeps of several lattices of one batch, each with its own
+    schedule: a dict with `lattice`, `rho_start`, `rho_end`, `delta` and
+    `t_sample` (steps, or a function of the current mean density).  Every
+    lattice keeps its own countdown; the batch is stepped to the next due
+    sample, the due lattices are sampled (just before their density change,
+    as in App. C.3) and shifted by their delta.  A lattice whose sweep is over
+    keeps being stepped with the others.  Returns, per schedule, the list of
+    (rho_bar, observables)."""
+    state = []
+    for sch in schedules:
+        if sch["delta"] == 0 or (sch["rho_end"] - sch["rho_start"]) * sch["delta"] < 0:
+            raise ValueError("delta must move rho_start towards rho_end")
+        ts = sch["t_sample"]
+        interval = ts if callable(ts) else (lambda r, ts=ts: ts)
+        state.append(dict(sch=sch, interval=interval, k=0, rho=sch["rho_start"], out=[],
+                          left=int(interval(sch["rho_start"]))))
+
+    def active(st):
+        sch = st["sch"]
+        return (st["rho"] - sch["rho_end"]) * (1 if sch["delta"] > 0 else -1) <= 1e-12
+
+    while any(active(st) for st in state):
+        n = min(st["left"] for st in state if active(st))
+        sim.step(n)
+        for st in state:
+            if not active(st):
+                continue
+            st["left"] -= n
+            if st["left"] == 0:
+                sch = st["sch"]
+                st["out"].append((st["rho"], sim.observables(sch["lattice"])))
+                sim.add_density(sch["delta"], sch["lattice"])
+                st["k"] += 1
+                st["rho"] = sch["rho_start"] + st["k"] * sch["delta"]
+                if active(st):
+                    st["left"] = int(st["interval"](st["rho"]))
+    return [st["out"] for st in state]
 
 
 def phase_densities(rho, width: int = PHASE_WINDOW):

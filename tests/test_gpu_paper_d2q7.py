@@ -101,32 +101,42 @@ def test_mips_phase_separation_stops_near_paper_sigma():
     assert gaps[-1] < gaps[0], gaps  # liquid and gas approach each other towards the critical noise
 
 
-def _cil_sweep(direction, runs, seed):
-    """phi of every run at every density of one App. C.3 sweep (increasing or decreasing)."""
+def _cil_up_and_down(runs, seed):
+    """phi of every run at every density of the App. C.3 increasing and
+    decreasing sweeps, `runs` of each, all in one batch (each lattice on its
+    own sampling schedule)."""
     from paper_1902_00530_gb300 import Lattice, Simulation
     from paper_1902_00530_gb300 import regimes as R
     proc = G["cil_hysteresis_procedure"]
     d = W.preset("CIL_Q7_PAPER")
     model = d.pop("model")
     nx, ny = G["boxes"]["cil"]
-    if direction > 0:
-        r0, r1, delta = proc["rho_start"], proc["rho_end"], proc["delta"]
-    else:
-        r0, r1, delta = proc["rho_start_down"], proc["rho_start"], -proc["delta"]
-    sim = Simulation([Lattice(nx, ny, "f32", k, "d2q7") for k in range(runs)], [model] * runs, [d] * runs)
-    sim.init(seed, [dict(W.INIT_PAPER_CIL, rho_mean=r0)] * runs)
+    up0, down0 = proc["rho_start"], proc["rho_start_down"]
+    sim = Simulation([Lattice(nx, ny, "f32", k, "d2q7") for k in range(2 * runs)], [model] * (2 * runs),
+                     [d] * (2 * runs))
+    sim.init(seed, [dict(W.INIT_PAPER_CIL, rho_mean=up0 if k < runs else down0) for k in range(2 * runs)])
     sim.step(proc["init_steps"])
-    sweep = R.density_sweep(sim, r0, r1, delta, proc["t_sample_low"],
-                            t_sample_of=lambda r: proc["t_sample_high"] if r > proc["t_switch_rho"] + 1e-9
-                            else proc["t_sample_low"], sample=list(range(runs)))
+    ts = lambda r: proc["t_sample_high"] if r > proc["t_switch_rho"] + 1e-9 else proc["t_sample_low"]
+    sched = [dict(lattice=k, rho_start=up0, rho_end=proc["rho_end"], delta=proc["delta"], t_sample=ts)
+             for k in range(runs)]
+    sched += [dict(lattice=runs + k, rho_start=down0, rho_end=up0, delta=-proc["delta"], t_sample=ts)
+              for k in range(runs)]
+    out = R.density_sweeps(sim, sched)
     sim.close()
-    return {round(r, 4): [o["phi"] for o in obs] for r, obs in sweep}
+
+    def collect(series):
+        by = {}
+        for seq in series:
+            for r, o in seq:
+                by.setdefault(round(r, 4), []).append(o["phi"])
+        return by
+    return collect(out[:runs]), collect(out[runs:])
 
 
 def test_cil_hysteresis_loops_at_the_transitions():
     """Fig. Hysteresis (a): increasing and decreasing runs at A = 2 (App. C.3;
-    the runs reinitialised between directions), sixteen runs per direction as
-    one batch.  The mean phi of the two directions must coincide across the
+    independently initialised), sixteen runs per direction, all 32 in one
+    batch with their own sampling schedules.  The mean phi of the two directions must coincide across the
     homogeneous ordered range well inside the paper's B and RB snapshot densities
     (every point within 4.5 standard errors), and must split by more than 5
     standard errors somewhere between the HD and B snapshot densities and
@@ -134,8 +144,7 @@ def test_cil_hysteresis_loops_at_the_transitions():
     return to disorder at high density."""
     import numpy as np
     hyst = G["cil_hysteresis"]
-    up = _cil_sweep(+1, 16, W.seed(21))
-    down = _cil_sweep(-1, 16, W.seed(22))
+    up, down = _cil_up_and_down(16, W.seed(21))
     z = {}
     for r in up:
         if r in down:

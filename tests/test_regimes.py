@@ -97,3 +97,39 @@ def test_phase_densities_window():
     assert abs(liq - max(w)) < 1e-14 and abs(gas - min(w)) < 1e-14
     with pytest.raises(ValueError):
         R.phase_densities(prof, width=0)
+
+
+class FakeBatch:
+    """Per-lattice mean densities and a step clock, for the batched sweeps."""
+
+    def __init__(self, rhos):
+        self.rho = list(rhos)
+        self.t = 0
+        self.log = []
+
+    def step(self, n):
+        self.t += n
+        self.log.append(("step", n))
+
+    def observables(self, lattice=0):
+        return {"rho": self.rho[lattice], "t": self.t}
+
+    def add_density(self, delta, lattice=-1):
+        self.rho[lattice] += delta
+
+
+def test_density_sweeps_follow_each_schedule():
+    """An increasing and a decreasing run in one batch, each sampled on its
+    own App. C.3 interval (500 steps above rho-bar 0.2, 1500 below)."""
+    ts = lambda r: 500 if r > 0.2 + 1e-9 else 1500
+    sim = FakeBatch([0.195, 0.21])
+    up, down = R.density_sweeps(sim, [dict(lattice=0, rho_start=0.195, rho_end=0.205, delta=0.005, t_sample=ts),
+                                      dict(lattice=1, rho_start=0.21, rho_end=0.2, delta=-0.005, t_sample=ts)])
+    assert [round(r, 6) for r, _ in up] == [0.195, 0.2, 0.205]
+    assert [round(r, 6) for r, _ in down] == [0.21, 0.205, 0.2]
+    # each sample taken after its own interval, before its density change
+    assert [o["t"] for _, o in up] == [1500, 3000, 3500]
+    assert [o["t"] for _, o in down] == [500, 1000, 2500]
+    assert all(abs(o["rho"] - r) < 1e-12 for r, o in up + down)
+    with pytest.raises(ValueError):
+        R.density_sweeps(sim, [dict(lattice=0, rho_start=0.1, rho_end=0.2, delta=-0.01, t_sample=10)])
