@@ -160,19 +160,20 @@ def test_cil_hysteresis_loops_at_the_transitions():
 
 def test_cil_phase_diagram_closes_near_paper_critical_point():
     """Fig. PhaseDiagram (App. C.4 procedure: fixed A, rho-bar up by 0.01 every
-    10^4 steps), eight runs at each of A = 2, 2.5 and 3 in one batch: the range
+    10^4 steps), eight runs at each of A = 0, 2, 2.5 and 3 in one batch: the range
     of densities where the majority of runs is ordered (B, HO or RB) narrows
     as A grows and is empty at A = 3, above the paper's critical point
     A_c ~ 2.75, where its four transition lines meet (Sec. 5); at A = 2.5 the
     homogeneous ordered window still holds the paper's rho-bar_c ~ 0.18.
-    Above B - A rho-bar^2 = 0 every run is classified motionless."""
+    Above B - A rho-bar^2 = 0 every run is classified motionless.  At A = 0 the
+    model is a plain polar active fluid (Sec. 5): B and HO appear, RB does not."""
     from paper_1902_00530_gb300 import Lattice, Simulation
     from paper_1902_00530_gb300 import regimes as R
     pd, proc = G["cil_phase_diagram"], G["cil_hysteresis_procedure"]
     d0 = W.preset("CIL_Q7_PAPER")
     model = d0.pop("model")
     nx, ny = G["boxes"]["cil"]
-    As, runs = (2.0, 2.5, 3.0), 8
+    As, runs = (0.0, 2.0, 2.5, 3.0), 8
     lats = [Lattice(nx, ny, "f32", a * runs + r, "d2q7") for a in range(len(As)) for r in range(runs)]
     prms = [dict(d0, A=A) for A in As for _ in range(runs)]
     sim = Simulation(lats, [model] * len(lats), prms)
@@ -182,14 +183,15 @@ def test_cil_phase_diagram_closes_near_paper_critical_point():
                   t_sample=pd["t_sample"]) for k in range(len(lats))]
     out = R.density_sweeps(sim, sched)
     sim.close()
-    ordered, ho = {}, {}
+    ordered, ho, majority = {}, {}, {}
     for a, A in enumerate(As):
-        ordered[A], ho[A] = [], []
+        ordered[A], ho[A], majority[A] = [], [], []
         for j in range(len(out[0])):
             rho = out[a * runs][j][0]
             cls = [R.classify_cil(o["phi"], o["drho_y"], o["zeta"], A=A, B=d0["B"], rho_bar=rho)
                    for o in (out[a * runs + r][j][1] for r in range(runs))]
             top, n = Counter(cls).most_common(1)[0]
+            majority[A].append(top if n > runs // 2 else None)
             if 0.3 - A * rho * rho <= 0:
                 assert cls == ["motionless"] * runs, (A, rho, cls)
             if n > runs // 2 and top in ("B", "HO", "RB"):
@@ -198,3 +200,5 @@ def test_cil_phase_diagram_closes_near_paper_critical_point():
                 ho[A].append(rho)
     assert len(ordered[2.0]) > len(ordered[2.5]) > 0 and ordered[3.0] == [], ordered
     assert min(ho[2.5]) - 1e-9 <= pd["rho_bar_c"] <= max(ho[2.5]) + 1e-9, ho[2.5]
+    # A = 0 (Sec. 5): a Vicsek-like polar fluid, HD -> B -> HO, no reverse banding
+    assert "B" in majority[0.0] and "HO" in majority[0.0] and "RB" not in majority[0.0], majority[0.0]
