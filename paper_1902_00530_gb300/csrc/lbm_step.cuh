@@ -150,6 +150,8 @@ __device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a
 __device__ __forceinline__ float2 vsub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
 __device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float vneg(float a) { return -a; }
+__device__ __forceinline__ float2 vneg(float2 a) { return make_float2(-a.x, -a.y); }
 
 template <typename V> __device__ __forceinline__ V splat(float s);
 template <> __device__ __forceinline__ float splat<float>(float s) { return s; }
@@ -217,28 +219,30 @@ __device__ __forceinline__ V collide_v(V f[9], V gx, V gy, const SiteParams &d, 
     // step 3: u* of the model
     V sx, sy;
     ustar_v<MODEL, V>(rho, ux, uy, gx, gy, d, sx, sy);
-    // step 3 (cont.): f^SS = w rho [1 + 3 e.u* + 9/2 (e.u*)^2 - 3/2 |u*|^2].  The
+    // step 3 (cont.): f^SS = w rho [1 + 3 e.u* + 9/2 (e.u*)^2 - 3/2 |u*|^2].  With
+    // r = w rho folded into the constants, each opposite pair (e.u* = +-a) is
+    // t = r (1 - 3/2 |u*|^2) + (9/2) r a^2 and t +- 3 r a: one multiply and three
+    // fused multiply-adds (r = rho/9 on the axes, rho/36 on the diagonals).  The
     // rest population takes rho minus the moving ones: identical in exact
     // arithmetic, but the FP32 weights sum to 1 + 7.5e-9, which would otherwise
     // change the mass by that much at every collision.
     const V base = vfma(splat<V>(-1.5f), vfma(sx, sx, vmul(sy, sy)), splat<V>(1.f));
-    const V r1 = vmul(splat<V>(wq(1)), rho), r5 = vmul(splat<V>(wq(5)), rho);
+    const V b1 = vmul(vmul(splat<V>(wq(1)), rho), base), b5 = vmul(vmul(splat<V>(wq(5)), rho), base);
+    const V q1 = vmul(splat<V>(0.5f), rho), q5 = vmul(splat<V>(0.125f), rho);
+    const V k1 = vmul(splat<V>(1.f / 3.f), rho), k5 = vmul(splat<V>(1.f / 12.f), rho);
     V eq[9];
     {
-        // the odd term 3 e.u* is rounded once and shared by each opposite pair
-        const V tx = vfma(vmul(splat<V>(4.5f), sx), sx, base), ty = vfma(vmul(splat<V>(4.5f), sy), sy, base);
-        const V hx = vmul(splat<V>(3.f), sx), hy = vmul(splat<V>(3.f), sy);
-        eq[1] = vmul(r1, vadd(tx, hx));
-        eq[3] = vmul(r1, vsub(tx, hx));
-        eq[2] = vmul(r1, vadd(ty, hy));
-        eq[4] = vmul(r1, vsub(ty, hy));
         const V p = vadd(sx, sy), m = vsub(sy, sx);
-        const V tp = vfma(vmul(splat<V>(4.5f), p), p, base), tm = vfma(vmul(splat<V>(4.5f), m), m, base);
-        const V hp = vmul(splat<V>(3.f), p), hm = vmul(splat<V>(3.f), m);
-        eq[5] = vmul(r5, vadd(tp, hp));
-        eq[7] = vmul(r5, vsub(tp, hp));
-        eq[6] = vmul(r5, vadd(tm, hm));
-        eq[8] = vmul(r5, vsub(tm, hm));
+        const V tx = vfma(vmul(q1, sx), sx, b1), ty = vfma(vmul(q1, sy), sy, b1);
+        const V tp = vfma(vmul(q5, p), p, b5), tm = vfma(vmul(q5, m), m, b5);
+        eq[1] = vfma(k1, sx, tx);
+        eq[3] = vfma(vneg(k1), sx, tx);
+        eq[2] = vfma(k1, sy, ty);
+        eq[4] = vfma(vneg(k1), sy, ty);
+        eq[5] = vfma(k5, p, tp);
+        eq[7] = vfma(vneg(k5), p, tp);
+        eq[6] = vfma(k5, m, tm);
+        eq[8] = vfma(vneg(k5), m, tm);
         eq[0] = vsub(rho, vadd(vadd(vadd(eq[1], eq[3]), vadd(eq[2], eq[4])), vadd(vadd(eq[5], eq[7]), vadd(eq[6], eq[8]))));
     }
     // step 4: BGK redistribution f = f* - (f* - f^SS)/tau, and step 5: the
