@@ -223,9 +223,7 @@ __device__ __forceinline__ V collide_v(V f[9], V gx, V gy, const SiteParams &d, 
     // r = w rho folded into the constants, each opposite pair (e.u* = +-a) is
     // t = r (1 - 3/2 |u*|^2) + (9/2) r a^2 and t +- 3 r a: one multiply and three
     // fused multiply-adds (r = rho/9 on the axes, rho/36 on the diagonals).  The
-    // rest population takes rho minus the moving ones: identical in exact
-    // arithmetic, but the FP32 weights sum to 1 + 7.5e-9, which would otherwise
-    // change the mass by that much at every collision.
+    // rest population's f^SS_0 is not formed (see below).
     const V base = vfma(splat<V>(-1.5f), vfma(sx, sx, vmul(sy, sy)), splat<V>(1.f));
     const V b1 = vmul(vmul(splat<V>(wq(1)), rho), base), b5 = vmul(vmul(splat<V>(wq(5)), rho), base);
     const V q1 = vmul(splat<V>(0.5f), rho), q5 = vmul(splat<V>(0.125f), rho);
@@ -243,18 +241,25 @@ __device__ __forceinline__ V collide_v(V f[9], V gx, V gy, const SiteParams &d, 
         eq[7] = vfma(vneg(k5), p, tp);
         eq[6] = vfma(k5, m, tm);
         eq[8] = vfma(vneg(k5), m, tm);
-        eq[0] = vsub(rho, vadd(vadd(vadd(eq[1], eq[3]), vadd(eq[2], eq[4])), vadd(vadd(eq[5], eq[7]), vadd(eq[6], eq[8]))));
     }
     // step 4: BGK redistribution f = f* - (f* - f^SS)/tau, and step 5: the
-    // zero-sum noise, added in the same expression: f* + eta + (f^SS - f*)/tau
+    // zero-sum noise, added in the same expression: f* + eta + (f^SS - f*)/tau,
+    // for the eight moving populations
     const V om = splat<V>(d.omega);
     if (noise) {
 #pragma unroll
-        for (int i = 0; i < 9; ++i) f[i] = vfma(om, vsub(eq[i], f[i]), vadd(f[i], eta[i]));
+        for (int i = 1; i < 9; ++i) f[i] = vfma(om, vsub(eq[i], f[i]), vadd(f[i], eta[i]));
     } else {
 #pragma unroll
-        for (int i = 0; i < 9; ++i) f[i] = vfma(om, vsub(eq[i], f[i]), f[i]);
+        for (int i = 1; i < 9; ++i) f[i] = vfma(om, vsub(eq[i], f[i]), f[i]);
     }
+    // The rest population is rho minus the new moving ones.  Since sum_i f^SS_i
+    // = rho and sum_i eta_i = 0, this equals f*_0 + eta_0 + (f^SS_0 - f*_0)/tau in
+    // exact arithmetic; in FP32 it conserves the mass to one rounding (the
+    // rounded weights w_i sum to 1 + 7.5e-9, so a separately formed f^SS_0 would
+    // not), and the rest population, with e_0 = 0, absorbs the rounding of the
+    // noise sum without a momentum kick.
+    f[0] = vsub(rho, vadd(vadd(vadd(f[1], f[3]), vadd(f[2], f[4])), vadd(vadd(f[5], f[7]), vadd(f[6], f[8]))));
     return rho;
 }
 
@@ -311,13 +316,11 @@ __device__ __forceinline__ void noise_u(uint32_t x, uint32_t y, uint32_t t, uint
     u[8] = u_from_bits(m8 << 9);
 }
 
-// eta_i = 2 sigma (u_i - mean u) (the sum of nine u in [1, 2) is exact in
-// FP32).  The rest population takes minus the sum of the eight moving ones,
-// which is the same in exact arithmetic and keeps sum eta = 0 to one unbiased
-// rounding.  The rounded shift -2 sigma sum(u) / 9 is shared by the eight
-// moving directions, so its rounding error cancels in sum_i eta_i e_i; the
-// absorber must be the rest population, whose e_0 = 0: a moving one would
-// turn that error into the same momentum kick at every site and step.
+// eta_i = 2 sigma (u_i - mean u) for the eight moving directions (the sum of
+// nine u in [1, 2) is exact in FP32).  The rounded shift -2 sigma sum(u) / 9 is
+// shared by them, so its rounding error cancels in sum_i eta_i e_i.  eta_0 =
+// -sum of the others is never formed: the collide sets the rest population
+// from the mass, which adds exactly that amount.
 template <typename V>
 __device__ __forceinline__ void eta_from_u(const V u[9], float two_sigma, V eta[9])
 {
@@ -325,8 +328,7 @@ __device__ __forceinline__ void eta_from_u(const V u[9], float two_sigma, V eta[
     const V shift = vmul(su, splat<V>(-two_sigma * (1.f / 9.f)));
 #pragma unroll
     for (int i = 1; i < 9; ++i) eta[i] = vfma(splat<V>(two_sigma), u[i], shift);
-    eta[0] = vsub(splat<V>(0.f),
-                  vadd(vadd(vadd(eta[1], eta[2]), vadd(eta[3], eta[4])), vadd(vadd(eta[5], eta[6]), vadd(eta[7], eta[8]))));
+    eta[0] = splat<V>(0.f);
 }
 
 // The update of a lane's VEC sites, one site at a time.  f[i][j] holds f*_i

@@ -149,9 +149,9 @@ __device__ __forceinline__ void mips_gradients7(const float rm[VEC + 2], const f
 constexpr float Q7_HALF_SQRT3 = 0.86602540378443865f;
 
 // Steps 2-5 on one D2Q7 site; returns rho.  Same conventions as collide_v:
-// explicit round-to-nearest operations, the rest population taking rho minus
-// the moving ones (weights 1/12 are inexact in FP32), the noise added inside
-// the BGK expression.
+// explicit round-to-nearest operations, the noise added inside the BGK
+// expression of the moving populations, and the rest population set to rho
+// minus the new moving ones (the weights 1/12 are inexact in FP32).
 template <int MODEL>
 __device__ __forceinline__ float collide7(float f[7], float gx, float gy, const SiteParams &d, bool noise,
                                           const float eta[7], const float *rho_known)
@@ -181,16 +181,16 @@ __device__ __forceinline__ float collide7(float f[7], float gx, float gy, const 
     eq[5] = __fmaf_rn(-k, a2, t2);
     eq[3] = __fmaf_rn(k, a3, t3);
     eq[6] = __fmaf_rn(-k, a3, t3);
-    eq[0] = __fsub_rn(rho, __fadd_rn(__fadd_rn(__fadd_rn(eq[1], eq[4]), __fadd_rn(eq[2], eq[5])),
-                                     __fadd_rn(eq[3], eq[6])));
     const float om = d.omega;
     if (noise) {
 #pragma unroll
-        for (int i = 0; i < 7; ++i) f[i] = __fmaf_rn(om, __fsub_rn(eq[i], f[i]), __fadd_rn(f[i], eta[i]));
+        for (int i = 1; i < 7; ++i) f[i] = __fmaf_rn(om, __fsub_rn(eq[i], f[i]), __fadd_rn(f[i], eta[i]));
     } else {
 #pragma unroll
-        for (int i = 0; i < 7; ++i) f[i] = __fmaf_rn(om, __fsub_rn(eq[i], f[i]), f[i]);
+        for (int i = 1; i < 7; ++i) f[i] = __fmaf_rn(om, __fsub_rn(eq[i], f[i]), f[i]);
     }
+    // the rest population from the mass, as on D2Q9 (collide_v)
+    f[0] = __fsub_rn(rho, __fadd_rn(__fadd_rn(__fadd_rn(f[1], f[4]), __fadd_rn(f[2], f[5])), __fadd_rn(f[3], f[6])));
     return rho;
 }
 
@@ -212,8 +212,8 @@ __device__ __forceinline__ void negative_correction7(float f[7], float rho)
 
 // D2Q7 noise: one Philox call, the 16-bit halves h_0..h_6 as variates
 // s_i = (2 h_i + 1 - 2^16) 2^-16 = 2 u_i - 3 with u_i = 1 + (h_i + 1/2) 2^-16
-// built as FP32 bits; eta_i = 2 sigma (u_i - mean u), the rest population
-// taking minus the sum of the moving ones (see eta_from_u).
+// built as FP32 bits; eta_i = 2 sigma (u_i - mean u) for the moving ones, the
+// rest population's share coming with the mass closure (see eta_from_u).
 __device__ __forceinline__ void noise_eta7(uint32_t x, uint32_t y, uint32_t t, uint32_t id, const uint32_t *rk,
                                            float two_sigma, float eta[7])
 {
@@ -229,8 +229,7 @@ __device__ __forceinline__ void noise_eta7(uint32_t x, uint32_t y, uint32_t t, u
     const float shift = __fmul_rn(su, -two_sigma * (1.f / 7.f));
 #pragma unroll
     for (int i = 1; i < 7; ++i) eta[i] = __fmaf_rn(two_sigma, u[i], shift);
-    eta[0] = __fsub_rn(0.f, __fadd_rn(__fadd_rn(__fadd_rn(eta[1], eta[2]), __fadd_rn(eta[3], eta[4])),
-                                      __fadd_rn(eta[5], eta[6])));
+    eta[0] = 0.f;
 }
 
 template <int VEC>
