@@ -119,13 +119,14 @@ __device__ __forceinline__ void density_window(const float f[9][VEC], const type
 
 // Model parameters of one lattice, held in registers.
 struct SiteParams {
-    float omega, sigma_q, C, inv_rho_star, rho_star, u_max, u_max2, A, B;
+    float omega, omc, sigma_q, C, inv_rho_star, rho_star, u_max, u_max2, A, B;  // omc = 1 - omega
 };
 
 __device__ __forceinline__ SiteParams load_params(const LatDesc *dp)
 {
     SiteParams p;
     p.omega = dp->omega;
+    p.omc = __fsub_rn(1.f, dp->omega);  // exact for tau in [1/2, 2] (Sterbenz)
     p.sigma_q = dp->sigma_q;
     p.C = dp->C;
     p.inv_rho_star = dp->inv_rho_star;
@@ -243,12 +244,15 @@ __device__ __forceinline__ V collide_v(V f[9], V gx, V gy, const SiteParams &d, 
         eq[8] = vfma(vneg(k5), m, tm);
     }
     // step 4: BGK redistribution f = f* - (f* - f^SS)/tau, and step 5: the
-    // zero-sum noise, added in the same expression: f* + eta + (f^SS - f*)/tau,
-    // for the eight moving populations
+    // zero-sum noise, for the eight moving populations.  With noise, as
+    // (1 - 1/tau) f* + (f^SS/tau + eta): two fused multiply-adds (the mass is
+    // closed by the rest population below, so the form need not conserve it);
+    // without, as f* + (f^SS - f*)/tau, which stays accurate near equilibrium.
     const V om = splat<V>(d.omega);
     if (noise) {
+        const V omc = splat<V>(d.omc);
 #pragma unroll
-        for (int i = 1; i < 9; ++i) f[i] = vfma(om, vsub(eq[i], f[i]), vadd(f[i], eta[i]));
+        for (int i = 1; i < 9; ++i) f[i] = vfma(omc, f[i], vfma(om, eq[i], eta[i]));
     } else {
 #pragma unroll
         for (int i = 1; i < 9; ++i) f[i] = vfma(om, vsub(eq[i], f[i]), f[i]);

@@ -184,7 +184,7 @@ __device__ __forceinline__ float collide7(float f[7], float gx, float gy, const 
     const float om = d.omega;
     if (noise) {
 #pragma unroll
-        for (int i = 1; i < 7; ++i) f[i] = __fmaf_rn(om, __fsub_rn(eq[i], f[i]), __fadd_rn(f[i], eta[i]));
+        for (int i = 1; i < 7; ++i) f[i] = __fmaf_rn(d.omc, f[i], __fmaf_rn(om, eq[i], eta[i]));  // as on D2Q9
     } else {
 #pragma unroll
         for (int i = 1; i < 7; ++i) f[i] = __fmaf_rn(om, __fsub_rn(eq[i], f[i]), f[i]);
