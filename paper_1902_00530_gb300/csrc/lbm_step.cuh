@@ -173,14 +173,17 @@ __device__ __forceinline__ V vdensity(const V f[9])
     return vadd(vadd(vadd(vadd(f[0], f[1]), vadd(f[2], f[3])), vadd(vadd(f[4], f[5]), vadd(f[6], f[7]))), f[8]);
 }
 
-// Step 3: the steady-state velocity u* of the model from rho, u and (MIPS)
-// grad rho; independent of the lattice.
+// Step 3: the steady-state velocity u* of the model from rho, the momentum
+// j = rho u and (MIPS) grad rho; independent of the lattice.  Only the passive
+// model needs u = j/rho itself: the MIPS u* does not depend on u, and the CIL
+// u* only on its direction u/|u| = j/|j|.
 template <int MODEL, typename V>
-__device__ __forceinline__ void ustar_v(V rho, V ux, V uy, V gx, V gy, const SiteParams &d, V &sx, V &sy)
+__device__ __forceinline__ void ustar_v(V rho, V jx, V jy, V gx, V gy, const SiteParams &d, V &sx, V &sy)
 {
     if constexpr (MODEL == MODEL_PASSIVE) {
-        sx = ux;
-        sy = uy;
+        const V inv = vmap(rho, [](float r) { return r > 0.f ? __frcp_rn(r) : 0.f; });  // u = 0 where rho <= 0
+        sx = vmul(jx, inv);
+        sy = vmul(jy, inv);
     } else if constexpr (MODEL == MODEL_MIPS) {
         // Eq. (bu_mips): C (1 - rho/rho*) grad rho below rho*, then |u*| <= U_max
         const V c0 = vmul(splat<V>(d.C), vfma(vsub(splat<V>(0.f), rho), splat<V>(d.inv_rho_star), splat<V>(1.f)));
@@ -194,20 +197,22 @@ __device__ __forceinline__ void ustar_v(V rho, V ux, V uy, V gx, V gy, const Sit
         sx = vmul(sx, sc);
         sy = vmul(sy, sc);
     } else {
-        // Eqs. (bu_CIL), (U0): U0(rho) u/|u|, U0 = max(B - A rho^2, 0); u* = 0 where u = 0
+        // Eqs. (bu_CIL), (U0): U0(rho) j/|j|, U0 = max(B - A rho^2, 0); u* = 0
+        // where u = 0 (j = 0, or rho <= 0)
         const V ar2 = vmul(vmul(splat<V>(d.A), rho), rho);
         const float B = d.B;
-        const V U0 = vmap(ar2, [B](float q) { return B >= q ? __fsub_rn(B, q) : 0.f; });
-        const V m2 = vfma(ux, ux, vmul(uy, uy));
+        const V U0 = vmap2(ar2, rho, [B](float q, float r) { return (B >= q && r > 0.f) ? __fsub_rn(B, q) : 0.f; });
+        const V m2 = vfma(jx, jx, vmul(jy, jy));
         const V sc = vmap2(U0, m2, [](float u0, float q) { return q > 0.f ? __fmul_rn(u0, rsqrtf(q)) : 0.f; });
-        sx = vmul(ux, sc);
-        sy = vmul(uy, sc);
+        sx = vmul(jx, sc);
+        sy = vmul(jy, sc);
     }
 }
 
 // Steps 2-5: moments of f*, u*, f^SS, BGK, noise.  Returns rho (for step 6).
+// u[i] are the site's noise uniforms (noise_u), read only when noise is on.
 template <int MODEL, typename V>
-__device__ __forceinline__ V collide_v(V f[9], V gx, V gy, const SiteParams &d, bool noise, const V eta[9],
+__device__ __forceinline__ V collide_v(V f[9], V gx, V gy, const SiteParams &d, bool noise, const V u[9],
                                        const V *rho_known = nullptr)
 {
     // step 2: moments of f* (rho may come precomputed, bitwise equal: the MIPS
@@ -215,20 +220,32 @@ __device__ __forceinline__ V collide_v(V f[9], V gx, V gy, const SiteParams &d, 
     const V rho = rho_known ? *rho_known : vdensity(f);
     const V jx = vsub(vadd(vadd(f[1], f[5]), f[8]), vadd(vadd(f[3], f[6]), f[7]));
     const V jy = vsub(vadd(vadd(f[2], f[5]), f[6]), vadd(vadd(f[4], f[7]), f[8]));
-    const V inv = vmap(rho, [](float r) { return r > 0.f ? __frcp_rn(r) : 0.f; });  // u = 0 where rho <= 0
-    const V ux = vmul(jx, inv), uy = vmul(jy, inv);
     // step 3: u* of the model
     V sx, sy;
-    ustar_v<MODEL, V>(rho, ux, uy, gx, gy, d, sx, sy);
+    ustar_v<MODEL, V>(rho, jx, jy, gx, gy, d, sx, sy);
     // step 3 (cont.): f^SS = w rho [1 + 3 e.u* + 9/2 (e.u*)^2 - 3/2 |u*|^2].  With
-    // r = w rho folded into the constants, each opposite pair (e.u* = +-a) is
-    // t = r (1 - 3/2 |u*|^2) + (9/2) r a^2 and t +- 3 r a: one multiply and three
-    // fused multiply-adds (r = rho/9 on the axes, rho/36 on the diagonals).  The
-    // rest population's f^SS_0 is not formed (see below).
+    // r = w R folded into the constants, each opposite pair (e.u* = +-a) is
+    // t = r (1 - 3/2 |u*|^2) + c + (9/2) r a^2 and t +- 3 r a: one multiply and
+    // three fused multiply-adds (r = R/9 on the axes, R/36 on the diagonals).
+    // Without noise R = rho and c = 0, giving f^SS.  With noise R = rho/tau and c
+    // is the shift of the zero-sum noise, eta_i = 2 sigma u_i + c with c = -2
+    // sigma (sum_j u_j)/9 (the sum is exact: nine multiples of 2^-15 below 2),
+    // giving f^SS/tau + c.  The rest population's f^SS_0 is not formed
+    // (see below).
+    const V om = splat<V>(d.omega);
     const V base = vfma(splat<V>(-1.5f), vfma(sx, sx, vmul(sy, sy)), splat<V>(1.f));
-    const V b1 = vmul(vmul(splat<V>(wq(1)), rho), base), b5 = vmul(vmul(splat<V>(wq(5)), rho), base);
-    const V q1 = vmul(splat<V>(0.5f), rho), q5 = vmul(splat<V>(0.125f), rho);
-    const V k1 = vmul(splat<V>(1.f / 3.f), rho), k5 = vmul(splat<V>(1.f / 12.f), rho);
+    const V R = noise ? vmul(om, rho) : rho;
+    V b1, b5;
+    if (noise) {
+        const V c = vmul(vdensity(u), splat<V>(-d.sigma_q * (1.f / 9.f)));
+        b1 = vfma(vmul(splat<V>(wq(1)), R), base, c);
+        b5 = vfma(vmul(splat<V>(wq(5)), R), base, c);
+    } else {
+        b1 = vmul(vmul(splat<V>(wq(1)), R), base);
+        b5 = vmul(vmul(splat<V>(wq(5)), R), base);
+    }
+    const V q1 = vmul(splat<V>(0.5f), R), q5 = vmul(splat<V>(0.125f), R);
+    const V k1 = vmul(splat<V>(1.f / 3.f), R), k5 = vmul(splat<V>(1.f / 12.f), R);
     V eq[9];
     {
         const V p = vadd(sx, sy), m = vsub(sy, sx);
@@ -245,14 +262,14 @@ __device__ __forceinline__ V collide_v(V f[9], V gx, V gy, const SiteParams &d, 
     }
     // step 4: BGK redistribution f = f* - (f* - f^SS)/tau, and step 5: the
     // zero-sum noise, for the eight moving populations.  With noise, as
-    // (1 - 1/tau) f* + (f^SS/tau + eta): two fused multiply-adds (the mass is
-    // closed by the rest population below, so the form need not conserve it);
-    // without, as f* + (f^SS - f*)/tau, which stays accurate near equilibrium.
-    const V om = splat<V>(d.omega);
+    // (1 - 1/tau) f* + (f^SS/tau + c + 2 sigma u_i): two fused multiply-adds (the
+    // mass is closed by the rest population below, so the form need not conserve
+    // it); without, as f* + (f^SS - f*)/tau, which stays accurate near
+    // equilibrium.
     if (noise) {
-        const V omc = splat<V>(d.omc);
+        const V omc = splat<V>(d.omc), ts = splat<V>(d.sigma_q);
 #pragma unroll
-        for (int i = 1; i < 9; ++i) f[i] = vfma(omc, f[i], vfma(om, eq[i], eta[i]));
+        for (int i = 1; i < 9; ++i) f[i] = vfma(omc, f[i], vfma(ts, u[i], eq[i]));
     } else {
 #pragma unroll
         for (int i = 1; i < 9; ++i) f[i] = vfma(om, vsub(eq[i], f[i]), f[i]);
@@ -261,8 +278,9 @@ __device__ __forceinline__ V collide_v(V f[9], V gx, V gy, const SiteParams &d, 
     // = rho and sum_i eta_i = 0, this equals f*_0 + eta_0 + (f^SS_0 - f*_0)/tau in
     // exact arithmetic; in FP32 it conserves the mass to one rounding (the
     // rounded weights w_i sum to 1 + 7.5e-9, so a separately formed f^SS_0 would
-    // not), and the rest population, with e_0 = 0, absorbs the rounding of the
-    // noise sum without a momentum kick.
+    // not), and the rest population, with e_0 = 0, takes the noise sum.  The
+    // shift c enters the two members of an opposite pair through the same t,
+    // so its rounding cancels in their difference and gives no momentum kick.
     f[0] = vsub(rho, vadd(vadd(vadd(f[1], f[3]), vadd(f[2], f[4])), vadd(vadd(f[5], f[7]), vadd(f[6], f[8]))));
     return rho;
 }
@@ -304,8 +322,9 @@ __device__ __forceinline__ void negative_correction(float f[9], float rho)
     for (int i = 0; i < 9; ++i) f[i] = __fmul_rn(f[i], sc);
 }
 
-// Zero-sum noise of one site as uniforms u_i = 1 + (m_i + 1/2) 2^-14 (see
-// noise_eta); the paired form turns them into eta below.
+// The noise uniforms of one site, u_i = 1 + (m_i + 1/2) 2^-14 (the variates
+// are s_i = 2 u_i - 3); collide_v turns them into the zero-sum noise eta_i =
+// 2 sigma (u_i - mean u).
 __device__ __forceinline__ void noise_u(uint32_t x, uint32_t y, uint32_t t, uint32_t id, const uint32_t *rk,
                                         float u[9])
 {
@@ -318,21 +337,6 @@ __device__ __forceinline__ void noise_u(uint32_t x, uint32_t y, uint32_t t, uint
     }
     const uint32_t m8 = (w[0] & 0xFu) | ((w[1] & 0xFu) << 4) | ((w[2] & 0xFu) << 8) | ((w[3] & 0x3u) << 12);
     u[8] = u_from_bits(m8 << 9);
-}
-
-// eta_i = 2 sigma (u_i - mean u) for the eight moving directions (the sum of
-// nine u in [1, 2) is exact in FP32).  The rounded shift -2 sigma sum(u) / 9 is
-// shared by them, so its rounding error cancels in sum_i eta_i e_i.  eta_0 =
-// -sum of the others is never formed: the collide sets the rest population
-// from the mass, which adds exactly that amount.
-template <typename V>
-__device__ __forceinline__ void eta_from_u(const V u[9], float two_sigma, V eta[9])
-{
-    const V su = vdensity(u);
-    const V shift = vmul(su, splat<V>(-two_sigma * (1.f / 9.f)));
-#pragma unroll
-    for (int i = 1; i < 9; ++i) eta[i] = vfma(splat<V>(two_sigma), u[i], shift);
-    eta[0] = splat<V>(0.f);
 }
 
 // The update of a lane's VEC sites, one site at a time.  f[i][j] holds f*_i
@@ -348,15 +352,11 @@ __device__ __forceinline__ void collide_sites(float f[9][VEC], const float gxs[V
 {
 #pragma unroll
     for (int j = 0; j < VEC; ++j) {
-        float g[9], eta[9];
+        float g[9], u[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) g[i] = f[i][j];
-        if (noise) {
-            float u[9];
-            noise_u(x0 + j, y, t, id, rk, u);
-            eta_from_u(u, d.sigma_q, eta);
-        }
-        const float rho = collide_v<MODEL, float>(g, gxs[j], gys[j], d, noise, eta, rho_row ? rho_row + j : nullptr);
+        if (noise) noise_u(x0 + j, y, t, id, rk, u);
+        const float rho = collide_v<MODEL, float>(g, gxs[j], gys[j], d, noise, u, rho_row ? rho_row + j : nullptr);
         negative_correction(g, rho);
 #pragma unroll
         for (int i = 0; i < 9; ++i) f[i][j] = g[i];

@@ -149,29 +149,33 @@ __device__ __forceinline__ void mips_gradients7(const float rm[VEC + 2], const f
 constexpr float Q7_HALF_SQRT3 = 0.86602540378443865f;
 
 // Steps 2-5 on one D2Q7 site; returns rho.  Same conventions as collide_v:
-// explicit round-to-nearest operations, the noise added inside the BGK
-// expression of the moving populations, and the rest population set to rho
-// minus the new moving ones (the weights 1/12 are inexact in FP32).
+// explicit round-to-nearest operations; with noise, 1/tau and the noise shift
+// folded into the equilibrium constants and each moving population updated
+// as (1 - 1/tau) f* + (f^SS/tau + c + 2 sigma u_i); the rest population set to
+// rho minus the new moving ones (the weights 1/12 are inexact in FP32).  u[i]
+// are the site's noise uniforms (noise_u7), read only when noise is on.
 template <int MODEL>
 __device__ __forceinline__ float collide7(float f[7], float gx, float gy, const SiteParams &d, bool noise,
-                                          const float eta[7], const float *rho_known)
+                                          const float u[7], const float *rho_known)
 {
     const float rho = rho_known ? *rho_known : density7(f);
     const float jx = __fmaf_rn(0.5f, __fsub_rn(__fadd_rn(f[2], f[6]), __fadd_rn(f[3], f[5])), __fsub_rn(f[1], f[4]));
     const float jy = __fmul_rn(Q7_HALF_SQRT3, __fsub_rn(__fadd_rn(f[2], f[3]), __fadd_rn(f[5], f[6])));
-    const float inv = rho > 0.f ? __frcp_rn(rho) : 0.f;
-    const float ux = __fmul_rn(jx, inv), uy = __fmul_rn(jy, inv);
     float sx, sy;
-    ustar_v<MODEL, float>(rho, ux, uy, gx, gy, d, sx, sy);
+    ustar_v<MODEL, float>(rho, jx, jy, gx, gy, d, sx, sy);
     // e_1.u* = sx, e_2.u* = sx/2 + (sqrt3/2) sy, e_3.u* = (sqrt3/2) sy - sx/2;
-    // e_4..e_6 are their negatives.  With r = rho/12 folded into the constants,
-    // each opposite pair is t = r (1 - 2|u*|^2) + 8 r (e.u*)^2 and t +- 4 r e.u*,
-    // one multiply and three fused multiply-adds
+    // e_4..e_6 are their negatives.  With r = R/12 folded into the constants,
+    // each opposite pair is t = r (1 - 2|u*|^2) + c + 8 r (e.u*)^2 and
+    // t +- 4 r e.u*, one multiply and three fused multiply-adds; R = rho and
+    // c = 0 without noise, R = rho/tau and c = -2 sigma (sum_j u_j)/7 with it
+    const float om = d.omega;
     const float base = __fmaf_rn(-2.f, __fmaf_rn(sx, sx, __fmul_rn(sy, sy)), 1.f);
-    const float r12 = __fmul_rn(1.f / 12.f, rho);
+    const float r12 = __fmul_rn(1.f / 12.f, noise ? __fmul_rn(om, rho) : rho);
     const float hy = __fmul_rn(Q7_HALF_SQRT3, sy), hx = __fmul_rn(0.5f, sx);
     const float a1 = sx, a2 = __fadd_rn(hy, hx), a3 = __fsub_rn(hy, hx);
-    const float b = __fmul_rn(r12, base), q = __fmul_rn(8.f, r12), k = __fmul_rn(4.f, r12);
+    const float b = noise ? __fmaf_rn(r12, base, __fmul_rn(density7(u), -d.sigma_q * (1.f / 7.f)))
+                          : __fmul_rn(r12, base);
+    const float q = __fmul_rn(8.f, r12), k = __fmul_rn(4.f, r12);
     const float t1 = __fmaf_rn(__fmul_rn(q, a1), a1, b), t2 = __fmaf_rn(__fmul_rn(q, a2), a2, b),
                 t3 = __fmaf_rn(__fmul_rn(q, a3), a3, b);
     float eq[7];
@@ -181,10 +185,9 @@ __device__ __forceinline__ float collide7(float f[7], float gx, float gy, const 
     eq[5] = __fmaf_rn(-k, a2, t2);
     eq[3] = __fmaf_rn(k, a3, t3);
     eq[6] = __fmaf_rn(-k, a3, t3);
-    const float om = d.omega;
     if (noise) {
 #pragma unroll
-        for (int i = 1; i < 7; ++i) f[i] = __fmaf_rn(d.omc, f[i], __fmaf_rn(om, eq[i], eta[i]));  // as on D2Q9
+        for (int i = 1; i < 7; ++i) f[i] = __fmaf_rn(d.omc, f[i], __fmaf_rn(d.sigma_q, u[i], eq[i]));
     } else {
 #pragma unroll
         for (int i = 1; i < 7; ++i) f[i] = __fmaf_rn(om, __fsub_rn(eq[i], f[i]), f[i]);
@@ -212,24 +215,18 @@ __device__ __forceinline__ void negative_correction7(float f[7], float rho)
 
 // D2Q7 noise: one Philox call, the 16-bit halves h_0..h_6 as variates
 // s_i = (2 h_i + 1 - 2^16) 2^-16 = 2 u_i - 3 with u_i = 1 + (h_i + 1/2) 2^-16
-// built as FP32 bits; eta_i = 2 sigma (u_i - mean u) for the moving ones, the
-// rest population's share coming with the mass closure (see eta_from_u).
-__device__ __forceinline__ void noise_eta7(uint32_t x, uint32_t y, uint32_t t, uint32_t id, const uint32_t *rk,
-                                           float two_sigma, float eta[7])
+// built as FP32 bits; collide7 turns them into eta_i = 2 sigma (u_i - mean u)
+// (their sum is exact there: seven multiples of 2^-17 below 2).
+__device__ __forceinline__ void noise_u7(uint32_t x, uint32_t y, uint32_t t, uint32_t id, const uint32_t *rk,
+                                         float u[7])
 {
     const uint4 a = philox4x32_10_rk(make_uint4(x, y, t, id & 0xFFFFFFu), rk);
     const uint32_t w[4] = {a.x, a.y, a.z, a.w};
-    float u[7];
 #pragma unroll
     for (int i = 0; i < 7; ++i) {
         const uint32_t h7 = (i & 1) ? ((w[i >> 1] >> 9) & 0x007FFF80u) : ((w[i >> 1] << 7) & 0x007FFF80u);
         u[i] = __uint_as_float(0x3F800040u | h7);
     }
-    const float su = density7(u);  // exact: 17-bit values below 2, at most 7 of them
-    const float shift = __fmul_rn(su, -two_sigma * (1.f / 7.f));
-#pragma unroll
-    for (int i = 1; i < 7; ++i) eta[i] = __fmaf_rn(two_sigma, u[i], shift);
-    eta[0] = 0.f;
 }
 
 template <int VEC>
@@ -278,11 +275,11 @@ __device__ __forceinline__ void q7_row(Q7Walk<VEC> &w, int y, const typename Sto
     float out[7][VEC];
 #pragma unroll
     for (int j = 0; j < VEC; ++j) {
-        float g[7], eta[7];
+        float g[7], u[7];
 #pragma unroll
         for (int i = 0; i < 7; ++i) g[i] = w.fc[i][j];
-        if (noise) noise_eta7((uint32_t)(x0 + j), (uint32_t)y, t, id, rk, d.sigma_q, eta);
-        const float rho = collide7<MODEL>(g, gx[j], gy[j], d, noise, eta, MODEL == MODEL_MIPS ? &w.rc[j + 1] : nullptr);
+        if (noise) noise_u7((uint32_t)(x0 + j), (uint32_t)y, t, id, rk, u);
+        const float rho = collide7<MODEL>(g, gx[j], gy[j], d, noise, u, MODEL == MODEL_MIPS ? &w.rc[j + 1] : nullptr);
         negative_correction7(g, rho);
 #pragma unroll
         for (int i = 0; i < 7; ++i) out[i][j] = g[i];

@@ -9,7 +9,7 @@
 // rows ahead of use.  The half-site column offsets of the brick layout (-1/0
 // from an even row, 0/+1 from an odd one) become shared-memory index offsets;
 // rows are walked in (even, odd) pairs so the parity is a template argument.
-// The per-site arithmetic is collide7 / negative_correction7 / noise_eta7 of
+// The per-site arithmetic is collide7 / negative_correction7 / noise_u7 of
 // lbm_step_q7.cuh, so states are bitwise those of step_kernel_q7.
 //
 // Requirements (checked on the host): nx a multiple of the 16-byte halo width
@@ -232,11 +232,11 @@ __global__ void __launch_bounds__(128, staged7_min_blocks<VEC>()) step_staged_ke
         float out[7][VEC];
 #pragma unroll
         for (int j = 0; j < VEC; ++j) {
-            float g[7], eta[7];
+            float g[7], u[7];
 #pragma unroll
             for (int i = 0; i < 7; ++i) g[i] = f[i][j];
-            if (noise) noise_eta7((uint32_t)(x0 + j), (uint32_t)y, t, id, a.rk, d.sigma_q, eta);
-            const float rho = collide7<MODEL>(g, gx[j], gy[j], d, noise, eta, MIPS ? &rc[j + 1] : nullptr);
+            if (noise) noise_u7((uint32_t)(x0 + j), (uint32_t)y, t, id, a.rk, u);
+            const float rho = collide7<MODEL>(g, gx[j], gy[j], d, noise, u, MIPS ? &rc[j + 1] : nullptr);
             negative_correction7(g, rho);
 #pragma unroll
             for (int i = 0; i < 7; ++i) out[i][j] = g[i];
