@@ -123,14 +123,18 @@ typedef struct lbm_ctx lbm_ctx;
 /* Create a context for one lattice.  Validates the parameters: tau <= 1/2,
  * sigma < 0, a NaN parameter, nx or ny outside [1, 65536], an unknown model or
  * storage, or a non-positive rho_star (MIPS) returns LBM_ERR_INVALID_ARG and
- * sets *out = NULL.  Host only; no CUDA call. */
+ * sets *out = NULL.  A D2Q9 lattice of more than 2^32 population elements per
+ * buffer (9 ny pitch, pitch = nx rounded up to 128 bytes; about 477 million
+ * sites) runs only the shared-memory staged kernel, which needs nx a multiple
+ * of 16 bytes of storage: otherwise LBM_ERR_UNSUPPORTED, *out = NULL.  Host
+ * only; no CUDA call. */
 lbm_status lbm_create(const lbm_lattice *lattice, lbm_model model, const lbm_params *params,
                       lbm_ctx **out);
 
 /* Create a context for n independent lattices advanced together (a batch, as
  * in the paper's sweeps over density and activity, App. C.3-C.4).  Arrays
  * hold n entries.  Lattice k of the batch is addressed by index k below.
- * Same validation as lbm_create.  Host only. */
+ * Same validation and status codes as lbm_create.  Host only. */
 lbm_status lbm_create_batch(int32_t n, const lbm_lattice *lattices, const lbm_model *models,
                             const lbm_params *params, lbm_ctx **out);
 
@@ -219,8 +223,10 @@ lbm_status lbm_load(lbm_ctx *ctx, const char *path);
  * global memory, or 2..8 (MIPS: 3..8; at most 4 warps) for the kernel that
  * stages population rows in shared memory with bulk copies, that many rows
  * per warp (needs nx a multiple of 16 bytes of storage; D2Q7 lattices also
- * need rows even).  Host only;
- * re-uploads descriptors (syncs) when bound. */
+ * need rows even).  stages = 0 is refused (LBM_ERR_INVALID_ARG) while a D2Q9
+ * lattice exceeds 2^32 elements per buffer (see lbm_create); such lattices
+ * start on a staged shape and the tuner tries only staged shapes for them.
+ * Host only; re-uploads descriptors (syncs) when bound. */
 lbm_status lbm_set_tuning(lbm_ctx *ctx, int32_t mode, int32_t vec, int32_t rows, int32_t warps,
                           int32_t stages);
 

@@ -136,11 +136,37 @@ std::string validate(const lbm_lattice &l, int model, const lbm_params &p)
 }
 
 // The staged kernels copy 16-byte halos: nx must be a multiple of that width.
+bool staged_fits(const lbm_lattice &l)
+{
+    const int halo = l.storage == LBM_F32 ? 4 : 8;
+    return l.nx % halo == 0 && l.nx >= halo;
+}
+
 bool staged_ok(const lbm_ctx *c, const GroupHost &g)
 {
-    const int halo = g.storage == LBM_F32 ? 4 : 8;
     for (int m : g.members)
-        if (c->lats[m].lat.nx % halo != 0 || c->lats[m].lat.nx < halo) return false;
+        if (!staged_fits(c->lats[m].lat)) return false;
+    return true;
+}
+
+// Row pitch in elements: nx rounded up to 128 bytes.
+size_t row_pitch(const lbm_lattice &l)
+{
+    const size_t align_elems = 128 / elem_bytes(l.storage);
+    return ((size_t)l.nx + align_elems - 1) / align_elems * align_elems;
+}
+
+// The direct D2Q9 kernel addresses a state buffer by unsigned 32-bit element
+// index (i plane + row pitch + x): its q ny pitch elements must not exceed 2^32.
+bool index32_fits(const lbm_lattice &l, int q)
+{
+    return q != 9 || (size_t)q * (size_t)l.ny * row_pitch(l) <= ((size_t)1 << 32);
+}
+
+bool direct_ok(const lbm_ctx *c, const GroupHost &g)
+{
+    for (int m : g.members)
+        if (!index32_fits(c->lats[m].lat, g.q)) return false;
     return true;
 }
 
@@ -170,8 +196,7 @@ void layout(lbm_ctx *c)
     size_t so = 0;
     for (auto &L : c->lats) {
         const size_t eb = elem_bytes(L.lat.storage);
-        const size_t align_elems = 128 / eb;
-        L.pitch = ((size_t)L.lat.nx + align_elems - 1) / align_elems * align_elems;
+        L.pitch = row_pitch(L.lat);
         L.buf_bytes = align256((size_t)L.q * L.lat.ny * L.pitch * eb);
         L.state_off = so;
         so += 2 * L.buf_bytes;
@@ -440,6 +465,7 @@ lbm_status tune_group(lbm_ctx *c, GroupHost &g)
     for (int m : g.members) max_ny = std::max<long long>(max_ny, c->lats[m].lat.ny);
     const int all_v[] = {1, 2, 4, 8};
     const bool staged = staged_ok(c, g);
+    const bool direct = direct_ok(c, g);
     const int base_stages = g.model == LBM_MIPS ? 4 : 3;
     for (int v : all_v) {
         if (!allowed_vec(g.storage, v)) continue;
@@ -448,7 +474,8 @@ lbm_status tune_group(lbm_ctx *c, GroupHost &g)
         if (!ok) continue;
         for (int r : {16, 32, 64, 128}) {
             if (r > 16 && r > 2 * max_ny) continue;
-            for (int w : {4, 8}) cands.push_back({v, r, w, 0});
+            if (direct)
+                for (int w : {4, 8}) cands.push_back({v, r, w, 0});
             if (staged && v >= 2) {
                 // MIPS also tries 3, the least its ring needs (less shared memory, more warps)
                 const int sts[3] = {base_stages, base_stages + 2, 3};
@@ -522,6 +549,12 @@ lbm_status create_common(int32_t n, const lbm_lattice *lats, const lbm_model *mo
             delete c;
             return LBM_ERR_INVALID_ARG;
         }
+        // beyond the direct kernel's 32-bit element index only the staged kernel runs
+        const int q = lats[k].velocity_set == LBM_D2Q7 ? 7 : 9;
+        if (!index32_fits(lats[k], q) && !staged_fits(lats[k])) {
+            delete c;
+            return LBM_ERR_UNSUPPORTED;
+        }
         LatHost L;
         L.lat = lats[k];
         L.model = (int)models[k];
@@ -552,6 +585,7 @@ lbm_status create_common(int32_t n, const lbm_lattice *lats, const lbm_model *mo
         g.vec = default_vec(c, g);
         g.rows = 32;
         g.warps = 4;
+        if (!direct_ok(c, g)) g.stages = g.model == LBM_MIPS ? 4 : 3;
     }
     layout(c);
     *out = c;
@@ -1027,6 +1061,10 @@ lbm_status lbm_set_tuning(lbm_ctx *c, int32_t mode, int32_t vec, int32_t rows, i
     if (stages != 0)
         for (auto &g : c->groups)
             if (!staged_ok(c, g)) return fail(c, LBM_ERR_INVALID_ARG, "staged kernel needs nx a multiple of 16 bytes");
+    if (stages == 0)
+        for (auto &g : c->groups)
+            if (!direct_ok(c, g))
+                return fail(c, LBM_ERR_INVALID_ARG, "direct kernel needs q ny pitch <= 2^32 elements: use stages > 0");
     for (auto &g : c->groups)
         if (g.q == 7 && rows % 2) return fail(c, LBM_ERR_INVALID_ARG, "D2Q7 strips need an even number of rows");
     for (auto &g : c->groups) {

@@ -25,10 +25,63 @@ namespace lbm {
 
 // Pull row `y` of population I for this lane's VEC sites:
 //   out[j] = f_I((x0 + j - e_x) mod nx, (y - e_y) mod ny).
+// Elements are addressed by their unsigned 32-bit index from the state base
+// (i plane + row pitch + x): one wide multiply-add per address.  The host
+// launches these kernels only on lattices whose q ny pitch elements fit.
 template <int ST, int VEC, int I>
-__device__ __forceinline__ void pull_pop(const typename Store<ST>::T *plane, int y, int ny,
+__device__ __forceinline__ void pull_pop(const typename Store<ST>::T *base, uint32_t plane, int y, int ny,
                                          int nx, int pitch, int x0, bool valid, bool last,
                                          int lane, float shift, float out[VEC])
+{
+    const uint32_t row = (uint32_t)I * plane + (uint32_t)wrap_once(y - vy(I), ny) * (uint32_t)pitch;
+    float a[VEC];
+    if (valid) {
+        load_vec<ST, VEC>(base + (row + (uint32_t)x0), shift, a);
+    } else {
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) a[j] = 0.f;
+    }
+    if constexpr (vx(I) == 0) {
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) out[j] = a[j];
+    } else if constexpr (vx(I) == 1) {  // from x - 1
+        float left = __shfl_up_sync(FULL, a[VEC - 1], 1);
+        if (lane == 0 && valid) left = load_one<ST>(base + (row + (uint32_t)(x0 == 0 ? nx - 1 : x0 - 1)), shift);
+        out[0] = left;
+#pragma unroll
+        for (int j = 1; j < VEC; ++j) out[j] = a[j - 1];
+    } else {  // from x + 1
+        float right = __shfl_down_sync(FULL, a[0], 1);
+        if (last && valid) right = load_one<ST>(base + (row + (uint32_t)(x0 + VEC >= nx ? 0 : x0 + VEC)), shift);
+#pragma unroll
+        for (int j = 0; j < VEC - 1; ++j) out[j] = a[j + 1];
+        out[VEC - 1] = right;
+    }
+}
+
+// All nine populations of row y.
+template <int ST, int VEC>
+__device__ __forceinline__ void pull_row(const typename Store<ST>::T *base, uint32_t plane, int y,
+                                         int ny, int nx, int pitch, int x0, bool valid, bool last,
+                                         int lane, float rho0, float f[9][VEC])
+{
+    pull_pop<ST, VEC, 0>(base, plane, y, ny, nx, pitch, x0, valid, last, lane, wq(0) * rho0, f[0]);
+    pull_pop<ST, VEC, 1>(base, plane, y, ny, nx, pitch, x0, valid, last, lane, wq(1) * rho0, f[1]);
+    pull_pop<ST, VEC, 2>(base, plane, y, ny, nx, pitch, x0, valid, last, lane, wq(2) * rho0, f[2]);
+    pull_pop<ST, VEC, 3>(base, plane, y, ny, nx, pitch, x0, valid, last, lane, wq(3) * rho0, f[3]);
+    pull_pop<ST, VEC, 4>(base, plane, y, ny, nx, pitch, x0, valid, last, lane, wq(4) * rho0, f[4]);
+    pull_pop<ST, VEC, 5>(base, plane, y, ny, nx, pitch, x0, valid, last, lane, wq(5) * rho0, f[5]);
+    pull_pop<ST, VEC, 6>(base, plane, y, ny, nx, pitch, x0, valid, last, lane, wq(6) * rho0, f[6]);
+    pull_pop<ST, VEC, 7>(base, plane, y, ny, nx, pitch, x0, valid, last, lane, wq(7) * rho0, f[7]);
+    pull_pop<ST, VEC, 8>(base, plane, y, ny, nx, pitch, x0, valid, last, lane, wq(8) * rho0, f[8]);
+}
+
+// The same with 64-bit pointer steps from a per-population plane pointer:
+// the copy-bound noise-free kernels, where the 32-bit form costs registers.
+template <int ST, int VEC, int I>
+__device__ __forceinline__ void pull_pop_wide(const typename Store<ST>::T *plane, int y, int ny,
+                                              int nx, int pitch, int x0, bool valid, bool last,
+                                              int lane, float shift, float out[VEC])
 {
     const int r = wrap_once(y - vy(I), ny);
     const typename Store<ST>::T *row = plane + (size_t)r * pitch;
@@ -58,19 +111,19 @@ __device__ __forceinline__ void pull_pop(const typename Store<ST>::T *plane, int
 }
 
 template <int ST, int VEC>
-__device__ __forceinline__ void pull_row(const typename Store<ST>::T *base, size_t plane, int y,
-                                         int ny, int nx, int pitch, int x0, bool valid, bool last,
-                                         int lane, float rho0, float f[9][VEC])
+__device__ __forceinline__ void pull_row_wide(const typename Store<ST>::T *base, size_t plane, int y,
+                                              int ny, int nx, int pitch, int x0, bool valid, bool last,
+                                              int lane, float rho0, float f[9][VEC])
 {
-    pull_pop<ST, VEC, 0>(base + 0 * plane, y, ny, nx, pitch, x0, valid, last, lane, wq(0) * rho0, f[0]);
-    pull_pop<ST, VEC, 1>(base + 1 * plane, y, ny, nx, pitch, x0, valid, last, lane, wq(1) * rho0, f[1]);
-    pull_pop<ST, VEC, 2>(base + 2 * plane, y, ny, nx, pitch, x0, valid, last, lane, wq(2) * rho0, f[2]);
-    pull_pop<ST, VEC, 3>(base + 3 * plane, y, ny, nx, pitch, x0, valid, last, lane, wq(3) * rho0, f[3]);
-    pull_pop<ST, VEC, 4>(base + 4 * plane, y, ny, nx, pitch, x0, valid, last, lane, wq(4) * rho0, f[4]);
-    pull_pop<ST, VEC, 5>(base + 5 * plane, y, ny, nx, pitch, x0, valid, last, lane, wq(5) * rho0, f[5]);
-    pull_pop<ST, VEC, 6>(base + 6 * plane, y, ny, nx, pitch, x0, valid, last, lane, wq(6) * rho0, f[6]);
-    pull_pop<ST, VEC, 7>(base + 7 * plane, y, ny, nx, pitch, x0, valid, last, lane, wq(7) * rho0, f[7]);
-    pull_pop<ST, VEC, 8>(base + 8 * plane, y, ny, nx, pitch, x0, valid, last, lane, wq(8) * rho0, f[8]);
+    pull_pop_wide<ST, VEC, 0>(base + 0 * plane, y, ny, nx, pitch, x0, valid, last, lane, wq(0) * rho0, f[0]);
+    pull_pop_wide<ST, VEC, 1>(base + 1 * plane, y, ny, nx, pitch, x0, valid, last, lane, wq(1) * rho0, f[1]);
+    pull_pop_wide<ST, VEC, 2>(base + 2 * plane, y, ny, nx, pitch, x0, valid, last, lane, wq(2) * rho0, f[2]);
+    pull_pop_wide<ST, VEC, 3>(base + 3 * plane, y, ny, nx, pitch, x0, valid, last, lane, wq(3) * rho0, f[3]);
+    pull_pop_wide<ST, VEC, 4>(base + 4 * plane, y, ny, nx, pitch, x0, valid, last, lane, wq(4) * rho0, f[4]);
+    pull_pop_wide<ST, VEC, 5>(base + 5 * plane, y, ny, nx, pitch, x0, valid, last, lane, wq(5) * rho0, f[5]);
+    pull_pop_wide<ST, VEC, 6>(base + 6 * plane, y, ny, nx, pitch, x0, valid, last, lane, wq(6) * rho0, f[6]);
+    pull_pop_wide<ST, VEC, 7>(base + 7 * plane, y, ny, nx, pitch, x0, valid, last, lane, wq(7) * rho0, f[7]);
+    pull_pop_wide<ST, VEC, 8>(base + 8 * plane, y, ny, nx, pitch, x0, valid, last, lane, wq(8) * rho0, f[8]);
 }
 
 template <int VEC>
@@ -90,7 +143,7 @@ __device__ __forceinline__ float density(const float f[9][VEC], int j)
 // pull without its nine serial loads.
 template <int ST, int VEC>
 __device__ __forceinline__ void density_window(const float f[9][VEC], const typename Store<ST>::T *base,
-                                               size_t plane, int y, int nx, int ny, int pitch, int x0,
+                                               uint32_t plane, int y, int nx, int ny, int pitch, int x0,
                                                bool valid, bool last, int lane, float rho0,
                                                float r[VEC + 2])
 {
@@ -104,7 +157,8 @@ __device__ __forceinline__ void density_window(const float f[9][VEC], const type
     if (i < 9) {
         const int xh = lane >= 16 ? (xe >= nx ? 0 : xe) : (xs == 0 ? nx - 1 : xs - 1);
         const int xsrc = wrap_once(xh - vx(i), nx), ysrc = wrap_once(y - vy(i), ny);
-        v = load_one<ST>(base + i * plane + (size_t)ysrc * pitch + xsrc, wq(i) * rho0);
+        v = load_one<ST>(base + ((uint32_t)i * plane + (uint32_t)ysrc * (uint32_t)pitch + (uint32_t)xsrc),
+                         wq(i) * rho0);
     }
     const float s01 = __fadd_rn(v, __shfl_down_sync(FULL, v, 1));         // lanes 0, 2, 4, 6
     const float s03 = __fadd_rn(s01, __shfl_down_sync(FULL, s01, 2));     // lanes 0, 4
@@ -491,6 +545,9 @@ __global__ void __launch_bounds__(256, direct_min_blocks<MODEL, ST, VEC, SAMPLE>
     const bool last = (lane == 31) || (x0 + VEC >= nx);
     const int y_begin = sy * rows, y_end = min(y_begin + rows, ny);
     const size_t plane = (size_t)ny * pitch;
+    const uint32_t plane32 = (uint32_t)plane;  // q ny pitch <= 2^32 (host check) where used
+    // 64-bit pointer steps only in the copy-bound noise-free kernels (see pull_pop_wide)
+    constexpr bool WIDE = MODEL != MODEL_MIPS && NOISE == 0 && !SAMPLE;
     const T *src = reinterpret_cast<const T *>(dp->f[a.src]);
     T *dst = reinterpret_cast<T *>(dp->f[a.src ^ 1]);
     const float rho0 = dp->rho0;
@@ -515,10 +572,10 @@ __global__ void __launch_bounds__(256, direct_min_blocks<MODEL, ST, VEC, SAMPLE>
     if constexpr (MODEL == MODEL_MIPS) {
         float tmp[9][VEC];
         const int yp = wrap_once(y_begin - 1, ny);
-        pull_row<ST, VEC>(src, plane, yp, ny, nx, pitch, x0, valid, last, lane, rho0, tmp);
-        density_window<ST, VEC>(tmp, src, plane, yp, nx, ny, pitch, x0, valid, last, lane, rho0, rm);
-        pull_row<ST, VEC>(src, plane, y_begin, ny, nx, pitch, x0, valid, last, lane, rho0, tmp);
-        density_window<ST, VEC>(tmp, src, plane, y_begin, nx, ny, pitch, x0, valid, last, lane, rho0, rc);
+        pull_row<ST, VEC>(src, plane32, yp, ny, nx, pitch, x0, valid, last, lane, rho0, tmp);
+        density_window<ST, VEC>(tmp, src, plane32, yp, nx, ny, pitch, x0, valid, last, lane, rho0, rm);
+        pull_row<ST, VEC>(src, plane32, y_begin, ny, nx, pitch, x0, valid, last, lane, rho0, tmp);
+        density_window<ST, VEC>(tmp, src, plane32, y_begin, nx, ny, pitch, x0, valid, last, lane, rho0, rc);
     }
 
     for (int y = y_begin; y < y_end; ++y) {
@@ -529,7 +586,8 @@ __global__ void __launch_bounds__(256, direct_min_blocks<MODEL, ST, VEC, SAMPLE>
         if (MODEL == MODEL_MIPS && valid) {
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
-                const T *pp = src + i * plane + (size_t)wrap_once(wrap_once(y + 2, ny) - vy(i), ny) * pitch + x0;
+                const T *pp = src + ((uint32_t)i * plane32 +
+                                     (uint32_t)wrap_once(wrap_once(y + 2, ny) - vy(i), ny) * (uint32_t)pitch + (uint32_t)x0);
                 asm volatile("prefetch.global.L2 [%0];" ::"l"(pp));
             }
         }
@@ -537,10 +595,13 @@ __global__ void __launch_bounds__(256, direct_min_blocks<MODEL, ST, VEC, SAMPLE>
         if constexpr (MODEL == MODEL_MIPS) {
             float fn[9][VEC];
             const int yn = wrap_once(y + 1, ny);
-            pull_row<ST, VEC>(src, plane, yn, ny, nx, pitch, x0, valid, last, lane, rho0, fn);
-            density_window<ST, VEC>(fn, src, plane, yn, nx, ny, pitch, x0, valid, last, lane, rho0, rn);
+            pull_row<ST, VEC>(src, plane32, yn, ny, nx, pitch, x0, valid, last, lane, rho0, fn);
+            density_window<ST, VEC>(fn, src, plane32, yn, nx, ny, pitch, x0, valid, last, lane, rho0, rn);
         }
-        pull_row<ST, VEC>(src, plane, y, ny, nx, pitch, x0, valid, last, lane, rho0, fc);
+        if constexpr (WIDE)
+            pull_row_wide<ST, VEC>(src, plane, y, ny, nx, pitch, x0, valid, last, lane, rho0, fc);
+        else
+            pull_row<ST, VEC>(src, plane32, y, ny, nx, pitch, x0, valid, last, lane, rho0, fc);
         float gx[VEC], gy[VEC];
         if constexpr (MODEL == MODEL_MIPS) {
             mips_gradients<VEC>(rm, rc, rn, gx, gy);
@@ -558,7 +619,11 @@ __global__ void __launch_bounds__(256, direct_min_blocks<MODEL, ST, VEC, SAMPLE>
         if (valid) {
 #pragma unroll
             for (int i = 0; i < 9; ++i)
-                store_vec<ST, VEC>(dst + i * plane + (size_t)y * pitch + x0, wq(i) * rho0, out[i]);
+                if constexpr (WIDE)
+                    store_vec<ST, VEC>(dst + i * plane + (size_t)y * pitch + x0, wq(i) * rho0, out[i]);
+                else
+                    store_vec<ST, VEC>(dst + ((uint32_t)i * plane32 + (uint32_t)y * (uint32_t)pitch + (uint32_t)x0),
+                                       wq(i) * rho0, out[i]);
         }
         if constexpr (SAMPLE) {
             // observables of the stored (rounded) state

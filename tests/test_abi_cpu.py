@@ -144,3 +144,41 @@ def test_d2q7_buffers_and_tuning(lib):
     assert lib.lbm_get_tuning(ctx, 1, *[ctypes.byref(x) for x in (v, r, w, st)]) == 0
     assert st.value == 3
     lib.lbm_destroy(ctx)
+
+
+def test_direct_kernel_index_limit(lib):
+    """The direct D2Q9 kernel indexes a buffer with 32-bit element offsets: a
+    lattice of more than 2^32 elements per buffer (9 ny pitch) starts on a
+    staged shape and refuses direct ones; one that cannot be staged either (nx
+    not a multiple of 16 bytes) is refused at create.  D2Q7 is not limited.
+    Host only: nothing is allocated."""
+    from paper_1902_00530_gb300 import _abi
+    prm = _prm(tau=1.0, C=6.0, rho_star=1.6, u_max=0.3, sigma=0.08)
+    v, r, w, st = (ctypes.c_int32() for _ in range(4))
+
+    def create(nx, ny, storage=0, vs=0):
+        ctx = ctypes.c_void_p()
+        status = lib.lbm_create(ctypes.byref(_abi.lbm_lattice(nx, ny, storage, 0, vs)), 1, ctypes.byref(prm),
+                                ctypes.byref(ctx))
+        return status, ctx
+
+    # 9 * 14563 * 32768 = 4294803456 <= 2^32: direct shapes allowed
+    status, ctx = create(32768, 14563)
+    assert status == 0
+    assert lib.lbm_get_tuning(ctx, 0, *[ctypes.byref(x) for x in (v, r, w, st)]) == 0 and st.value == 0
+    assert lib.lbm_set_tuning(ctx, 1, 4, 32, 4, 0) == 0
+    lib.lbm_destroy(ctx)
+    # one row more crosses 2^32: staged by default, direct refused, staged accepted
+    status, ctx = create(32768, 14564)
+    assert status == 0
+    assert lib.lbm_get_tuning(ctx, 0, *[ctypes.byref(x) for x in (v, r, w, st)]) == 0 and st.value == 4
+    assert lib.lbm_set_tuning(ctx, 1, 4, 32, 4, 0) == 1
+    assert lib.lbm_set_tuning(ctx, 1, 4, 32, 4, 3) == 0
+    lib.lbm_destroy(ctx)
+    # FP16 storage: pitch in 64-element steps; nx = 65530 pads to 65536 and is not a
+    # multiple of 8 elements, so it can be neither direct nor staged at this height
+    assert create(65530, 8000, storage=1)[0] == 6
+    assert create(65530, 7000, storage=1)[0] == 0     # 9 * 7000 * 65536 < 2^32
+    status, ctx = create(65530, 8000, storage=1, vs=1)  # D2Q7 keeps 64-bit indexing
+    assert status == 0
+    lib.lbm_destroy(ctx)
