@@ -18,6 +18,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -41,10 +42,14 @@ KERNEL_SOURCES = ["paper_1902_00530_gb300/csrc/lbm_step.cuh", "paper_1902_00530_
 
 
 def kernel_hash() -> str:
+    """Hash of the step-kernel sources with comments removed: the recorded DRAM
+    traffic stays valid across comment edits, not across code changes."""
     h = hashlib.sha256()
     for p in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, p), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, p), encoding="utf-8") as f:
+            code = re.sub(r"/\*.*?\*/", "", f.read(), flags=re.S)
+        code = re.sub(r"//[^\n]*", "", code)
+        h.update(code.encode())
     return h.hexdigest()[:16]
 
 

@@ -265,7 +265,12 @@ LatDesc make_desc(const lbm_ctx *c, const LatHost &L, int block_begin, const Gro
     d.q = L.q;
     const long long nstrip = (long long)d.nsx * d.nsy;
     d.nchunk = std::min(L.nchunk_max, std::max(1, ceil_div(std::max<long long>({L.lat.nx, L.lat.ny, nstrip}), CHUNK_COLS)));
-    d.omega = (float)(1.0 / L.p.tau);
+    // 1/tau in FP32 such that 1 - 1/tau is exact too (the noisy update weighs f*
+    // by 1 - 1/tau and f^SS by 1/tau): automatic for 1/tau in [1/2, 2]
+    // (Sterbenz); below 1/2 the value is rounded to a multiple of 2^-24.
+    double om = 1.0 / L.p.tau;
+    if (om < 0.5) om = std::nearbyint(om * 16777216.0) / 16777216.0;
+    d.omega = (float)om;
     d.sigma_q = (float)(2.0 * L.p.sigma);
     d.C = (float)L.p.C;
     d.rho_star = (float)L.p.rho_star;

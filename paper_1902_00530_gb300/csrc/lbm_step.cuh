@@ -180,7 +180,7 @@ __device__ __forceinline__ SiteParams load_params(const LatDesc *dp)
 {
     SiteParams p;
     p.omega = dp->omega;
-    p.omc = __fsub_rn(1.f, dp->omega);  // exact for tau in [1/2, 2] (Sterbenz)
+    p.omc = __fsub_rn(1.f, dp->omega);  // exact: the host picks omega so
     p.sigma_q = dp->sigma_q;
     p.C = dp->C;
     p.inv_rho_star = dp->inv_rho_star;

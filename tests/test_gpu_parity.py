@@ -55,6 +55,8 @@ STABLE = {
     "mips_rho1_stable_C": ("MIPS_RHO1", dict(C=0.2), W.INIT_CONFIG1),
     "cil_paper_literal": ("CIL_PAPER_LITERAL", {}, W.INIT_CONFIG2),
     "passive_tau_1p7": ("PASSIVE", dict(tau=1.7, sigma=0.005), W.INIT_CONFIG2),
+    # tau > 2: 1/tau below 1/2, rounded by the host so that 1 - 1/tau is exact
+    "passive_tau_3": ("PASSIVE", dict(tau=3.0, sigma=0.005), W.INIT_CONFIG2),
     "mips_rho1_stable_C_low_noise": ("MIPS_RHO1", dict(C=0.2, sigma=0.0099), W.INIT_CONFIG1),
 }
 GROWING = {
