@@ -32,8 +32,9 @@ template <int ST, int VEC> struct StageGeom7 {
     static constexpr int STAGE_BYTES = 7 * SEG * (int)sizeof(T);
 };
 
-// Issue the seven segment copies of destination row y (lanes 0..20, one copy
-// each: left halo, strip, right halo of each population) and arm the barrier.
+// Issue the segment copies of destination row y and arm the barrier: one copy
+// per population (lanes 0..6) for a strip whose halos lie inside the row,
+// else three (lanes 0..20: left halo, strip, right halo), as in issue_row.
 template <int ST, int VEC>
 __device__ __forceinline__ void issue_row7(typename Store<ST>::T *buf, uint64_t *bar, const typename Store<ST>::T *src,
                                            size_t plane, int pitch, int nx, int ny, int xs, int xe, int y, int lane)
@@ -44,7 +45,15 @@ __device__ __forceinline__ void issue_row7(typename Store<ST>::T *buf, uint64_t 
     __syncwarp();  // every lane has finished reading this buffer's previous row
     if (lane == 0) mbar_arrive_expect_tx(bar, 7u * (main_bytes + 32u));
     __syncwarp();
-    if (lane < 21) {
+    if (xs >= G::HALO && xe + G::HALO <= nx) {
+        if (lane < 7) {
+            fence_proxy_async_smem();
+            const int i = lane;
+            const int r = wrap_once(y + ((i == 2 || i == 3) ? -1 : ((i == 5 || i == 6) ? 1 : 0)), ny);
+            const T *row = src + (size_t)i * plane + (size_t)r * pitch;
+            bulk_copy_g2s(buf + i * G::SEG, row + (xs - G::HALO), main_bytes + 32u, bar);
+        }
+    } else if (lane < 21) {
         fence_proxy_async_smem();
         const int i = lane / 3, part = lane % 3;
         const int r = wrap_once(y + ((i == 2 || i == 3) ? -1 : ((i == 5 || i == 6) ? 1 : 0)), ny);

@@ -91,8 +91,13 @@ template <int ST, int VEC> struct StageGeom {
     static constexpr int STAGE_BYTES = 9 * SEG * (int)sizeof(T);
 };
 
-// Issue the nine segment copies of destination row y into stage buffer `buf`
-// and arm its barrier (lanes 0..26 issue one copy each; lane 0 arms).
+// Issue the segment copies of destination row y into stage buffer `buf` and
+// arm its barrier (lane 0 arms).  A strip whose halos lie inside the row
+// (xs >= HALO, xe + HALO <= nx) takes one copy per population, lanes 0..8:
+// the left halo, the strip and the right halo are contiguous in the row and
+// in the segment.  A strip at the periodic edge takes three per population,
+// lanes 0..26.  Each copy is issued by one elected lane at a time, so fewer
+// copies is fewer issue slots.
 template <int ST, int VEC>
 __device__ __forceinline__ void issue_row(typename Store<ST>::T *buf, uint64_t *bar,
                                           const typename Store<ST>::T *src, size_t plane, int pitch,
@@ -104,7 +109,16 @@ __device__ __forceinline__ void issue_row(typename Store<ST>::T *buf, uint64_t *
     __syncwarp();  // every lane has finished reading this buffer's previous row
     if (lane == 0) mbar_arrive_expect_tx(bar, 9u * (main_bytes + 32u));
     __syncwarp();
-    if (lane < 27) {
+    if (xs >= G::HALO && xe + G::HALO <= nx) {
+        if (lane < 9) {
+            fence_proxy_async_smem();  // order those reads before the copy's writes
+            const int i = lane;
+            const int dy = (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+            const int r = wrap_once(y - dy, ny);
+            const T *row = src + (size_t)i * plane + (size_t)r * pitch;
+            bulk_copy_g2s(buf + i * G::SEG, row + (xs - G::HALO), main_bytes + 32u, bar);
+        }
+    } else if (lane < 27) {
         fence_proxy_async_smem();  // order those reads before the copy's writes
         const int i = lane / 3, part = lane % 3;
         const int dy = (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
