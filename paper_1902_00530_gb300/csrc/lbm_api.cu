@@ -484,7 +484,7 @@ lbm_status tune_group(lbm_ctx *c, GroupHost &g)
             if (staged && v >= 2) {
                 // MIPS also tries 3, the least its ring needs (less shared memory, more warps)
                 const int sts[3] = {base_stages, base_stages + 2, 3};
-                for (int w : {2, 4})
+                for (int w : {1, 2, 4})
                     for (int k = 0; k < (base_stages > 3 ? 3 : 2); ++k) cands.push_back({v, r, w, sts[k]});
             }
         }

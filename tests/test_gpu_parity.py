@@ -186,7 +186,8 @@ def test_ragged_sizes_default_shape(nx, ny):
 
 
 SHAPES_FIXED = [(1, 16), (2, 16), (4, 16), (4, 48), (2, 128), (8, 32),
-                (1, 16, 4, 3), (2, 32, 2, 4), (4, 64, 4, 6), (2, 48, 4, 3), (8, 32, 2, 4)]
+                (1, 16, 4, 3), (2, 32, 2, 4), (4, 64, 4, 6), (2, 48, 4, 3), (8, 32, 2, 4), (4, 16, 1, 3),
+                (2, 32, 1, 4)]
 
 
 @pytest.mark.parametrize("shape", SHAPES_FIXED, ids=lambda s: "x".join(map(str, s)))
