@@ -201,25 +201,14 @@ __device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b)
 __device__ __forceinline__ float vsub(float a, float b) { return __fsub_rn(a, b); }
 __device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ float vfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
-__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 vsub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
-__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float vneg(float a) { return -a; }
-__device__ __forceinline__ float2 vneg(float2 a) { return make_float2(-a.x, -a.y); }
 
 template <typename V> __device__ __forceinline__ V splat(float s);
 template <> __device__ __forceinline__ float splat<float>(float s) { return s; }
-template <> __device__ __forceinline__ float2 splat<float2>(float s) { return make_float2(s, s); }
 
-// per-component operations (no paired form): apply a scalar function
+// apply a scalar function (comparisons, selects, reciprocals)
 template <typename F> __device__ __forceinline__ float vmap(float a, F fn) { return fn(a); }
-template <typename F> __device__ __forceinline__ float2 vmap(float2 a, F fn) { return make_float2(fn(a.x), fn(a.y)); }
 template <typename F> __device__ __forceinline__ float vmap2(float a, float b, F fn) { return fn(a, b); }
-template <typename F> __device__ __forceinline__ float2 vmap2(float2 a, float2 b, F fn)
-{
-    return make_float2(fn(a.x, b.x), fn(a.y, b.y));
-}
 
 template <typename V>
 __device__ __forceinline__ V vdensity(const V f[9])
@@ -395,10 +384,10 @@ __device__ __forceinline__ void noise_u(uint32_t x, uint32_t y, uint32_t t, uint
 
 // The update of a lane's VEC sites, one site at a time.  f[i][j] holds f*_i
 // of site j on entry and the new f_i on exit; g*[j] are the MIPS gradients
-// (ignored otherwise).  (The paired V = float2 form of collide_v is kept for
-// completeness but not used: inlined into the kernels, the compiler rounds
-// a few of its paired steps differently from the single-site form, and launch
-// shapes must agree bitwise.)
+// (ignored otherwise).  The helpers above take the value type as a parameter;
+// only V = float is instantiated (a paired float2 form was measured and
+// dropped: its paired products did not round as the single-site ones, and
+// launch shapes must agree bitwise).
 template <int MODEL, int VEC>
 __device__ __forceinline__ void collide_sites(float f[9][VEC], const float gxs[VEC], const float gys[VEC],
                                               const SiteParams &d, bool noise, uint32_t x0, uint32_t y, uint32_t t,
