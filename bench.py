@@ -42,14 +42,15 @@ KERNEL_SOURCES = ["paper_1902_00530_gb300/csrc/lbm_step.cuh", "paper_1902_00530_
 
 
 def kernel_hash() -> str:
-    """Hash of the step-kernel sources with comments removed: the recorded DRAM
-    traffic stays valid across comment edits, not across code changes."""
+    """Hash of the step-kernel sources with comments removed and whitespace
+    collapsed: the recorded DRAM traffic stays valid across comment and layout
+    edits, not across code changes."""
     h = hashlib.sha256()
     for p in KERNEL_SOURCES:
         with open(os.path.join(ROOT, p), encoding="utf-8") as f:
-            code = re.sub(r"/\*.*?\*/", "", f.read(), flags=re.S)
-        code = re.sub(r"//[^\n]*", "", code)
-        h.update(code.encode())
+            code = re.sub(r"/\*.*?\*/", " ", f.read(), flags=re.S)
+        code = re.sub(r"//[^\n]*", " ", code)
+        h.update(" ".join(code.split()).encode())
     return h.hexdigest()[:16]
 
 
