@@ -45,6 +45,8 @@ MUTATIONS = [
     ("noise_variance", "s[i] = (2.0 * (double)m[i] + 1.0 - 16384.0) / 16384.0;",
      "s[i] = (2.0 * (double)m[i] + 1.0 - 16384.0) / 32768.0;"),
     ("clamp_ignored", "if (mag > (real)p->u_max) {", "if (mag > (real)1e30) {"),
+    ("philox_round_multiplier", "#define PHILOX_M0 0xD2511F53u", "#define PHILOX_M0 0xD2511F55u"),
+    ("philox_key_increment", "#define PHILOX_W1 0xBB67AE85u", "#define PHILOX_W1 0xBB67AE87u"),
 ]
 
 # slips in the D2Q7 file: (name, text in lbm_oracle_d2q7.c, replacement)
@@ -86,6 +88,7 @@ PINS = [
     (P.test_rotation_equivariance, dict(name="MIPS_RHO1")),
     (P.test_observables_closed_forms, {}),
     (P.test_noise_statistics, {}),
+    (P.test_philox_matches_an_independent_library_implementation, {}),
 ]
 
 

@@ -433,6 +433,60 @@ def test_philox_bijection_and_avalanche():
     assert abs(np.mean(flips) - 64) < 2.0
 
 
+_TRITON_PHILOX = r"""
+import json, sys
+import numpy as np, torch
+import triton
+import triton.language as tl
+
+@triton.jit
+def philox_kernel(c_ptr, out_ptr, seed, N: tl.constexpr):
+    i = tl.arange(0, N)
+    r0, r1, r2, r3 = tl.philox(seed, tl.load(c_ptr + 4 * i), tl.load(c_ptr + 4 * i + 1),
+                               tl.load(c_ptr + 4 * i + 2), tl.load(c_ptr + 4 * i + 3))
+    tl.store(out_ptr + 4 * i, r0)
+    tl.store(out_ptr + 4 * i + 1, r1)
+    tl.store(out_ptr + 4 * i + 2, r2)
+    tl.store(out_ptr + 4 * i + 3, r3)
+
+req = json.load(sys.stdin)
+c = np.array(req["counters"], dtype=np.uint32)
+res = {}
+for seed in req["seeds"]:
+    ct = torch.from_numpy(c.view(np.int32).copy())
+    out = torch.zeros_like(ct)
+    philox_kernel[(1,)](ct, out, seed, N=len(c))
+    res[str(seed)] = out.numpy().view(np.uint32).tolist()
+print(json.dumps(res))
+"""
+
+
+def test_philox_matches_an_independent_library_implementation():
+    """The oracle's Philox4x32-10 (written from Salmon et al. 2011) against the
+    one Triton ships in its language library (tl.philox: same rounds, key
+    (seed_lo, seed_hi) bumped by the Weyl constants after every round), run by
+    Triton's CPU interpreter in a child process: counters and keys at random
+    and at the extremes."""
+    pytest.importorskip("triton")
+    import subprocess
+    import sys
+    rng = np.random.default_rng(11)
+    c = rng.integers(0, 2 ** 32, (64, 4), dtype=np.uint64).astype(np.uint32)
+    c[0] = 0
+    c[1] = 0xFFFFFFFF
+    seeds = [0, 0xFFFFFFFFFFFFFFFF, 0x9ABCDEF012345678, 190200530]
+    env = dict(os.environ, TRITON_INTERPRET="1", CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, "-c", _TRITON_PHILOX], input=json.dumps(
+        {"counters": c.tolist(), "seeds": seeds}), capture_output=True, text=True, env=env, timeout=300)
+    if r.returncode != 0:
+        pytest.skip("Triton's interpreter is not usable here: " + r.stderr.strip().splitlines()[-1][:200])
+    got = json.loads(r.stdout.strip().splitlines()[-1])
+    for seed in seeds:
+        key = (seed & 0xFFFFFFFF, seed >> 32)
+        ref = [[int(v) for v in O.philox4x32_10(tuple(int(x) for x in row), key)] for row in c]
+        assert got[str(seed)] == ref, seed
+
+
 def test_init_uniforms_and_recipe():
     """App. C.2 initialisation: rho within +-10 % of rho-bar, u magnitude as set."""
     u = np.array([O.init_uniforms(5, i, 0) for i in range(20000)])
