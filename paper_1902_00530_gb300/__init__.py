@@ -87,6 +87,9 @@ class Simulation:
         prms = (_abi.lbm_params * n)(*[_params(p) for p in params])
         ctx = ctypes.c_void_p()
         st = self.lib.lbm_create_batch(n, lats, mods, prms, ctypes.byref(ctx))
+        if st == _abi.LBM_ERR_UNSUPPORTED:
+            raise LBMError(st, "a D2Q9 lattice beyond 2^32 elements per buffer runs only the staged kernel, "
+                               "which needs nx a multiple of 16 bytes of storage")
         if st != 0:
             raise LBMError(st, "invalid lattice or parameters")
         self.ctx = ctx

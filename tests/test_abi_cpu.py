@@ -182,3 +182,12 @@ def test_direct_kernel_index_limit(lib):
     status, ctx = create(65530, 8000, storage=1, vs=1)  # D2Q7 keeps 64-bit indexing
     assert status == 0
     lib.lbm_destroy(ctx)
+
+
+def test_binding_names_the_unsupported_lattice(lib):
+    """The Python binding reports LBM_ERR_UNSUPPORTED with its reason before
+    touching the GPU (creation is host only)."""
+    from paper_1902_00530_gb300 import LBMError, Lattice, Simulation
+    with pytest.raises(LBMError) as e:
+        Simulation([Lattice(65530, 8000, "f16s")], ["mips"], [dict(tau=1.0, C=6.0, rho_star=1.6, u_max=0.3)])
+    assert e.value.status == 6 and "staged kernel" in str(e.value)
