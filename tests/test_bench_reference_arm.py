@@ -28,3 +28,16 @@ def test_reference_arm_json_line():
     e = d["e2e"]
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+
+
+def test_reference_arm_under_torchrun_ranks():
+    """Launched as N ranks, rank 0 alone runs the oracle and prints the line;
+    the other ranks exit 0 without output."""
+    base = dict(os.environ, WORLD_SIZE="2", LOCAL_RANK="0", MASTER_ADDR="127.0.0.1", MASTER_PORT="29555")
+    cmd = [sys.executable, "bench.py", "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "3"]
+    r1 = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=600, env=dict(base, RANK="1"))
+    assert r1.returncode == 0 and not [ln for ln in r1.stdout.splitlines() if ln.startswith("{")], r1.stdout
+    r0 = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=600, env=dict(base, RANK="0"))
+    assert r0.returncode == 0, r0.stderr[-2000:]
+    d = json.loads([ln for ln in r0.stdout.splitlines() if ln.startswith("{")][-1])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2
