@@ -439,3 +439,35 @@ def test_init7_recipe():
                     u = (U0 * math.cos(a), U0 * math.sin(a))
                 assert abs(rho[y, x] - r) < 1e-14
                 assert abs(ux[y, x] - u[0]) < 1e-14 and abs(uy[y, x] - u[1]) < 1e-14
+
+
+# ------------------------------------------------------------ windows ----
+WINDOWS7 = [(30, 28, 24, 20), (5, 2, 18, 16), (0, 30, 40, 12)]  # even y offsets and heights, 40 x 36 box
+
+
+def _window_of7(full, x_off, y_off, nx, ny):
+    gny, gnx = full.shape[1:]
+    ys = (y_off + np.arange(ny)) % gny
+    xs = (x_off + np.arange(nx)) % gnx
+    return full[:, ys][:, :, xs]
+
+
+@pytest.mark.parametrize("name,reach", [("MIPS_RHO1", 2), ("CIL_RHO1", 1)])
+def test_window_equals_interior_of_periodic_run7(name, reach):
+    """The D2Q7 window form against the full periodic box: equal everywhere at
+    init and, after k noisy steps, inside the light cone (a hop moves at most
+    one row and one column on the brick box; MIPS's gradient adds one hop)."""
+    model, p = prm_of(name)
+    gnx, gny, seed, k = 40, 36, 7654321, 3
+    full0 = O.init7(gnx, gny, seed, **W.INIT_CONFIG2, prm=p)
+    full = O.run7(full0, model, p, seed, 9, k)
+    for (xo, yo, nx, ny) in WINDOWS7:
+        win = (xo, yo, gnx, gny)
+        w0 = O.init7(nx, ny, seed, **W.INIT_CONFIG2, prm=p, window=win)
+        np.testing.assert_array_equal(w0, _window_of7(full0, xo, yo, nx, ny))
+        wk = O.run7(w0, model, p, seed, 9, k, window=win)
+        ref = _window_of7(full, xo, yo, nx, ny)
+        m = reach * k
+        inner_x = slice(m, nx - m) if nx < gnx else slice(None)
+        np.testing.assert_array_equal(wk[:, m:ny - m, inner_x], ref[:, m:ny - m, inner_x])
+        assert not np.array_equal(wk[:, :m], ref[:, :m])

@@ -47,6 +47,17 @@ MUTATIONS = [
     ("clamp_ignored", "if (mag > (real)p->u_max) {", "if (mag > (real)1e30) {"),
     ("philox_round_multiplier", "#define PHILOX_M0 0xD2511F53u", "#define PHILOX_M0 0xD2511F55u"),
     ("philox_key_increment", "#define PHILOX_W1 0xBB67AE85u", "#define PHILOX_W1 0xBB67AE87u"),
+    # the window form: noise keyed by window instead of global coordinates, the
+    # offset applied with the wrong sign, init draws at window coordinates
+    ("window_noise_at_window_coordinates",
+     "orc_noise_variates(seed, (uint32_t)wrap(x + x_off, gnx), (uint32_t)wrap(y + y_off, gny),",
+     "orc_noise_variates(seed, (uint32_t)x, (uint32_t)y,"),
+    ("window_offset_sign",
+     "orc_noise_variates(seed, (uint32_t)wrap(x + x_off, gnx), (uint32_t)wrap(y + y_off, gny),",
+     "orc_noise_variates(seed, (uint32_t)wrap(x - x_off, gnx), (uint32_t)wrap(y - y_off, gny),"),
+    ("window_init_at_window_coordinates",
+     "orc_init_uniforms(seed, (uint32_t)wrap(x + x_off, gnx), (uint32_t)wrap(y + y_off, gny), id,",
+     "orc_init_uniforms(seed, (uint32_t)x, (uint32_t)y, id,"),
 ]
 
 # slips in the D2Q7 file: (name, text in lbm_oracle_d2q7.c, replacement)
@@ -69,6 +80,15 @@ MUTATIONS7 = [
     ("q7_moments_row_spacing", "jy += fi * hs3 * ERY[i];", "jy += fi * 0.5 * ERY[i];"),
     ("q7_noise_bits", "s[i] = (2.0 * (double)h + 1.0 - 65536.0) / 65536.0;",
      "s[i] = (2.0 * (double)h + 1.0 - 65536.0) / 131072.0;"),
+    ("q7_window_noise_at_window_coordinates",
+     "orc7_noise_variates(seed, (uint32_t)wrap7(x + x_off, gnx), (uint32_t)wrap7(y + y_off, gny), t, id,",
+     "orc7_noise_variates(seed, (uint32_t)x, (uint32_t)y, t, id,"),
+    ("q7_window_offset_sign",
+     "orc7_noise_variates(seed, (uint32_t)wrap7(x + x_off, gnx), (uint32_t)wrap7(y + y_off, gny), t, id,",
+     "orc7_noise_variates(seed, (uint32_t)wrap7(x - x_off, gnx), (uint32_t)wrap7(y - y_off, gny), t, id,"),
+    ("q7_window_init_at_window_coordinates",
+     "orc_init_uniforms(seed, (uint32_t)wrap7(x + x_off, gnx), (uint32_t)wrap7(y + y_off, gny), id, U);",
+     "orc_init_uniforms(seed, (uint32_t)x, (uint32_t)y, id, U);"),
 ]
 
 # the pin checks run against each planted copy (all fast)
@@ -89,6 +109,7 @@ PINS = [
     (P.test_observables_closed_forms, {}),
     (P.test_noise_statistics, {}),
     (P.test_philox_matches_an_independent_library_implementation, {}),
+    (P.test_window_equals_interior_of_periodic_run, dict(name="MIPS_RHO1", reach=2)),
 ]
 
 
@@ -106,6 +127,7 @@ PINS7 = [
     (P7.test_mips_growth_rate_matches_chapman_enskog7, dict(axis="y", tau=1.0, C=1.0)),
     (P7.test_noise_statistics7, {}),
     (P7.test_init7_recipe, {}),
+    (P7.test_window_equals_interior_of_periodic_run7, dict(name="MIPS_RHO1", reach=2)),
 ]
 
 

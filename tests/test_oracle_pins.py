@@ -537,3 +537,45 @@ def test_d2q7_presets_follow_paper_tables():
     s = 1 / g["mips_sweep"]["rho_bar"]
     r = W.PRESETS["MIPS_Q7_RHO1"]
     assert abs(r["C"] - m["C"] / s) < 1e-12 and abs(r["sigma"] - m["sigma"] * s) < 1e-12 and r["tau"] == m["tau"]
+
+
+# ------------------------------------------------------------ windows ------
+# The window form (an nx x ny piece of a larger periodic lattice, keyed by the
+# global coordinates) carries the CPU baseline and the full-size sampled GPU
+# parity.  It is pinned here to the plain periodic run: inside the light cone
+# the window's sites must equal the full lattice's bit for bit.  Per step a
+# site depends on sites one hop away (streaming) and, for MIPS, one more hop
+# (the post-stream density of the eight neighbours enters the gradient).
+WINDOWS9 = [(30, 28, 24, 20), (5, 3, 18, 16), (0, 31, 40, 12)]  # (x_off, y_off, nx, ny) in a 40 x 36 box
+
+
+def _window_of(full, x_off, y_off, nx, ny):
+    gny, gnx = full.shape[1:]
+    ys = (y_off + np.arange(ny)) % gny
+    xs = (x_off + np.arange(nx)) % gnx
+    return full[:, ys][:, :, xs]
+
+
+@pytest.mark.parametrize("name,reach", [("MIPS_RHO1", 2), ("CIL_RHO1", 1)])
+def test_window_equals_interior_of_periodic_run(name, reach):
+    """Init and k noisy steps of windows (one wrapping across both global
+    edges, one at a small offset, one spanning the full width) equal the
+    matching sites of the full periodic run: every site at init, and after k
+    steps the sites farther than reach * k from the window edge."""
+    d = W.preset(name)
+    model = d.pop("model")
+    p = O.params(**d)
+    gnx, gny, seed, k = 40, 36, 1234567, 3
+    full0 = O.init(gnx, gny, seed, **W.INIT_CONFIG2, prm=p)
+    full = O.run(full0, model, p, seed, 5, k)
+    for (xo, yo, nx, ny) in WINDOWS9:
+        win = (xo, yo, gnx, gny)
+        w0 = O.init(nx, ny, seed, **W.INIT_CONFIG2, prm=p, window=win)
+        np.testing.assert_array_equal(w0, _window_of(full0, xo, yo, nx, ny))
+        wk = O.run(w0, model, p, seed, 5, k, window=win)
+        ref = _window_of(full, xo, yo, nx, ny)
+        m = reach * k
+        inner_x = slice(m, nx - m) if nx < gnx else slice(None)
+        np.testing.assert_array_equal(wk[:, m:ny - m, inner_x], ref[:, m:ny - m, inner_x])
+        # and the window is no trivial copy: outside the cone it differs
+        assert not np.array_equal(wk[:, :m], ref[:, :m])
