@@ -56,23 +56,52 @@ class OrcParams(ctypes.Structure):
     ]
 
 
+# builds: FP64, FP32, and FP64 with OpenMP row loops (key 65: the same
+# arithmetic on several host threads)
+_BUILDS = {64: ("double", []), 32: ("float", []), 65: ("double", ["-fopenmp"])}
+
+
 def _lib_path(bits: int) -> str:
-    return os.path.join(_BUILD, f"liblbm_oracle{bits}.so")
+    return os.path.join(_BUILD, f"liblbm_oracle{bits}.so" if bits != 65 else "liblbm_oracle64mt.so")
 
 
 def build(force: bool = False) -> None:
-    """Compile the FP64 and FP32 builds of the oracle with gcc."""
+    """Compile the FP64 and FP32 builds of the oracle, and the FP64 build with
+    OpenMP row loops, with gcc."""
     os.makedirs(_BUILD, exist_ok=True)
-    for bits, real in ((64, "double"), (32, "float")):
+    for bits, (real, extra) in _BUILDS.items():
         out = _lib_path(bits)
         if not force and os.path.exists(out) and all(os.path.getmtime(out) >= os.path.getmtime(src)
                                                      for src in _SRCS):
             continue
         tmp = out + f".tmp{os.getpid()}"
-        cmd = ["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", f"-DREAL={real}",
+        cmd = ["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", f"-DREAL={real}", *extra,
                "-o", tmp, *_SRCS, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, out)
+
+
+def _key(bits: int, threads: int) -> int:
+    if threads == 1:
+        return bits
+    if bits != 64:
+        raise ValueError("the threaded oracle is the FP64 build")
+    return 65
+
+
+def host_cores() -> int:
+    """Host cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:  # pragma: no cover
+        return os.cpu_count() or 1
+
+
+def threads_in_use(threads: int = 0) -> int:
+    """Threads the threaded oracle uses; threads > 0 sets the count first
+    (0 = all host cores)."""
+    lib = _lib(65)
+    return int(lib.orc_threads(threads if threads > 0 else host_cores()))
 
 
 def _lib(bits: int = 64) -> ctypes.CDLL:
@@ -81,7 +110,7 @@ def _lib(bits: int = 64) -> ctypes.CDLL:
             return _LIBS[bits]
         build()
         lib = ctypes.CDLL(_lib_path(bits))
-        real_p = ctypes.POINTER(ctypes.c_double if bits == 64 else ctypes.c_float)
+        real_p = ctypes.POINTER(ctypes.c_float if bits == 32 else ctypes.c_double)
         dbl_p = ctypes.POINTER(ctypes.c_double)
         u32, u64, i32, i64 = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int, ctypes.c_int64
         prm = ctypes.POINTER(OrcParams)
@@ -97,11 +126,11 @@ def _lib(bits: int = 64) -> ctypes.CDLL:
         lib.orc_moments.argtypes = [real_p, i32, i32, dbl_p, dbl_p, dbl_p]
         lib.orc_observables.argtypes = [real_p, i32, i32, ctypes.c_double, dbl_p]
         lib.orc_observables.restype = i32
-        lib.orc_equilibrium.argtypes = [ctypes.c_double if bits == 64 else ctypes.c_float] * 3 + [real_p]
-        lib.orc_negative_correction.argtypes = [real_p, ctypes.c_double if bits == 64 else ctypes.c_float]
+        rl = ctypes.c_float if bits == 32 else ctypes.c_double
+        lib.orc_equilibrium.argtypes = [rl] * 3 + [real_p]
+        lib.orc_negative_correction.argtypes = [real_p, rl]
         lib.orc_negative_correction.restype = i32
         lib.orc_gradient.argtypes = [real_p, i32, i32, i32, i32, real_p]
-        rl = ctypes.c_double if bits == 64 else ctypes.c_float
         lib.orc_ustar.argtypes = [i32, prm, rl, rl, rl, real_p, real_p]
         lib.orc_philox4x32_10.argtypes = [ctypes.POINTER(u32), ctypes.POINTER(u32), ctypes.POINTER(u32)]
         lib.orc_noise_variates.argtypes = [u64, u32, u32, u32, u32, dbl_p]
@@ -122,13 +151,15 @@ def _lib(bits: int = 64) -> ctypes.CDLL:
         lib.orc7_noise_variates.argtypes = [u64, u32, u32, u32, u32, dbl_p]
         ip = ctypes.POINTER(ctypes.c_int)
         lib.orc7_neighbour.argtypes = [i32, i32, i32, i32, i32, i32, ip, ip]
-        assert lib.orc_real_bytes() * 8 == bits
+        lib.orc_threads.argtypes = [i32]
+        lib.orc_threads.restype = i32
+        assert lib.orc_real_bytes() * 8 == (64 if bits == 65 else bits)
         _LIBS[bits] = lib
         return lib
 
 
 def _dtype(bits: int):
-    return np.float64 if bits == 64 else np.float32
+    return np.float32 if bits == 32 else np.float64
 
 
 def _ptr(a: np.ndarray, ctype):
@@ -136,7 +167,7 @@ def _ptr(a: np.ndarray, ctype):
 
 
 def _rp(a: np.ndarray, bits: int):
-    return _ptr(a, ctypes.c_double if bits == 64 else ctypes.c_float)
+    return _ptr(a, ctypes.c_float if bits == 32 else ctypes.c_double)
 
 
 def params(tau=1.0, sigma=0.0, C=0.0, rho_star=1.0, u_max=1.0, A=0.0, B=0.0, **_ignored) -> OrcParams:
@@ -192,15 +223,18 @@ def step(f: np.ndarray, model: str, prm: OrcParams, seed: int, t: int, lattice_i
 
 
 def run(f: np.ndarray, model: str, prm: OrcParams, seed: int, t0: int, nsteps: int,
-        lattice_id: int = 0, bits: int = 64, window=None) -> np.ndarray:
+        lattice_id: int = 0, bits: int = 64, window=None, threads: int = 1) -> np.ndarray:
     """nsteps steps from t0 (returns a new array; the input is untouched).
 
     window = (x_off, y_off, gnx, gny) keys the noise by global coordinates; the
     window wraps on itself, so only sites at least nsteps (MIPS: 2 nsteps) from
-    its edge are exact."""
+    its edge are exact.  threads != 1 runs the FP64 step loops on that many
+    host threads (0 = all host cores): the same arithmetic, the same result."""
     g = np.array(f, dtype=_dtype(bits), order="C", copy=True)
     _check_f(g, bits)
-    lib = _lib(bits)
+    lib = _lib(_key(bits, threads))
+    if threads != 1:
+        threads_in_use(threads)
     xo, yo, gx, gy = window if window is not None else (0, 0, g.shape[2], g.shape[1])
     rc = lib.orc_run_window(_rp(g, bits), g.shape[2], g.shape[1], MODELS[model], ctypes.byref(prm),
                             seed, t0, nsteps, lattice_id, xo, yo, gx, gy)
@@ -350,11 +384,14 @@ def from_moments7(rho: np.ndarray, ux: np.ndarray, uy: np.ndarray, bits: int = 6
 
 
 def run7(f: np.ndarray, model: str, prm: OrcParams, seed: int, t0: int, nsteps: int,
-         lattice_id: int = 0, bits: int = 64, window=None) -> np.ndarray:
-    """nsteps D2Q7 steps from t0 (App. A.2); window as in run() with an even y offset."""
+         lattice_id: int = 0, bits: int = 64, window=None, threads: int = 1) -> np.ndarray:
+    """nsteps D2Q7 steps from t0 (App. A.2); window and threads as in run()
+    (the window with an even y offset)."""
     g = np.array(f, dtype=_dtype(bits), order="C", copy=True)
     _check_f7(g, bits)
-    lib = _lib(bits)
+    lib = _lib(_key(bits, threads))
+    if threads != 1:
+        threads_in_use(threads)
     xo, yo, gx, gy = window if window is not None else (0, 0, g.shape[2], g.shape[1])
     rc = lib.orc7_run_window(_rp(g, bits), g.shape[2], g.shape[1], MODELS[model], ctypes.byref(prm),
                              seed, t0, nsteps, lattice_id, xo, yo, gx, gy)

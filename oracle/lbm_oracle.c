@@ -31,6 +31,32 @@
 #endif
 typedef REAL real;
 
+/* Row loops of the step may run on several host threads (the build with
+ * -fopenmp): every site writes only its own outputs and its arithmetic is the
+ * same sequence in the same order, so the result does not depend on the
+ * thread count.  Without OpenMP the pragma is empty. */
+#ifdef _OPENMP
+#include <omp.h>
+#define ORC_PARALLEL_ROWS _Pragma("omp parallel for schedule(static)")
+#define ORC_PARALLEL_PLANES_ROWS _Pragma("omp parallel for collapse(2) schedule(static)")
+#else
+#define ORC_PARALLEL_ROWS
+#define ORC_PARALLEL_PLANES_ROWS
+#endif
+
+/* Host threads the step loops use (1 in a build without OpenMP); n > 0 sets
+ * the count first. */
+int orc_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
 #define Q 9
 
 /* D2Q9 velocity set, weights and opposite directions (Sec. 2 lifted to D2Q9;
@@ -266,11 +292,13 @@ int orc_step_window(const real *fin, real *fout, int nx, int ny, int model, cons
         return -1;
     }
     /* 1. streaming */
+    ORC_PARALLEL_PLANES_ROWS
     for (int i = 0; i < Q; ++i)
         for (int y = 0; y < ny; ++y)
             for (int x = 0; x < nx; ++x)
                 AT(fs, i, y, x) = AT(fin, i, wrap(y - EY[i], ny), wrap(x - EX[i], nx));
     /* 2. moments of f* */
+    ORC_PARALLEL_ROWS
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             real r = 0, jx = 0, jy = 0;
@@ -287,6 +315,7 @@ int orc_step_window(const real *fin, real *fout, int nx, int ny, int model, cons
         }
     real tau = (real)p->tau;
     real sigma = (real)p->sigma;
+    ORC_PARALLEL_ROWS
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             size_t c = (size_t)y * nx + x;

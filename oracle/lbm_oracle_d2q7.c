@@ -34,6 +34,17 @@
 #endif
 typedef REAL real;
 
+/* Row loops on several host threads in the -fopenmp build (see lbm_oracle.c:
+ * per-site arithmetic and order unchanged, so results are thread-count
+ * independent). */
+#ifdef _OPENMP
+#define ORC_PARALLEL_ROWS _Pragma("omp parallel for schedule(static)")
+#define ORC_PARALLEL_PLANES_ROWS _Pragma("omp parallel for collapse(2) schedule(static)")
+#else
+#define ORC_PARALLEL_ROWS
+#define ORC_PARALLEL_PLANES_ROWS
+#endif
+
 #define Q7 7
 
 /* shared with lbm_oracle.c (same library) */
@@ -167,6 +178,7 @@ int orc7_step_window(const real *fin, real *fout, int nx, int ny, int model, con
         return -1;
     }
     /* 1. streaming: f*_i(r) = f_i(r - e_i) */
+    ORC_PARALLEL_PLANES_ROWS
     for (int i = 0; i < Q7; ++i)
         for (int y = 0; y < ny; ++y)
             for (int x = 0; x < nx; ++x) {
@@ -175,6 +187,7 @@ int orc7_step_window(const real *fin, real *fout, int nx, int ny, int model, con
                 AT7(fs, i, y, x) = AT7(fin, i, ys, xs);
             }
     /* 2. rho and u of f* (Eq. (D2Q7macroscopic_u_disc)) */
+    ORC_PARALLEL_ROWS
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             real r = 0, jx = 0, jy = 0;
@@ -190,6 +203,7 @@ int orc7_step_window(const real *fin, real *fout, int nx, int ny, int model, con
             uy[c] = r > 0 ? jy / r : (real)0;
         }
     real tau = (real)p->tau, sigma = (real)p->sigma;
+    ORC_PARALLEL_ROWS
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             size_t c = (size_t)y * nx + x;
