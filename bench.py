@@ -257,15 +257,23 @@ def run_gpu(args, world, rank, local):
         dist.barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    sim.set_state(host_state)              # H2D of the populations
+    sim.set_state(host_state)              # H2D of the populations (returns when the copy is done)
+    t_h2d = time.perf_counter()
     sim.step(args.steps)
+    sim.synchronize()
+    t_d2h = time.perf_counter()
     sim.get_state(host=True, out=out_state)  # D2H of the result
+    t_d2h_end = time.perf_counter()
     obs = sim.observables()                # D2H of the observables (syncs)
     t1 = time.perf_counter()
     e2e_value, _ = aggregate_over_ranks(cells, args.steps, (t1 - t0) * 1e3, world, dist if world > 1 else None)
     e2e = {"value": round(e2e_value, 3), "unit": UNIT,
            "h2d_bytes_per_step": round(state_bytes / args.steps, 1),
-           "d2h_bytes_per_step": round((out_state.numel() * 4 + 56) / args.steps, 1)}
+           "d2h_bytes_per_step": round((out_state.numel() * 4 + 56) / args.steps, 1),
+           "h2d_gbs": round(state_bytes / (t_h2d - t0) / 1e9, 1),
+           "d2h_gbs": round(out_state.numel() * 4 / (t_d2h_end - t_d2h) / 1e9, 1),
+           "note": "one upload of the populations, the K steps, one download and the observables: "
+                   "the copies are spread over K steps"}
     del out_state, host_state
     sim.close()
     del sim

@@ -258,24 +258,25 @@ lbm_status lbm_profile_read(lbm_ctx *ctx, double *step_ms, int64_t *step_launche
  *
  * The paper has no counterpart: this is a service for callers that cannot
  * allocate device memory -- code inside a memory pool or allocator owned by
- * another runtime, a replayed stream or graph pipeline in which cudaMalloc
- * would synchronise the device, or an embedding that must keep its memory
- * footprint fixed.  It computes the same record as lbm_observables (Eq. (phi),
- * App. D) for a caller-supplied state instead of a context's.
+ * another runtime, which may not take device memory of its own, or an
+ * embedding that must keep its device memory footprint fixed.  It computes
+ * the same record as lbm_observables for a caller-supplied state instead of a
+ * context's.
  *
  * f_dev: DEVICE pointer to dense FP32 D2Q9 populations [9][ny][nx] (caller-owned,
  * read only); 1 <= nx, ny <= LBM_NOALLOC_MAX_SIDE.  B: the CIL constant used
  * by zeta.  out: host record (t is set to 0).  cuda_stream: the stream to run
- * on (NULL = legacy default stream); the call waits for it before returning.
+ * on (NULL = legacy default stream).  The call copies the record to a host
+ * buffer and synchronises that stream before it returns.
  *
  * Scratch: a fixed array of LBM_NOALLOC_SCRATCH_BYTES compiled into the
  * library, held by every GPU that loads the library until the process exits.
  * The first call on a device looks up the array's device address (with that
- * device current) and caches it; make that first call before any stream
- * capture.  All calls share the array, which keeps the last call's partial
- * sums (each call overwrites what it reads): calls that overlap on the GPU --
- * from two streams or two host threads -- race and must be serialised by the
- * caller.  No cudaMalloc, cudaFree or allocating library routine is called.
+ * device current) and caches it.  All calls share the array, which keeps the
+ * last call's partial sums (each call overwrites what it reads): calls that
+ * overlap on the GPU -- from two streams or two host threads -- race and must
+ * be serialised by the caller.  No cudaMalloc, cudaFree or allocating library
+ * routine is called.
  * Returns LBM_ERR_INVALID_ARG for sizes beyond the maximum or null pointers,
  * LBM_ERR_CUDA if a CUDA call fails, LBM_ERR_NUMERIC for non-finite sums. */
 #define LBM_NOALLOC_MAX_SIDE 4096

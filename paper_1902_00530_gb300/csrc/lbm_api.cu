@@ -239,6 +239,18 @@ void layout(lbm_ctx *c)
     c->scratch_bytes = o;
 }
 
+// The storage shifts of a lattice (rest, axis, diagonal; D2Q7: rest, moving),
+// each exactly representable in its storage type.
+Shift3 host_shift(const LatHost &L)
+{
+    Shift3 s;
+    const int st = L.lat.storage == LBM_F16_SHIFTED ? ST_F16 : (L.lat.storage == LBM_BF16_SHIFTED ? ST_BF16 : ST_F32);
+    s.c[0] = storage_shift(st, L.q == 7 ? wq7_d(0) : wq_d(0), L.rho0);
+    s.c[1] = storage_shift(st, L.q == 7 ? wq7_d(1) : wq_d(1), L.rho0);
+    s.c[2] = storage_shift(st, L.q == 7 ? wq7_d(1) : wq_d(5), L.rho0);
+    return s;
+}
+
 LatDesc make_desc(const lbm_ctx *c, const LatHost &L, int block_begin, const GroupHost &g)
 {
     LatDesc d;
@@ -280,6 +292,8 @@ LatDesc make_desc(const lbm_ctx *c, const LatHost &L, int block_begin, const Gro
     d.A = (float)L.p.A;
     d.B = (float)L.p.B;
     d.rho0 = L.rho0;
+    const Shift3 sh = host_shift(L);
+    for (int k = 0; k < 3; ++k) d.sh[k] = sh.c[k];
     return d;
 }
 
@@ -838,7 +852,11 @@ lbm_status lbm_get_state(lbm_ctx *c, int32_t lattice, float *dst, int32_t dst_is
     const char *src = c->state + L.state_off + (c->parity ? L.buf_bytes : 0);
     const size_t eb = elem_bytes(L.lat.storage);
     const long long cells = (long long)L.lat.nx * L.lat.ny;
-    if (L.lat.storage == LBM_F32) {
+    if (L.lat.storage == LBM_F32 && L.pitch == (size_t)L.lat.nx) {  // dense rows: one linear copy
+        CK(cudaMemcpyAsync(dst, src, (size_t)L.q * cells * 4,
+                           dst_is_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c->stream),
+           "copy populations");
+    } else if (L.lat.storage == LBM_F32) {
         CK(cudaMemcpy2DAsync(dst, L.lat.nx * 4, src, L.pitch * 4, L.lat.nx * 4, (size_t)L.q * L.lat.ny,
                              dst_is_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c->stream),
            "copy populations");
@@ -851,7 +869,7 @@ lbm_status lbm_get_state(lbm_ctx *c, int32_t lattice, float *dst, int32_t dst_is
            "copy populations");
         CK(cudaStreamSynchronize(c->stream), "synchronise");
         for (int i = 0; i < L.q; ++i) {
-            const float shift = pop_shift(L.q, i, L.rho0);
+            const float shift = host_shift(L).of(L.q, i);
             for (long long q = 0; q < cells; ++q) {
                 const uint16_t bits = raw[(size_t)i * cells + q];
                 float v;
@@ -887,7 +905,11 @@ lbm_status lbm_set_state(lbm_ctx *c, int32_t lattice, const float *src, int32_t 
     char *dstp = c->state + L.state_off + (c->parity ? L.buf_bytes : 0);
     const size_t eb = elem_bytes(L.lat.storage);
     const long long cells = (long long)L.lat.nx * L.lat.ny;
-    if (L.lat.storage == LBM_F32) {
+    if (L.lat.storage == LBM_F32 && L.pitch == (size_t)L.lat.nx) {  // dense rows: one linear copy
+        CK(cudaMemcpyAsync(dstp, src, (size_t)L.q * cells * 4,
+                           src_is_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, c->stream),
+           "copy populations");
+    } else if (L.lat.storage == LBM_F32) {
         CK(cudaMemcpy2DAsync(dstp, L.pitch * 4, src, L.lat.nx * 4, L.lat.nx * 4, (size_t)L.q * L.lat.ny,
                              src_is_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, c->stream),
            "copy populations");
@@ -896,7 +918,7 @@ lbm_status lbm_set_state(lbm_ctx *c, int32_t lattice, const float *src, int32_t 
     } else {
         std::vector<uint16_t> raw((size_t)L.q * cells);
         for (int i = 0; i < L.q; ++i) {
-            const float shift = pop_shift(L.q, i, L.rho0);
+            const float shift = host_shift(L).of(L.q, i);
             for (long long q = 0; q < cells; ++q) {
                 const float v = src[(size_t)i * cells + q] - shift;
                 uint16_t bits;

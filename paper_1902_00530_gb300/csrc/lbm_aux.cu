@@ -20,6 +20,7 @@ __global__ void init_kernel(const LatDesc *desc, const InitSpecDev *specs, int d
 {
     using T = typename Store<ST>::T;
     const LatDesc d = desc[blockIdx.y];
+    const Shift3 shf = load_shift(&d);
     const InitSpecDev sp = specs[blockIdx.y];
     const long long n = (long long)d.nx * d.ny;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
@@ -67,13 +68,13 @@ __global__ void init_kernel(const LatDesc *desc, const InitSpecDev *specs, int d
 #pragma unroll
             for (int i = 0; i < 7; ++i) {
                 const double eu = ex[i] * ux + ey[i] * uy;
-                put(i, wq7_d(i) * rho * (1.0 + 4.0 * eu + 8.0 * eu * eu - 2.0 * usq), wq7(i) * d.rho0);
+                put(i, wq7_d(i) * rho * (1.0 + 4.0 * eu + 8.0 * eu * eu - 2.0 * usq), shf.q7(i));
             }
         } else {
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
                 const double eu = vx(i) * ux + vy(i) * uy;
-                put(i, wq_d(i) * rho * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * usq), wq(i) * d.rho0);
+                put(i, wq_d(i) * rho * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * usq), shf.q9(i));
             }
         }
     }
@@ -85,6 +86,7 @@ __global__ void moments_kernel(const LatDesc *desc, int lat, int src, float *rho
 {
     using T = typename Store<ST>::T;
     const LatDesc d = desc[lat];
+    const Shift3 shf = load_shift(&d);
     const T *base = reinterpret_cast<const T *>(d.f[src]);
     const size_t plane = (size_t)d.ny * d.pitch;
     const long long n = (long long)d.nx * d.ny;
@@ -96,14 +98,14 @@ __global__ void moments_kernel(const LatDesc *desc, int lat, int src, float *rho
         if (d.q == 7) {
 #pragma unroll
             for (int i = 0; i < 7; ++i)
-                f[i] = load_one<ST>(base + i * plane + (size_t)y * d.pitch + x, wq7(i) * d.rho0);
+                f[i] = load_one<ST>(base + i * plane + (size_t)y * d.pitch + x, shf.q7(i));
             r = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + f[6]);
             jx = (f[1] - f[4]) + 0.5f * ((f[2] + f[6]) - (f[3] + f[5]));
             jy = 0.86602540378443865f * ((f[2] + f[3]) - (f[5] + f[6]));
         } else {
 #pragma unroll
             for (int i = 0; i < 9; ++i)
-                f[i] = load_one<ST>(base + i * plane + (size_t)y * d.pitch + x, wq(i) * d.rho0);
+                f[i] = load_one<ST>(base + i * plane + (size_t)y * d.pitch + x, shf.q9(i));
             r = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
             jx = (f[1] + f[5] + f[8]) - (f[3] + f[6] + f[7]);
             jy = (f[2] + f[5] + f[6]) - (f[4] + f[7] + f[8]);
@@ -120,6 +122,7 @@ __global__ void export_kernel(const LatDesc *desc, int lat, int src, float *out)
 {
     using T = typename Store<ST>::T;
     const LatDesc d = desc[lat];
+    const Shift3 shf = load_shift(&d);
     const T *base = reinterpret_cast<const T *>(d.f[src]);
     const size_t plane = (size_t)d.ny * d.pitch;
     const long long n = (long long)d.nx * d.ny;
@@ -128,7 +131,7 @@ __global__ void export_kernel(const LatDesc *desc, int lat, int src, float *out)
         const int i = (int)(c / n);
         const long long r = c % n;
         const int x = (int)(r % d.nx), y = (int)(r / d.nx);
-        out[c] = Store<ST>::get(base[i * plane + (size_t)y * d.pitch + x], pop_shift(d.q, i, d.rho0));
+        out[c] = Store<ST>::get(base[i * plane + (size_t)y * d.pitch + x], shf.of(d.q, i));
     }
 }
 
@@ -137,6 +140,7 @@ __global__ void import_kernel(const LatDesc *desc, int lat, int dst, const float
 {
     using T = typename Store<ST>::T;
     const LatDesc d = desc[lat];
+    const Shift3 shf = load_shift(&d);
     T *base = reinterpret_cast<T *>(d.f[dst]);
     const size_t plane = (size_t)d.ny * d.pitch;
     const long long n = (long long)d.nx * d.ny;
@@ -145,7 +149,7 @@ __global__ void import_kernel(const LatDesc *desc, int lat, int dst, const float
         const int i = (int)(c / n);
         const long long r = c % n;
         const int x = (int)(r % d.nx), y = (int)(r / d.nx);
-        base[i * plane + (size_t)y * d.pitch + x] = Store<ST>::put(in[c], pop_shift(d.q, i, d.rho0));
+        base[i * plane + (size_t)y * d.pitch + x] = Store<ST>::put(in[c], shf.of(d.q, i));
     }
 }
 
@@ -155,6 +159,7 @@ __global__ void add_density_kernel(const LatDesc *desc, int lat, int buf, float 
 {
     using T = typename Store<ST>::T;
     const LatDesc d = desc[lat];
+    const Shift3 shf = load_shift(&d);
     T *base = reinterpret_cast<T *>(d.f[buf]);
     const size_t plane = (size_t)d.ny * d.pitch;
     const long long n = (long long)d.nx * d.ny;
@@ -164,7 +169,7 @@ __global__ void add_density_kernel(const LatDesc *desc, int lat, int buf, float 
         const long long r = c % n;
         const int x = (int)(r % d.nx), y = (int)(r / d.nx);
         T *p = base + i * plane + (size_t)y * d.pitch + x;
-        const float shift = pop_shift(d.q, i, d.rho0);
+        const float shift = shf.of(d.q, i);
         *p = Store<ST>::put(__fadd_rn(Store<ST>::get(*p, shift), per_population), shift);
     }
 }

@@ -48,8 +48,6 @@ static_assert(reverse_of(1) == 3 && reverse_of(2) == 4 && reverse_of(3) == 1 &&
 __host__ __device__ constexpr float wq7(int i) { return i == 0 ? 0.5f : 1.0f / 12.0f; }
 __host__ __device__ constexpr double wq7_d(int i) { return i == 0 ? 0.5 : 1.0 / 12.0; }
 
-// Storage shift w_i rho0 of population i on a lattice with q populations.
-__host__ __device__ inline float pop_shift(int q, int i, float rho0) { return (q == 7 ? wq7(i) : wq(i)) * rho0; }
 
 enum { MODEL_PASSIVE = 0, MODEL_MIPS = 1, MODEL_CIL = 2 };
 enum { ST_F32 = 0, ST_F16 = 1, ST_BF16 = 2 };
@@ -73,8 +71,41 @@ struct LatDesc {
     float omega;         // 1/tau
     float sigma_q;       // 2 sigma: noise scale of u in [1, 2) (0 = no noise)
     float C, inv_rho_star, rho_star, u_max, u_max2, A, B;
-    float rho0;          // storage shift
+    float rho0;          // reference density of the storage shift
+    float sh[3];         // storage shifts per weight class (see Shift3)
 };
+
+// The shift of 16-bit storage, s_i = f_i - shift_i with shift_i = w_i rho0,
+// per weight class: rest, axis (D2Q7: every moving population), diagonal.
+// The host rounds each shift to a value the storage type holds exactly
+// (storage_shift), so that a population the negative correction set to zero,
+// or one equal to its shift, is stored exactly: with a shift the format rounds
+// (1/9 and 1/36 are not dyadic), every such store would err the same way, a
+// systematic drift of mass and momentum.  FP32 storage ignores the shift.
+struct Shift3 {
+    float c[3];
+    __host__ __device__ __forceinline__ float q9(int i) const { return i == 0 ? c[0] : (i <= 4 ? c[1] : c[2]); }
+    __host__ __device__ __forceinline__ float q7(int i) const { return i == 0 ? c[0] : c[1]; }
+    __host__ __device__ __forceinline__ float of(int q, int i) const { return q == 7 ? q7(i) : q9(i); }
+};
+
+__host__ __device__ __forceinline__ Shift3 load_shift(const LatDesc *d)
+{
+    Shift3 s;
+    s.c[0] = d->sh[0];
+    s.c[1] = d->sh[1];
+    s.c[2] = d->sh[2];
+    return s;
+}
+
+// w rho0 in FP32, rounded to the nearest value of the storage type.
+inline float storage_shift(int storage, double w, float rho0)
+{
+    const float s = (float)(w * (double)rho0);
+    if (storage == ST_F16) return __half2float(__float2half_rn(s));
+    if (storage == ST_BF16) return __bfloat162float(__float2bfloat16_rn(s));
+    return s;
+}
 
 struct StepArgs {
     const LatDesc *desc;  // lattices of this launch group
@@ -143,23 +174,24 @@ template <> struct Store<ST_F32> {
     __device__ static __forceinline__ float get(T v, float) { return v; }
     __device__ static __forceinline__ T put(float f, float) { return f; }
 };
-// The 16-bit forms also convert two values at a time (packed conversions,
-// the same round-to-nearest per element): put2 packs (a, b) into one word, a
-// in the low half, and get2 unpacks it.
+// The 16-bit forms also convert two values at a time (packed conversions and
+// a paired shift, the same round-to-nearest per element): put2 packs (a, b)
+// into one word, a in the low half, and get2 unpacks it.
 template <> struct Store<ST_F16> {
     using T = __half;
     __device__ static __forceinline__ float get(T v, float shift) { return __half2float(v) + shift; }
     __device__ static __forceinline__ T put(float f, float shift) { return __float2half_rn(f - shift); }
     __device__ static __forceinline__ uint32_t put2(float a, float b, float shift)
     {
-        const __half2 h = __floats2half2_rn(a - shift, b - shift);
+        const float2 s = __fadd2_rn(make_float2(a, b), make_float2(-shift, -shift));
+        const __half2 h = __floats2half2_rn(s.x, s.y);
         return *reinterpret_cast<const uint32_t *>(&h);
     }
     __device__ static __forceinline__ void get2(uint32_t w, float shift, float &a, float &b)
     {
-        const float2 v = __half22float2(*reinterpret_cast<const __half2 *>(&w));
-        a = v.x + shift;
-        b = v.y + shift;
+        const float2 v = __fadd2_rn(__half22float2(*reinterpret_cast<const __half2 *>(&w)), make_float2(shift, shift));
+        a = v.x;
+        b = v.y;
     }
 };
 template <> struct Store<ST_BF16> {
@@ -174,14 +206,16 @@ template <> struct Store<ST_BF16> {
     }
     __device__ static __forceinline__ uint32_t put2(float a, float b, float shift)
     {
-        const __nv_bfloat162 h = __floats2bfloat162_rn(a - shift, b - shift);
+        const float2 s = __fadd2_rn(make_float2(a, b), make_float2(-shift, -shift));
+        const __nv_bfloat162 h = __floats2bfloat162_rn(s.x, s.y);
         return *reinterpret_cast<const uint32_t *>(&h);
     }
     __device__ static __forceinline__ void get2(uint32_t w, float shift, float &a, float &b)
     {
-        const float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w));
-        a = v.x + shift;
-        b = v.y + shift;
+        const float2 v =
+            __fadd2_rn(__bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w)), make_float2(shift, shift));
+        a = v.x;
+        b = v.y;
     }
 };
 

@@ -1,9 +1,9 @@
 // lbm_noalloc.cu -- observables of a population field without any allocation.
 //
 // For callers that cannot allocate device memory -- code running inside a
-// memory pool that forbids new allocations, a stream-ordered or graph-replayed
-// pipeline where cudaMalloc would synchronise the device, or a host whose
-// allocator is owned by another runtime -- this entry point reduces a dense
+// memory pool that forbids new allocations, an embedding whose device memory
+// footprint is fixed, or a host whose allocator is owned by another runtime
+// -- this entry point reduces a dense
 // FP32 population field to the observables of lbm_observables using a fixed
 // scratch array compiled into the library instead of caller-provided scratch.
 //

@@ -63,17 +63,17 @@ __device__ __forceinline__ void pull_pop(const typename Store<ST>::T *base, uint
 template <int ST, int VEC>
 __device__ __forceinline__ void pull_row(const typename Store<ST>::T *base, uint32_t plane, int y,
                                          int ny, int nx, int pitch, int x0, bool valid, bool last,
-                                         int lane, float rho0, float f[9][VEC])
+                                         int lane, const Shift3 &sh, float f[9][VEC])
 {
-    pull_pop<ST, VEC, 0>(base, plane, y, ny, nx, pitch, x0, valid, last, lane, wq(0) * rho0, f[0]);
-    pull_pop<ST, VEC, 1>(base, plane, y, ny, nx, pitch, x0, valid, last, lane, wq(1) * rho0, f[1]);
-    pull_pop<ST, VEC, 2>(base, plane, y, ny, nx, pitch, x0, valid, last, lane, wq(2) * rho0, f[2]);
-    pull_pop<ST, VEC, 3>(base, plane, y, ny, nx, pitch, x0, valid, last, lane, wq(3) * rho0, f[3]);
-    pull_pop<ST, VEC, 4>(base, plane, y, ny, nx, pitch, x0, valid, last, lane, wq(4) * rho0, f[4]);
-    pull_pop<ST, VEC, 5>(base, plane, y, ny, nx, pitch, x0, valid, last, lane, wq(5) * rho0, f[5]);
-    pull_pop<ST, VEC, 6>(base, plane, y, ny, nx, pitch, x0, valid, last, lane, wq(6) * rho0, f[6]);
-    pull_pop<ST, VEC, 7>(base, plane, y, ny, nx, pitch, x0, valid, last, lane, wq(7) * rho0, f[7]);
-    pull_pop<ST, VEC, 8>(base, plane, y, ny, nx, pitch, x0, valid, last, lane, wq(8) * rho0, f[8]);
+    pull_pop<ST, VEC, 0>(base, plane, y, ny, nx, pitch, x0, valid, last, lane, sh.q9(0), f[0]);
+    pull_pop<ST, VEC, 1>(base, plane, y, ny, nx, pitch, x0, valid, last, lane, sh.q9(1), f[1]);
+    pull_pop<ST, VEC, 2>(base, plane, y, ny, nx, pitch, x0, valid, last, lane, sh.q9(2), f[2]);
+    pull_pop<ST, VEC, 3>(base, plane, y, ny, nx, pitch, x0, valid, last, lane, sh.q9(3), f[3]);
+    pull_pop<ST, VEC, 4>(base, plane, y, ny, nx, pitch, x0, valid, last, lane, sh.q9(4), f[4]);
+    pull_pop<ST, VEC, 5>(base, plane, y, ny, nx, pitch, x0, valid, last, lane, sh.q9(5), f[5]);
+    pull_pop<ST, VEC, 6>(base, plane, y, ny, nx, pitch, x0, valid, last, lane, sh.q9(6), f[6]);
+    pull_pop<ST, VEC, 7>(base, plane, y, ny, nx, pitch, x0, valid, last, lane, sh.q9(7), f[7]);
+    pull_pop<ST, VEC, 8>(base, plane, y, ny, nx, pitch, x0, valid, last, lane, sh.q9(8), f[8]);
 }
 
 // The same with 64-bit pointer steps from a per-population plane pointer:
@@ -113,17 +113,17 @@ __device__ __forceinline__ void pull_pop_wide(const typename Store<ST>::T *plane
 template <int ST, int VEC>
 __device__ __forceinline__ void pull_row_wide(const typename Store<ST>::T *base, size_t plane, int y,
                                               int ny, int nx, int pitch, int x0, bool valid, bool last,
-                                              int lane, float rho0, float f[9][VEC])
+                                              int lane, const Shift3 &sh, float f[9][VEC])
 {
-    pull_pop_wide<ST, VEC, 0>(base + 0 * plane, y, ny, nx, pitch, x0, valid, last, lane, wq(0) * rho0, f[0]);
-    pull_pop_wide<ST, VEC, 1>(base + 1 * plane, y, ny, nx, pitch, x0, valid, last, lane, wq(1) * rho0, f[1]);
-    pull_pop_wide<ST, VEC, 2>(base + 2 * plane, y, ny, nx, pitch, x0, valid, last, lane, wq(2) * rho0, f[2]);
-    pull_pop_wide<ST, VEC, 3>(base + 3 * plane, y, ny, nx, pitch, x0, valid, last, lane, wq(3) * rho0, f[3]);
-    pull_pop_wide<ST, VEC, 4>(base + 4 * plane, y, ny, nx, pitch, x0, valid, last, lane, wq(4) * rho0, f[4]);
-    pull_pop_wide<ST, VEC, 5>(base + 5 * plane, y, ny, nx, pitch, x0, valid, last, lane, wq(5) * rho0, f[5]);
-    pull_pop_wide<ST, VEC, 6>(base + 6 * plane, y, ny, nx, pitch, x0, valid, last, lane, wq(6) * rho0, f[6]);
-    pull_pop_wide<ST, VEC, 7>(base + 7 * plane, y, ny, nx, pitch, x0, valid, last, lane, wq(7) * rho0, f[7]);
-    pull_pop_wide<ST, VEC, 8>(base + 8 * plane, y, ny, nx, pitch, x0, valid, last, lane, wq(8) * rho0, f[8]);
+    pull_pop_wide<ST, VEC, 0>(base + 0 * plane, y, ny, nx, pitch, x0, valid, last, lane, sh.q9(0), f[0]);
+    pull_pop_wide<ST, VEC, 1>(base + 1 * plane, y, ny, nx, pitch, x0, valid, last, lane, sh.q9(1), f[1]);
+    pull_pop_wide<ST, VEC, 2>(base + 2 * plane, y, ny, nx, pitch, x0, valid, last, lane, sh.q9(2), f[2]);
+    pull_pop_wide<ST, VEC, 3>(base + 3 * plane, y, ny, nx, pitch, x0, valid, last, lane, sh.q9(3), f[3]);
+    pull_pop_wide<ST, VEC, 4>(base + 4 * plane, y, ny, nx, pitch, x0, valid, last, lane, sh.q9(4), f[4]);
+    pull_pop_wide<ST, VEC, 5>(base + 5 * plane, y, ny, nx, pitch, x0, valid, last, lane, sh.q9(5), f[5]);
+    pull_pop_wide<ST, VEC, 6>(base + 6 * plane, y, ny, nx, pitch, x0, valid, last, lane, sh.q9(6), f[6]);
+    pull_pop_wide<ST, VEC, 7>(base + 7 * plane, y, ny, nx, pitch, x0, valid, last, lane, sh.q9(7), f[7]);
+    pull_pop_wide<ST, VEC, 8>(base + 8 * plane, y, ny, nx, pitch, x0, valid, last, lane, sh.q9(8), f[8]);
 }
 
 template <int VEC>
@@ -144,7 +144,7 @@ __device__ __forceinline__ float density(const float f[9][VEC], int j)
 template <int ST, int VEC>
 __device__ __forceinline__ void density_window(const float f[9][VEC], const typename Store<ST>::T *base,
                                                uint32_t plane, int y, int nx, int ny, int pitch, int x0,
-                                               bool valid, bool last, int lane, float rho0,
+                                               bool valid, bool last, int lane, const Shift3 &sh,
                                                float r[VEC + 2])
 {
 #pragma unroll
@@ -158,7 +158,7 @@ __device__ __forceinline__ void density_window(const float f[9][VEC], const type
         const int xh = lane >= 16 ? (xe >= nx ? 0 : xe) : (xs == 0 ? nx - 1 : xs - 1);
         const int xsrc = wrap_once(xh - vx(i), nx), ysrc = wrap_once(y - vy(i), ny);
         v = load_one<ST>(base + ((uint32_t)i * plane + (uint32_t)ysrc * (uint32_t)pitch + (uint32_t)xsrc),
-                         wq(i) * rho0);
+                         sh.q9(i));
     }
     const float s01 = __fadd_rn(v, __shfl_down_sync(FULL, v, 1));         // lanes 0, 2, 4, 6
     const float s03 = __fadd_rn(s01, __shfl_down_sync(FULL, s01, 2));     // lanes 0, 4
@@ -210,6 +210,23 @@ template <> __device__ __forceinline__ float splat<float>(float s) { return s; }
 template <typename F> __device__ __forceinline__ float vmap(float a, F fn) { return fn(a); }
 template <typename F> __device__ __forceinline__ float vmap2(float a, float b, F fn) { return fn(a, b); }
 
+// The same operations on two sites at once (V = float2): the paired FP32
+// instructions of sm_100-class GPUs round each element exactly as the scalar
+// instruction does (round to nearest; a - b is formed as a + (-b), which is
+// the same number), so a site's result does not depend on whether it was
+// computed alone or paired with a neighbour.
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 vneg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 vsub(float2 a, float2 b) { return __fadd2_rn(a, vneg(b)); }
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+template <> __device__ __forceinline__ float2 splat<float2>(float s) { return make_float2(s, s); }
+template <typename F> __device__ __forceinline__ float2 vmap(float2 a, F fn) { return make_float2(fn(a.x), fn(a.y)); }
+template <typename F> __device__ __forceinline__ float2 vmap2(float2 a, float2 b, F fn)
+{
+    return make_float2(fn(a.x, b.x), fn(a.y, b.y));
+}
+
 template <typename V>
 __device__ __forceinline__ V vdensity(const V f[9])
 {
@@ -249,6 +266,28 @@ __device__ __forceinline__ void ustar_v(V rho, V jx, V jy, V gx, V gy, const Sit
         const V sc = vmap2(U0, m2, [](float u0, float q) { return q > 0.f ? __fmul_rn(u0, rsqrtf(q)) : 0.f; });
         sx = vmul(jx, sc);
         sy = vmul(jy, sc);
+    }
+}
+
+// Post-stream densities of a lane's VEC sites (out[j] = density of site j),
+// two sites per paired instruction when PAIRED: the same sums in the same
+// order as density().
+template <int VEC, bool PAIRED>
+__device__ __forceinline__ void densities(const float f[9][VEC], float *out)
+{
+    if constexpr (PAIRED) {
+#pragma unroll
+        for (int p = 0; p < VEC / 2; ++p) {
+            float2 g[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) g[i] = make_float2(f[i][2 * p], f[i][2 * p + 1]);
+            const float2 r = vdensity(g);
+            out[2 * p] = r.x;
+            out[2 * p + 1] = r.y;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) out[j] = density<VEC>(f, j);
     }
 }
 
@@ -365,6 +404,38 @@ __device__ __forceinline__ void negative_correction(float f[9], float rho)
     for (int i = 0; i < 9; ++i) f[i] = __fmul_rn(f[i], sc);
 }
 
+// The same for two sites at once.  A site with nothing negative must come out
+// unchanged, as in the single-site form's early return: its settle steps
+// subtract zeros (exact) and its rescale factor is exactly 1.
+__device__ __forceinline__ void negative_correction2(float2 f[9], float2 rho)
+{
+    unsigned sa = 0u, sb = 0u;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        sa |= __float_as_uint(f[i].x);
+        sb |= __float_as_uint(f[i].y);
+    }
+    if (!((sa | sb) & 0x80000000u)) return;
+    f[0] = make_float2(fmaxf(f[0].x, 0.f), fmaxf(f[0].y, 0.f));
+    auto settle2 = [](float2 &a, float2 &b) {
+        const float2 na = make_float2(fminf(a.x, 0.f), fminf(a.y, 0.f));
+        a = vsub(a, na);
+        b = vsub(b, na);
+        const float2 nb = make_float2(fminf(b.x, 0.f), fminf(b.y, 0.f));
+        b = vsub(b, nb);
+        a = vsub(a, nb);
+    };
+    settle2(f[1], f[3]);
+    settle2(f[2], f[4]);
+    settle2(f[5], f[7]);
+    settle2(f[6], f[8]);
+    const float2 s = vdensity(f);
+    const float2 sc = make_float2((sa & 0x80000000u) ? __fmul_rn(rho.x, __frcp_rn(s.x)) : 1.f,
+                                  (sb & 0x80000000u) ? __fmul_rn(rho.y, __frcp_rn(s.y)) : 1.f);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) f[i] = vmul(f[i], sc);
+}
+
 // The noise uniforms of one site, u_i = 1 + (m_i + 1/2) 2^-14 (the variates
 // are s_i = 2 u_i - 3); collide_v turns them into the zero-sum noise eta_i =
 // 2 sigma (u_i - mean u).
@@ -382,17 +453,58 @@ __device__ __forceinline__ void noise_u(uint32_t x, uint32_t y, uint32_t t, uint
     u[8] = u_from_bits(m8 << 9);
 }
 
-// The update of a lane's VEC sites, one site at a time.  f[i][j] holds f*_i
-// of site j on entry and the new f_i on exit; g*[j] are the MIPS gradients
-// (ignored otherwise).  The helpers above take the value type as a parameter;
-// only V = float is instantiated (a paired float2 form was measured and
-// dropped: its paired products did not round as the single-site ones, and
-// launch shapes must agree bitwise).
-template <int MODEL, int VEC>
+// The update of a lane's VEC sites.  f[i][j] holds f*_i of site j on entry
+// and the new f_i on exit; g*[j] are the MIPS gradients (ignored otherwise).
+// With PAIRED (an even VEC) the sites go two at a time through paired FP32
+// instructions (V = float2: half the arithmetic instructions, each element
+// rounded as the single-site form rounds it), otherwise one at a time: every
+// launch shape gives the same bits.  Measured at 8192^2 MIPS: the 16-bit
+// storage kernels gain 5 % from pairing; the FP32 kernels lose 2-4 % (the
+// paired temporaries spill at the register cap that their occupancy needs),
+// so FP32 keeps single sites.
+#ifndef LBM_PAIRED_F32
+#define LBM_PAIRED_F32 0
+#endif
+#ifndef LBM_PAIRED_16
+#define LBM_PAIRED_16 1
+#endif
+template <int ST, int VEC> __host__ __device__ constexpr bool paired_sites()
+{
+    return VEC % 2 == 0 && (ST == ST_F32 ? LBM_PAIRED_F32 != 0 : LBM_PAIRED_16 != 0);
+}
+
+template <int MODEL, int VEC, bool PAIRED>
 __device__ __forceinline__ void collide_sites(float f[9][VEC], const float gxs[VEC], const float gys[VEC],
                                               const SiteParams &d, bool noise, uint32_t x0, uint32_t y, uint32_t t,
                                               uint32_t id, const uint32_t *rk, const float *rho_row = nullptr)
 {
+    if constexpr (PAIRED) {
+#pragma unroll
+        for (int p = 0; p < VEC / 2; ++p) {
+            const int j0 = 2 * p, j1 = 2 * p + 1;
+            float2 g[9], u[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) g[i] = make_float2(f[i][j0], f[i][j1]);
+            if (noise) {
+                float ua[9], ub[9];
+                noise_u(x0 + j0, y, t, id, rk, ua);
+                noise_u(x0 + j1, y, t, id, rk, ub);
+#pragma unroll
+                for (int i = 0; i < 9; ++i) u[i] = make_float2(ua[i], ub[i]);
+            }
+            float2 rk2;
+            if (rho_row) rk2 = make_float2(rho_row[j0], rho_row[j1]);
+            const float2 rho = collide_v<MODEL, float2>(g, make_float2(gxs[j0], gxs[j1]), make_float2(gys[j0], gys[j1]),
+                                                        d, noise, u, rho_row ? &rk2 : nullptr);
+            negative_correction2(g, rho);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                f[i][j0] = g[i].x;
+                f[i][j1] = g[i].y;
+            }
+        }
+        return;
+    }
 #pragma unroll
     for (int j = 0; j < VEC; ++j) {
         float g[9], u[9];
@@ -539,7 +651,7 @@ __global__ void __launch_bounds__(256, direct_min_blocks<MODEL, ST, VEC, SAMPLE>
     constexpr bool WIDE = MODEL != MODEL_MIPS && NOISE == 0 && !SAMPLE;
     const T *src = reinterpret_cast<const T *>(dp->f[a.src]);
     T *dst = reinterpret_cast<T *>(dp->f[a.src ^ 1]);
-    const float rho0 = dp->rho0;
+    const Shift3 sh = load_shift(dp);
     const uint32_t id = (uint32_t)dp->id;
     const uint32_t t = *a.t_ptr + a.k;
     const bool noise = NOISE == 2 ? d.sigma_q > 0.f : NOISE == 1;
@@ -561,10 +673,10 @@ __global__ void __launch_bounds__(256, direct_min_blocks<MODEL, ST, VEC, SAMPLE>
     if constexpr (MODEL == MODEL_MIPS) {
         float tmp[9][VEC];
         const int yp = wrap_once(y_begin - 1, ny);
-        pull_row<ST, VEC>(src, plane32, yp, ny, nx, pitch, x0, valid, last, lane, rho0, tmp);
-        density_window<ST, VEC>(tmp, src, plane32, yp, nx, ny, pitch, x0, valid, last, lane, rho0, rm);
-        pull_row<ST, VEC>(src, plane32, y_begin, ny, nx, pitch, x0, valid, last, lane, rho0, tmp);
-        density_window<ST, VEC>(tmp, src, plane32, y_begin, nx, ny, pitch, x0, valid, last, lane, rho0, rc);
+        pull_row<ST, VEC>(src, plane32, yp, ny, nx, pitch, x0, valid, last, lane, sh, tmp);
+        density_window<ST, VEC>(tmp, src, plane32, yp, nx, ny, pitch, x0, valid, last, lane, sh, rm);
+        pull_row<ST, VEC>(src, plane32, y_begin, ny, nx, pitch, x0, valid, last, lane, sh, tmp);
+        density_window<ST, VEC>(tmp, src, plane32, y_begin, nx, ny, pitch, x0, valid, last, lane, sh, rc);
     }
 
     for (int y = y_begin; y < y_end; ++y) {
@@ -584,13 +696,13 @@ __global__ void __launch_bounds__(256, direct_min_blocks<MODEL, ST, VEC, SAMPLE>
         if constexpr (MODEL == MODEL_MIPS) {
             float fn[9][VEC];
             const int yn = wrap_once(y + 1, ny);
-            pull_row<ST, VEC>(src, plane32, yn, ny, nx, pitch, x0, valid, last, lane, rho0, fn);
-            density_window<ST, VEC>(fn, src, plane32, yn, nx, ny, pitch, x0, valid, last, lane, rho0, rn);
+            pull_row<ST, VEC>(src, plane32, yn, ny, nx, pitch, x0, valid, last, lane, sh, fn);
+            density_window<ST, VEC>(fn, src, plane32, yn, nx, ny, pitch, x0, valid, last, lane, sh, rn);
         }
         if constexpr (WIDE)
-            pull_row_wide<ST, VEC>(src, plane, y, ny, nx, pitch, x0, valid, last, lane, rho0, fc);
+            pull_row_wide<ST, VEC>(src, plane, y, ny, nx, pitch, x0, valid, last, lane, sh, fc);
         else
-            pull_row<ST, VEC>(src, plane32, y, ny, nx, pitch, x0, valid, last, lane, rho0, fc);
+            pull_row<ST, VEC>(src, plane32, y, ny, nx, pitch, x0, valid, last, lane, sh, fc);
         float gx[VEC], gy[VEC];
         if constexpr (MODEL == MODEL_MIPS) {
             mips_gradients<VEC>(rm, rc, rn, gx, gy);
@@ -603,16 +715,16 @@ __global__ void __launch_bounds__(256, direct_min_blocks<MODEL, ST, VEC, SAMPLE>
         for (int i = 0; i < 9; ++i)
 #pragma unroll
             for (int j = 0; j < VEC; ++j) out[i][j] = fc[i][j];
-        collide_sites<MODEL, VEC>(out, gx, gy, d, noise, (uint32_t)x0, (uint32_t)y, t, id, a.rk,
+        collide_sites<MODEL, VEC, paired_sites<ST, VEC>()>(out, gx, gy, d, noise, (uint32_t)x0, (uint32_t)y, t, id, a.rk,
                                   MODEL == MODEL_MIPS ? rc + 1 : nullptr);
         if (valid) {
 #pragma unroll
             for (int i = 0; i < 9; ++i)
                 if constexpr (WIDE)
-                    store_vec<ST, VEC>(dst + i * plane + (size_t)y * pitch + x0, wq(i) * rho0, out[i]);
+                    store_vec<ST, VEC>(dst + i * plane + (size_t)y * pitch + x0, sh.q9(i), out[i]);
                 else
                     store_vec<ST, VEC>(dst + ((uint32_t)i * plane32 + (uint32_t)y * (uint32_t)pitch + (uint32_t)x0),
-                                       wq(i) * rho0, out[i]);
+                                       sh.q9(i), out[i]);
         }
         if constexpr (SAMPLE) {
             // observables of the stored (rounded) state
@@ -621,7 +733,7 @@ __global__ void __launch_bounds__(256, direct_min_blocks<MODEL, ST, VEC, SAMPLE>
             for (int i = 0; i < 9; ++i)
 #pragma unroll
                 for (int j = 0; j < VEC; ++j)
-                    g[i][j] = Store<ST>::get(Store<ST>::put(out[i][j], wq(i) * rho0), wq(i) * rho0);
+                    g[i][j] = Store<ST>::get(Store<ST>::put(out[i][j], sh.q9(i)), sh.q9(i));
             observe_row<VEC>(g, valid, col, acc, dp->rowp + (size_t)sx * ny + y, lane);
         }
         if constexpr (MODEL == MODEL_MIPS) {
@@ -647,7 +759,7 @@ __global__ void __launch_bounds__(256) observe_kernel(const StepArgs a)
     const int s = (blockIdx.x - dp->block_begin) * (blockDim.x >> 5) + warp;
     if (s >= nsx * nsy) return;
     const int nx = dp->nx, ny = dp->ny, pitch = dp->pitch, rows = dp->rows;
-    const float rho0 = dp->rho0;
+    const Shift3 sh = load_shift(dp);
     const int sx = s % nsx, sy = s / nsx;
     const int x0 = sx * 32 * VEC + lane * VEC;
     const bool valid = x0 < nx;
@@ -664,7 +776,7 @@ __global__ void __launch_bounds__(256) observe_kernel(const StepArgs a)
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             if (valid) {
-                load_vec<ST, VEC>(src + i * plane + (size_t)y * pitch + x0, wq(i) * rho0, g[i]);
+                load_vec<ST, VEC>(src + i * plane + (size_t)y * pitch + x0, sh.q9(i), g[i]);
             } else {
 #pragma unroll
                 for (int j = 0; j < VEC; ++j) g[i][j] = 0.f;

@@ -71,16 +71,16 @@ __device__ __forceinline__ void pull_pop7(const typename Store<ST>::T *plane, in
 
 template <int ST, int VEC, int P>
 __device__ __forceinline__ void pull_row7(const typename Store<ST>::T *base, size_t plane, int y, int ny, int nx,
-                                          int pitch, int x0, bool valid, bool last, int lane, float rho0,
+                                          int pitch, int x0, bool valid, bool last, int lane, const Shift3 &sh,
                                           float f[7][VEC])
 {
-    pull_pop7<ST, VEC, 0, P>(base + 0 * plane, y, ny, nx, pitch, x0, valid, last, lane, wq7(0) * rho0, f[0]);
-    pull_pop7<ST, VEC, 1, P>(base + 1 * plane, y, ny, nx, pitch, x0, valid, last, lane, wq7(1) * rho0, f[1]);
-    pull_pop7<ST, VEC, 2, P>(base + 2 * plane, y, ny, nx, pitch, x0, valid, last, lane, wq7(2) * rho0, f[2]);
-    pull_pop7<ST, VEC, 3, P>(base + 3 * plane, y, ny, nx, pitch, x0, valid, last, lane, wq7(3) * rho0, f[3]);
-    pull_pop7<ST, VEC, 4, P>(base + 4 * plane, y, ny, nx, pitch, x0, valid, last, lane, wq7(4) * rho0, f[4]);
-    pull_pop7<ST, VEC, 5, P>(base + 5 * plane, y, ny, nx, pitch, x0, valid, last, lane, wq7(5) * rho0, f[5]);
-    pull_pop7<ST, VEC, 6, P>(base + 6 * plane, y, ny, nx, pitch, x0, valid, last, lane, wq7(6) * rho0, f[6]);
+    pull_pop7<ST, VEC, 0, P>(base + 0 * plane, y, ny, nx, pitch, x0, valid, last, lane, sh.q7(0), f[0]);
+    pull_pop7<ST, VEC, 1, P>(base + 1 * plane, y, ny, nx, pitch, x0, valid, last, lane, sh.q7(1), f[1]);
+    pull_pop7<ST, VEC, 2, P>(base + 2 * plane, y, ny, nx, pitch, x0, valid, last, lane, sh.q7(2), f[2]);
+    pull_pop7<ST, VEC, 3, P>(base + 3 * plane, y, ny, nx, pitch, x0, valid, last, lane, sh.q7(3), f[3]);
+    pull_pop7<ST, VEC, 4, P>(base + 4 * plane, y, ny, nx, pitch, x0, valid, last, lane, sh.q7(4), f[4]);
+    pull_pop7<ST, VEC, 5, P>(base + 5 * plane, y, ny, nx, pitch, x0, valid, last, lane, sh.q7(5), f[5]);
+    pull_pop7<ST, VEC, 6, P>(base + 6 * plane, y, ny, nx, pitch, x0, valid, last, lane, sh.q7(6), f[6]);
 }
 
 __device__ __forceinline__ float density7(const float f[7])
@@ -99,7 +99,7 @@ __device__ __forceinline__ float density7_at(const float f[7][VEC], int j)
 template <int ST, int VEC, int P>
 __device__ __forceinline__ void density_window7(const float f[7][VEC], const typename Store<ST>::T *base,
                                                 size_t plane, int y, int nx, int ny, int pitch, int x0, bool valid,
-                                                bool last, int lane, float rho0, float r[VEC + 2])
+                                                bool last, int lane, const Shift3 &sh, float r[VEC + 2])
 {
 #pragma unroll
     for (int j = 0; j < VEC; ++j) r[j + 1] = density7_at<VEC>(f, j);
@@ -113,7 +113,7 @@ __device__ __forceinline__ void density_window7(const float f[7][VEC], const typ
     if (i < 7) {
         const int xh = lane >= 16 ? (xe >= nx ? 0 : xe) : (xs == 0 ? nx - 1 : xs - 1);
         const int xsrc = wrap_once(xh + q7_src_dx(i, P), nx), ysrc = wrap_once(y + q7_src_dy(i), ny);
-        v = load_one<ST>(base + i * plane + (size_t)ysrc * pitch + xsrc, wq7(i) * rho0);
+        v = load_one<ST>(base + i * plane + (size_t)ysrc * pitch + xsrc, sh.q7(i));
     }
     const float n1 = __shfl_down_sync(FULL, v, 1);
     const float s01 = i == 6 ? v : __fadd_rn(v, n1);                 // lanes 0, 2, 4: pairs; lane 6: f6
@@ -254,16 +254,16 @@ struct Q7Walk {
 template <int MODEL, int ST, int VEC, bool SAMPLE, int P>
 __device__ __forceinline__ void q7_row(Q7Walk<VEC> &w, int y, const typename Store<ST>::T *src,
                                        typename Store<ST>::T *dst, size_t plane, int nx, int ny, int pitch, int x0,
-                                       bool valid, bool last, int lane, float rho0, const SiteParams &d, bool noise,
+                                       bool valid, bool last, int lane, const Shift3 &sh, const SiteParams &d, bool noise,
                                        uint32_t t, uint32_t id, const uint32_t *rk, double *rowp)
 {
     float fn[7][VEC];
     if constexpr (MODEL == MODEL_MIPS) {
         const int yn = wrap_once(y + 1, ny);
-        pull_row7<ST, VEC, 1 - P>(src, plane, yn, ny, nx, pitch, x0, valid, last, lane, rho0, fn);
-        density_window7<ST, VEC, 1 - P>(fn, src, plane, yn, nx, ny, pitch, x0, valid, last, lane, rho0, w.rn);
+        pull_row7<ST, VEC, 1 - P>(src, plane, yn, ny, nx, pitch, x0, valid, last, lane, sh, fn);
+        density_window7<ST, VEC, 1 - P>(fn, src, plane, yn, nx, ny, pitch, x0, valid, last, lane, sh, w.rn);
     } else {
-        pull_row7<ST, VEC, P>(src, plane, y, ny, nx, pitch, x0, valid, last, lane, rho0, w.fc);
+        pull_row7<ST, VEC, P>(src, plane, y, ny, nx, pitch, x0, valid, last, lane, sh, w.fc);
     }
     float gx[VEC], gy[VEC];
     if constexpr (MODEL == MODEL_MIPS) {
@@ -286,7 +286,7 @@ __device__ __forceinline__ void q7_row(Q7Walk<VEC> &w, int y, const typename Sto
     }
     if (valid) {
 #pragma unroll
-        for (int i = 0; i < 7; ++i) store_vec<ST, VEC>(dst + i * plane + (size_t)y * pitch + x0, wq7(i) * rho0, out[i]);
+        for (int i = 0; i < 7; ++i) store_vec<ST, VEC>(dst + i * plane + (size_t)y * pitch + x0, sh.q7(i), out[i]);
     }
     if constexpr (SAMPLE) {
         float g[7][VEC];
@@ -294,7 +294,7 @@ __device__ __forceinline__ void q7_row(Q7Walk<VEC> &w, int y, const typename Sto
         for (int i = 0; i < 7; ++i)
 #pragma unroll
             for (int j = 0; j < VEC; ++j)
-                g[i][j] = Store<ST>::get(Store<ST>::put(out[i][j], wq7(i) * rho0), wq7(i) * rho0);
+                g[i][j] = Store<ST>::get(Store<ST>::put(out[i][j], sh.q7(i)), sh.q7(i));
         observe_row7<VEC>(g, valid, w.col, w.acc, rowp + y, lane);
     }
     if constexpr (MODEL == MODEL_MIPS) {
@@ -330,7 +330,7 @@ __global__ void __launch_bounds__(256) step_kernel_q7(const StepArgs a)
     const size_t plane = (size_t)ny * pitch;
     const T *src = reinterpret_cast<const T *>(dp->f[a.src]);
     T *dst = reinterpret_cast<T *>(dp->f[a.src ^ 1]);
-    const float rho0 = dp->rho0;
+    const Shift3 sh = load_shift(dp);
     const uint32_t id = (uint32_t)dp->id;
     const uint32_t t = *a.t_ptr + a.k;
     const bool noise = NOISE == 2 ? d.sigma_q > 0.f : NOISE == 1;  // as in step_kernel
@@ -346,15 +346,15 @@ __global__ void __launch_bounds__(256) step_kernel_q7(const StepArgs a)
     if constexpr (MODEL == MODEL_MIPS) {
         float tmp[7][VEC];
         const int yp = wrap_once(y_begin - 1, ny);  // odd
-        pull_row7<ST, VEC, 1>(src, plane, yp, ny, nx, pitch, x0, valid, last, lane, rho0, tmp);
-        density_window7<ST, VEC, 1>(tmp, src, plane, yp, nx, ny, pitch, x0, valid, last, lane, rho0, w.rm);
-        pull_row7<ST, VEC, 0>(src, plane, y_begin, ny, nx, pitch, x0, valid, last, lane, rho0, w.fc);
-        density_window7<ST, VEC, 0>(w.fc, src, plane, y_begin, nx, ny, pitch, x0, valid, last, lane, rho0, w.rc);
+        pull_row7<ST, VEC, 1>(src, plane, yp, ny, nx, pitch, x0, valid, last, lane, sh, tmp);
+        density_window7<ST, VEC, 1>(tmp, src, plane, yp, nx, ny, pitch, x0, valid, last, lane, sh, w.rm);
+        pull_row7<ST, VEC, 0>(src, plane, y_begin, ny, nx, pitch, x0, valid, last, lane, sh, w.fc);
+        density_window7<ST, VEC, 0>(w.fc, src, plane, y_begin, nx, ny, pitch, x0, valid, last, lane, sh, w.rc);
     }
     for (int y = y_begin; y < y_end; y += 2) {
-        q7_row<MODEL, ST, VEC, SAMPLE, 0>(w, y, src, dst, plane, nx, ny, pitch, x0, valid, last, lane, rho0, d, noise,
+        q7_row<MODEL, ST, VEC, SAMPLE, 0>(w, y, src, dst, plane, nx, ny, pitch, x0, valid, last, lane, sh, d, noise,
                                           t, id, a.rk, rowp);
-        q7_row<MODEL, ST, VEC, SAMPLE, 1>(w, y + 1, src, dst, plane, nx, ny, pitch, x0, valid, last, lane, rho0, d,
+        q7_row<MODEL, ST, VEC, SAMPLE, 1>(w, y + 1, src, dst, plane, nx, ny, pitch, x0, valid, last, lane, sh, d,
                                           noise, t, id, a.rk, rowp);
     }
     if constexpr (SAMPLE) observe_flush<VEC>(dp->colp, dp->scal, nx, s, sy, x0, valid, w.col, w.acc, lane);
@@ -370,7 +370,7 @@ __global__ void __launch_bounds__(256) observe_kernel_q7(const StepArgs a)
     const int s = (blockIdx.x - dp->block_begin) * (blockDim.x >> 5) + warp;
     if (s >= nsx * nsy) return;
     const int nx = dp->nx, ny = dp->ny, pitch = dp->pitch, rows = dp->rows;
-    const float rho0 = dp->rho0;
+    const Shift3 sh = load_shift(dp);
     const int sx = s % nsx, sy = s / nsx;
     const int x0 = sx * 32 * VEC + lane * VEC;
     const bool valid = x0 < nx;
@@ -387,7 +387,7 @@ __global__ void __launch_bounds__(256) observe_kernel_q7(const StepArgs a)
 #pragma unroll
         for (int i = 0; i < 7; ++i) {
             if (valid) {
-                load_vec<ST, VEC>(src + i * plane + (size_t)y * pitch + x0, wq7(i) * rho0, g[i]);
+                load_vec<ST, VEC>(src + i * plane + (size_t)y * pitch + x0, sh.q7(i), g[i]);
             } else {
 #pragma unroll
                 for (int j = 0; j < VEC; ++j) g[i][j] = 0.f;

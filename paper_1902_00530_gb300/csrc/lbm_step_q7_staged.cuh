@@ -94,40 +94,40 @@ __device__ __forceinline__ void stage_pop7(const typename Store<ST>::T *seg, int
 }
 
 template <int ST, int VEC, int P>
-__device__ __forceinline__ void stage_row7(const typename Store<ST>::T *buf, int b, float rho0, float f[7][VEC])
+__device__ __forceinline__ void stage_row7(const typename Store<ST>::T *buf, int b, const Shift3 &sh, float f[7][VEC])
 {
     using G = StageGeom7<ST, VEC>;
-    stage_pop7<ST, VEC, 0, P>(buf + 0 * G::SEG, b, wq7(0) * rho0, f[0]);
-    stage_pop7<ST, VEC, 1, P>(buf + 1 * G::SEG, b, wq7(1) * rho0, f[1]);
-    stage_pop7<ST, VEC, 2, P>(buf + 2 * G::SEG, b, wq7(2) * rho0, f[2]);
-    stage_pop7<ST, VEC, 3, P>(buf + 3 * G::SEG, b, wq7(3) * rho0, f[3]);
-    stage_pop7<ST, VEC, 4, P>(buf + 4 * G::SEG, b, wq7(4) * rho0, f[4]);
-    stage_pop7<ST, VEC, 5, P>(buf + 5 * G::SEG, b, wq7(5) * rho0, f[5]);
-    stage_pop7<ST, VEC, 6, P>(buf + 6 * G::SEG, b, wq7(6) * rho0, f[6]);
+    stage_pop7<ST, VEC, 0, P>(buf + 0 * G::SEG, b, sh.q7(0), f[0]);
+    stage_pop7<ST, VEC, 1, P>(buf + 1 * G::SEG, b, sh.q7(1), f[1]);
+    stage_pop7<ST, VEC, 2, P>(buf + 2 * G::SEG, b, sh.q7(2), f[2]);
+    stage_pop7<ST, VEC, 3, P>(buf + 3 * G::SEG, b, sh.q7(3), f[3]);
+    stage_pop7<ST, VEC, 4, P>(buf + 4 * G::SEG, b, sh.q7(4), f[4]);
+    stage_pop7<ST, VEC, 5, P>(buf + 5 * G::SEG, b, sh.q7(5), f[5]);
+    stage_pop7<ST, VEC, 6, P>(buf + 6 * G::SEG, b, sh.q7(6), f[6]);
 }
 
 // Post-stream density at shared index c of a staged row of parity P.
 template <int ST, int VEC, int P>
-__device__ __forceinline__ float stage_density_at7(const typename Store<ST>::T *buf, int c, float rho0)
+__device__ __forceinline__ float stage_density_at7(const typename Store<ST>::T *buf, int c, const Shift3 &sh)
 {
     using G = StageGeom7<ST, VEC>;
     float v[7];
 #pragma unroll
-    for (int i = 0; i < 7; ++i) v[i] = Store<ST>::get(buf[i * G::SEG + c + q7_src_dx(i, P)], wq7(i) * rho0);
+    for (int i = 0; i < 7; ++i) v[i] = Store<ST>::get(buf[i * G::SEG + c + q7_src_dx(i, P)], sh.q7(i));
     return density7(v);
 }
 
 template <int ST, int VEC, int P>
-__device__ __forceinline__ void stage_density_window7(const typename Store<ST>::T *buf, int b, float rho0, int lane,
+__device__ __forceinline__ void stage_density_window7(const typename Store<ST>::T *buf, int b, const Shift3 &sh, int lane,
                                                       float r[VEC + 2])
 {
     float f[7][VEC];
-    stage_row7<ST, VEC, P>(buf, b, rho0, f);
+    stage_row7<ST, VEC, P>(buf, b, sh, f);
 #pragma unroll
     for (int j = 0; j < VEC; ++j) r[j + 1] = density7_at<VEC>(f, j);
-    const float right = stage_density_at7<ST, VEC, P>(buf, b + VEC, rho0);
+    const float right = stage_density_at7<ST, VEC, P>(buf, b + VEC, sh);
     float left = __shfl_up_sync(FULL, r[VEC], 1);
-    if (lane == 0) left = stage_density_at7<ST, VEC, P>(buf, b - 1, rho0);
+    if (lane == 0) left = stage_density_at7<ST, VEC, P>(buf, b - 1, sh);
     r[0] = left;
     r[VEC + 1] = right;
 }
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(128, staged7_min_blocks<VEC>()) step_staged_ke
     const size_t plane = (size_t)ny * pitch;
     const T *src = reinterpret_cast<const T *>(dp->f[a.src]);
     T *dst = reinterpret_cast<T *>(dp->f[a.src ^ 1]);
-    const float rho0 = dp->rho0;
+    const Shift3 sh = load_shift(dp);
     const uint32_t id = (uint32_t)dp->id;
     const uint32_t t = *a.t_ptr + a.k;
     const bool noise = NOISE == 2 ? d.sigma_q > 0.f : NOISE == 1;
@@ -211,10 +211,10 @@ __global__ void __launch_bounds__(128, staged7_min_blocks<VEC>()) step_staged_ke
     float rm[VEC + 2], rc[VEC + 2], rn[VEC + 2];
     int q = 0;
     if constexpr (MIPS) {
-        if (wait_q(0)) stage_density_window7<ST, VEC, 1>(stage_ptr(0), b, rho0, lane, rm);  // row y_begin-1: odd
+        if (wait_q(0)) stage_density_window7<ST, VEC, 1>(stage_ptr(0), b, sh, lane, rm);  // row y_begin-1: odd
         issue_next();
         q = 1;
-        if (wait_q(1)) stage_density_window7<ST, VEC, 0>(stage_ptr(1), b, rho0, lane, rc);
+        if (wait_q(1)) stage_density_window7<ST, VEC, 0>(stage_ptr(1), b, sh, lane, rc);
     }
 
     // one row of parity P; returns false if a wait gave up
@@ -224,11 +224,11 @@ __global__ void __launch_bounds__(128, staged7_min_blocks<VEC>()) step_staged_ke
         float f[7][VEC];
         if constexpr (MIPS) {
             if (!wait_q(qc + 1)) return false;
-            stage_density_window7<ST, VEC, 1 - P>(stage_ptr(qc + 1), b, rho0, lane, rn);
+            stage_density_window7<ST, VEC, 1 - P>(stage_ptr(qc + 1), b, sh, lane, rn);
         } else {
             if (!wait_q(qc)) return false;
         }
-        stage_row7<ST, VEC, P>(stage_ptr(qc), b, rho0, f);
+        stage_row7<ST, VEC, P>(stage_ptr(qc), b, sh, f);
         issue_next();
         q = qc + 1;
         float gx[VEC], gy[VEC];
@@ -253,7 +253,7 @@ __global__ void __launch_bounds__(128, staged7_min_blocks<VEC>()) step_staged_ke
         if (valid) {
 #pragma unroll
             for (int i = 0; i < 7; ++i)
-                store_vec<ST, VEC>(dst + i * plane + (size_t)y * pitch + x0, wq7(i) * rho0, out[i]);
+                store_vec<ST, VEC>(dst + i * plane + (size_t)y * pitch + x0, sh.q7(i), out[i]);
         }
         if constexpr (SAMPLE) {
             float g[7][VEC];
@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(128, staged7_min_blocks<VEC>()) step_staged_ke
             for (int i = 0; i < 7; ++i)
 #pragma unroll
                 for (int j = 0; j < VEC; ++j)
-                    g[i][j] = Store<ST>::get(Store<ST>::put(out[i][j], wq7(i) * rho0), wq7(i) * rho0);
+                    g[i][j] = Store<ST>::get(Store<ST>::put(out[i][j], sh.q7(i)), sh.q7(i));
             observe_row7<VEC>(g, valid, col, acc, rowp + y, lane);
         }
         if constexpr (MIPS) {

@@ -159,45 +159,49 @@ __device__ __forceinline__ void stage_pop(const typename Store<ST>::T *seg, int 
 }
 
 template <int ST, int VEC>
-__device__ __forceinline__ void stage_row(const typename Store<ST>::T *buf, int b, float rho0, float f[9][VEC])
+__device__ __forceinline__ void stage_row(const typename Store<ST>::T *buf, int b, const Shift3 &sh, float f[9][VEC])
 {
     using G = StageGeom<ST, VEC>;
-    stage_pop<ST, VEC, 0>(buf + 0 * G::SEG, b, wq(0) * rho0, f[0]);
-    stage_pop<ST, VEC, 1>(buf + 1 * G::SEG, b, wq(1) * rho0, f[1]);
-    stage_pop<ST, VEC, 2>(buf + 2 * G::SEG, b, wq(2) * rho0, f[2]);
-    stage_pop<ST, VEC, 3>(buf + 3 * G::SEG, b, wq(3) * rho0, f[3]);
-    stage_pop<ST, VEC, 4>(buf + 4 * G::SEG, b, wq(4) * rho0, f[4]);
-    stage_pop<ST, VEC, 5>(buf + 5 * G::SEG, b, wq(5) * rho0, f[5]);
-    stage_pop<ST, VEC, 6>(buf + 6 * G::SEG, b, wq(6) * rho0, f[6]);
-    stage_pop<ST, VEC, 7>(buf + 7 * G::SEG, b, wq(7) * rho0, f[7]);
-    stage_pop<ST, VEC, 8>(buf + 8 * G::SEG, b, wq(8) * rho0, f[8]);
+    stage_pop<ST, VEC, 0>(buf + 0 * G::SEG, b, sh.q9(0), f[0]);
+    stage_pop<ST, VEC, 1>(buf + 1 * G::SEG, b, sh.q9(1), f[1]);
+    stage_pop<ST, VEC, 2>(buf + 2 * G::SEG, b, sh.q9(2), f[2]);
+    stage_pop<ST, VEC, 3>(buf + 3 * G::SEG, b, sh.q9(3), f[3]);
+    stage_pop<ST, VEC, 4>(buf + 4 * G::SEG, b, sh.q9(4), f[4]);
+    stage_pop<ST, VEC, 5>(buf + 5 * G::SEG, b, sh.q9(5), f[5]);
+    stage_pop<ST, VEC, 6>(buf + 6 * G::SEG, b, sh.q9(6), f[6]);
+    stage_pop<ST, VEC, 7>(buf + 7 * G::SEG, b, sh.q9(7), f[7]);
+    stage_pop<ST, VEC, 8>(buf + 8 * G::SEG, b, sh.q9(8), f[8]);
 }
 
 // Post-stream density at shared index c (one site) of a staged row.
 template <int ST, int VEC>
-__device__ __forceinline__ float stage_density_at(const typename Store<ST>::T *buf, int c, float rho0)
+__device__ __forceinline__ float stage_density_at(const typename Store<ST>::T *buf, int c, const Shift3 &sh)
 {
     using G = StageGeom<ST, VEC>;
     float v[9][1];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) v[i][0] = Store<ST>::get(buf[i * G::SEG + c - vx(i)], wq(i) * rho0);
+    for (int i = 0; i < 9; ++i) v[i][0] = Store<ST>::get(buf[i * G::SEG + c - vx(i)], sh.q9(i));
     return density<1>(v, 0);
 }
 
 // Density window of a staged row: r[0] at x0-1, r[1..VEC] the lane's sites,
-// r[VEC+1] at x0+VEC.  Neighbours inside the warp come by shuffle; lane 0's
-// left and every lane's right neighbour are summed from shared memory.
+// r[VEC+1] at x0+VEC.  Neighbours come by shuffle (a lane past a ragged strip
+// end sums the right halo's site, which its segment index reaches); the two
+// sites outside the warp's columns, lane 0's left and lane 31's right, are
+// summed from shared memory in one pass, each lane summing the site its role
+// needs (the same values and order as its neighbour's own sum).
 template <int ST, int VEC>
-__device__ __forceinline__ void stage_density_window(const typename Store<ST>::T *buf, int b, float rho0,
+__device__ __forceinline__ void stage_density_window(const typename Store<ST>::T *buf, int b, const Shift3 &sh,
                                                      int lane, float r[VEC + 2])
 {
     float f[9][VEC];
-    stage_row<ST, VEC>(buf, b, rho0, f);
-#pragma unroll
-    for (int j = 0; j < VEC; ++j) r[j + 1] = density<VEC>(f, j);
-    const float right = stage_density_at<ST, VEC>(buf, b + VEC, rho0);
+    stage_row<ST, VEC>(buf, b, sh, f);
+    densities<VEC, paired_sites<ST, VEC>()>(f, r + 1);
+    const float edge = stage_density_at<ST, VEC>(buf, lane == 0 ? b - 1 : b + VEC, sh);
     float left = __shfl_up_sync(FULL, r[VEC], 1);
-    if (lane == 0) left = stage_density_at<ST, VEC>(buf, b - 1, rho0);
+    float right = __shfl_down_sync(FULL, r[1], 1);
+    if (lane == 0) left = edge;
+    if (lane == 31) right = edge;
     r[0] = left;
     r[VEC + 1] = right;
 }
@@ -250,7 +254,7 @@ __global__ void __launch_bounds__(128, staged_min_blocks<VEC>()) step_staged_ker
     const size_t plane = (size_t)ny * pitch;
     const T *src = reinterpret_cast<const T *>(dp->f[a.src]);
     T *dst = reinterpret_cast<T *>(dp->f[a.src ^ 1]);
-    const float rho0 = dp->rho0;
+    const Shift3 sh = load_shift(dp);
     const uint32_t id = (uint32_t)dp->id;
     const uint32_t t = *a.t_ptr + a.k;
     const bool noise = NOISE == 2 ? d.sigma_q > 0.f : NOISE == 1;
@@ -297,10 +301,10 @@ __global__ void __launch_bounds__(128, staged_min_blocks<VEC>()) step_staged_ker
     float rm[VEC + 2], rc[VEC + 2], rn[VEC + 2];
     int q = 0;  // next stage to consume
     if constexpr (MIPS) {
-        if (wait_q(0)) stage_density_window<ST, VEC>(stage_ptr(0), b, rho0, lane, rm);
+        if (wait_q(0)) stage_density_window<ST, VEC>(stage_ptr(0), b, sh, lane, rm);
         issue_next();
         q = 1;
-        if (wait_q(1)) stage_density_window<ST, VEC>(stage_ptr(1), b, rho0, lane, rc);
+        if (wait_q(1)) stage_density_window<ST, VEC>(stage_ptr(1), b, sh, lane, rc);
     }
 
     for (int y = y_begin; y < y_end && ok; ++y) {
@@ -308,11 +312,11 @@ __global__ void __launch_bounds__(128, staged_min_blocks<VEC>()) step_staged_ker
         float f[9][VEC];
         if constexpr (MIPS) {
             if (!wait_q(qc + 1)) break;
-            stage_density_window<ST, VEC>(stage_ptr(qc + 1), b, rho0, lane, rn);
+            stage_density_window<ST, VEC>(stage_ptr(qc + 1), b, sh, lane, rn);
         } else {
             if (!wait_q(qc)) break;
         }
-        stage_row<ST, VEC>(stage_ptr(qc), b, rho0, f);
+        stage_row<ST, VEC>(stage_ptr(qc), b, sh, f);
         issue_next();  // refills this row's buffer (issue_row syncs the warp first)
         q = qc + 1;
 
@@ -328,12 +332,12 @@ __global__ void __launch_bounds__(128, staged_min_blocks<VEC>()) step_staged_ker
         for (int i = 0; i < 9; ++i)
 #pragma unroll
             for (int j = 0; j < VEC; ++j) out[i][j] = f[i][j];
-        collide_sites<MODEL, VEC>(out, gx, gy, d, noise, (uint32_t)x0, (uint32_t)y, t, id, a.rk,
+        collide_sites<MODEL, VEC, paired_sites<ST, VEC>()>(out, gx, gy, d, noise, (uint32_t)x0, (uint32_t)y, t, id, a.rk,
                                   MIPS ? rc + 1 : nullptr);
         if (valid) {
 #pragma unroll
             for (int i = 0; i < 9; ++i)
-                store_vec<ST, VEC>(dst + i * plane + (size_t)y * pitch + x0, wq(i) * rho0, out[i]);
+                store_vec<ST, VEC>(dst + i * plane + (size_t)y * pitch + x0, sh.q9(i), out[i]);
         }
         if constexpr (SAMPLE) {
             float g[9][VEC];
@@ -341,7 +345,7 @@ __global__ void __launch_bounds__(128, staged_min_blocks<VEC>()) step_staged_ker
             for (int i = 0; i < 9; ++i)
 #pragma unroll
                 for (int j = 0; j < VEC; ++j)
-                    g[i][j] = Store<ST>::get(Store<ST>::put(out[i][j], wq(i) * rho0), wq(i) * rho0);
+                    g[i][j] = Store<ST>::get(Store<ST>::put(out[i][j], sh.q9(i)), sh.q9(i));
             observe_row<VEC>(g, valid, col, acc, dp->rowp + (size_t)sx * ny + y, lane);
         }
         if constexpr (MIPS) {

@@ -8,6 +8,20 @@ import oracle as O
 import workloads as W
 
 
+def storage_shifts(storage: str, q: int = 9, rho0: float = 1.0) -> np.ndarray:
+    """The per-population shifts of 16-bit storage as the library sets them:
+    w_i rho0 in FP32, rounded to the nearest value of the storage type (so a
+    zero population is stored exactly)."""
+    import torch
+    w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4) if q == 9 else np.array([0.5] + [1 / 12] * 6)
+    s = torch.tensor(w * rho0, dtype=torch.float32)
+    if storage == "f16s":
+        s = s.to(torch.float16)
+    elif storage == "bf16s":
+        s = s.to(torch.bfloat16)
+    return s.to(torch.float64).numpy()
+
+
 def split_preset(name: str, **overrides):
     d = W.preset(name, **overrides)
     model = d.pop("model")
@@ -35,11 +49,11 @@ def gpu_run(model, d, nx, ny, steps, seed, spec, **kw):
     return f
 
 
-def oracle_run(model, d, nx, ny, steps, seed, spec, bits=64, lattice_id=0, q=9):
+def oracle_run(model, d, nx, ny, steps, seed, spec, bits=64, lattice_id=0, q=9, threads=1):
     p = O.params(**d)
     init, run = (O.init7, O.run7) if q == 7 else (O.init, O.run)
     f = init(nx, ny, seed, lattice_id=lattice_id, **spec, prm=p, bits=bits)
-    return run(f, model, p, seed, 0, steps, lattice_id=lattice_id, bits=bits)
+    return run(f, model, p, seed, 0, steps, lattice_id=lattice_id, bits=bits, threads=threads)
 
 
 def moments(f):

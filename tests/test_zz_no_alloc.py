@@ -1,13 +1,13 @@
 """The allocation-free observables entry point (lbm_observables_noalloc).
 
 Some callers cannot allocate device memory: code running inside a memory pool
-or allocator owned by another runtime, replayed stream or graph pipelines in
-which cudaMalloc would synchronise the device, embeddings with a fixed memory
+or allocator owned by another runtime, embeddings with a fixed device memory
 footprint.  For them the library offers one entry point whose scratch is a
 fixed array compiled into the library.  This test calls it through the C ABI
-on two different states in a row -- so the second call runs on scratch the
-first one left behind -- and checks each result against the context-based
-lbm_observables, within the tolerances the other observable tests use.  It
+on several states in a row -- so each call runs on scratch the one before left
+behind -- and checks each result against the context-based lbm_observables and
+the oracle's observables of the same state, within the tolerances the other
+observable tests use.  It
 lives in its own file, collected last.
 """
 import ctypes
@@ -36,9 +36,16 @@ def _close(a, b):
     assert abs(a["var_rho"] - b["var_rho"]) < 1e-7
 
 
-def test_noalloc_observables_match_context_observables_twice():
+def test_noalloc_observables_match_context_and_oracle_twice():
+    """Sizes below and above one block's 256 columns and the maximum side (a
+    thread then sums several columns), each checked against lbm_observables of
+    the same context and the oracle's observables of the same state."""
+    import numpy as np
+    import oracle as O
     cases = [("CIL_RHO1", 192, 96, W.init_ordered(0.23, rho_amp=0.05, u_amp=0.02)),
-             ("MIPS_RHO1", 80, 200, W.INIT_CONFIG1)]
+             ("MIPS_RHO1", 80, 200, W.INIT_CONFIG1),
+             ("CIL_RHO1", 300, 70, W.INIT_CONFIG2),
+             ("MIPS_RHO1", 4096, 8, W.INIT_CONFIG1)]
     results = []
     for name, nx, ny, spec in cases:
         model, d = split_preset(name)
@@ -46,12 +53,15 @@ def test_noalloc_observables_match_context_observables_twice():
         sim.step(40)
         ref = sim.observables()
         f = sim.get_state(host=False)          # dense FP32 (9, ny, nx) on the device
-        results.append((sim, f, d["B"], ref))
+        orc = O.observables(f.cpu().numpy().astype(np.float64), B=d["B"])
+        results.append((sim, f, d["B"], ref, orc))
     lib = results[0][0].lib
-    for sim, f, B, ref in results:             # two calls in a row, different sizes
-        _close(_noalloc(lib, f, B, sim.stream.cuda_stream), ref)
-    sim, f, B, ref = results[0]                # and the first state again
-    _close(_noalloc(lib, f, B, sim.stream.cuda_stream), ref)
+    for sim, f, B, ref, orc in results:        # calls in a row, different sizes
+        got = _noalloc(lib, f, B, sim.stream.cuda_stream)
+        _close(got, ref)
+        _close(got, orc)
+    sim, f, B, ref, orc = results[0]           # and the first state again
+    _close(_noalloc(lib, f, B, sim.stream.cuda_stream), orc)
     for sim, *_ in results:
         sim.close()
 
