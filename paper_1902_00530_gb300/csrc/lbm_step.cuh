@@ -503,18 +503,18 @@ __device__ __forceinline__ void collide_sites(float f[9][VEC], const float gxs[V
                 f[i][j1] = g[i].y;
             }
         }
-        return;
-    }
+    } else {
 #pragma unroll
-    for (int j = 0; j < VEC; ++j) {
-        float g[9], u[9];
+        for (int j = 0; j < VEC; ++j) {
+            float g[9], u[9];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) g[i] = f[i][j];
-        if (noise) noise_u(x0 + j, y, t, id, rk, u);
-        const float rho = collide_v<MODEL, float>(g, gxs[j], gys[j], d, noise, u, rho_row ? rho_row + j : nullptr);
-        negative_correction(g, rho);
+            for (int i = 0; i < 9; ++i) g[i] = f[i][j];
+            if (noise) noise_u(x0 + j, y, t, id, rk, u);
+            const float rho = collide_v<MODEL, float>(g, gxs[j], gys[j], d, noise, u, rho_row ? rho_row + j : nullptr);
+            negative_correction(g, rho);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) f[i][j] = g[i];
+            for (int i = 0; i < 9; ++i) f[i][j] = g[i];
+        }
     }
 }
 
@@ -753,14 +753,25 @@ template <int ST, int VEC>
 __global__ void __launch_bounds__(256) observe_kernel(const StepArgs a)
 {
     using T = typename Store<ST>::T;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, warps = blockDim.x >> 5;
     const LatDesc *dp = a.desc + find_lattice(a.desc, a.nlat, blockIdx.x);
     const int nsx = dp->nsx, nsy = dp->nsy;
-    const int s = (blockIdx.x - dp->block_begin) * (blockDim.x >> 5) + warp;
-    if (s >= nsx * nsy) return;
+    const int bl = blockIdx.x - dp->block_begin;
+    int sx, sy;
+    if (a.stages > 0) {  // a staged group's blocks hold `warps` adjacent strips of one strip row
+        const int ncx = (nsx + warps - 1) / warps;
+        sx = (bl % ncx) * warps + warp;
+        sy = bl / ncx;
+        if (sx >= nsx) return;
+    } else {
+        const int s0 = bl * warps + warp;
+        if (s0 >= nsx * nsy) return;
+        sx = s0 % nsx;
+        sy = s0 / nsx;
+    }
+    const int s = sy * nsx + sx;
     const int nx = dp->nx, ny = dp->ny, pitch = dp->pitch, rows = dp->rows;
     const Shift3 sh = load_shift(dp);
-    const int sx = s % nsx, sy = s / nsx;
     const int x0 = sx * 32 * VEC + lane * VEC;
     const bool valid = x0 < nx;
     const int y_begin = sy * rows, y_end = min(y_begin + rows, ny);

@@ -1,21 +1,26 @@
 // lbm_step_staged.cuh -- the fused step with TMA-staged population rows.
 //
 // Same per-site arithmetic as step_kernel (lbm_step.cuh), different data
-// movement: each warp owns a ring of `stages` shared-memory buffers.  Buffer q
-// holds, for destination row r(q), the nine source-row segments it pulls from
-// (row r - e_y of population i), each covering the warp's 32*VEC columns plus
-// 16 bytes of halo on both sides (the periodic wrap is resolved by copying the
-// halo from the other end of the row).  The segments arrive by bulk copies
-// (cp.async.bulk, global -> shared) that complete on the buffer's mbarrier,
-// issued `stages - 1` (MIPS: `stages - 2`) rows ahead of use, so the memory
-// latency is hidden without holding the rows in registers.  Lanes read their
+// movement.  A block of W warps owns W horizontally adjacent warp strips of one
+// strip row (W * 32 * VEC columns, `rows` rows) and a ring of `stages`
+// shared-memory buffers.  Buffer q holds, for destination row r(q), the nine
+// source-row segments it pulls from (row r - e_y of population i), each
+// covering the block's columns plus 16 bytes of halo on both sides (the
+// periodic wrap is resolved by copying the halo from the other end of the
+// row).  The segments arrive by bulk copies (cp.async.bulk, global -> shared)
+// that complete on the buffer's "full" mbarrier; warp 0 issues them for the
+// whole block, `stages - 1` (MIPS: `stages - 2`) rows ahead of use, once every
+// warp has released the buffer's previous row on its "empty" mbarrier.  So a
+// row costs nine copies per block rather than per warp, and the memory
+// latency is hidden without holding rows in registers.  Lanes read their
 // pulled values straight from shared memory, halo included: no shuffles and no
 // lane-divergent edge loads.
 //
 // Requirements (checked on the host): nx a multiple of the 16-byte halo width
 // (4 FP32 / 8 16-bit values) and at least that wide.  Every wait is bounded:
-// on expiry the warp raises DEVERR_TIMEOUT in the error word, drains its
-// copies (again bounded) and returns.
+// on expiry the warp raises DEVERR_TIMEOUT in the error word and leaves its
+// loop; warp 0 then drains the copies in flight (again bounded) before the
+// block exits.
 #pragma once
 
 #include "lbm_step.cuh"
@@ -86,55 +91,61 @@ __device__ __forceinline__ bool stage_wait(uint64_t *bar, uint32_t parity)
 template <int ST, int VEC> struct StageGeom {
     using T = typename Store<ST>::T;
     static constexpr int HALO = 16 / (int)sizeof(T);        // halo width in elements (16 bytes)
-    static constexpr int W = 32 * VEC;                       // strip width
-    static constexpr int SEG = W + 2 * HALO;                 // elements per population segment
-    static constexpr int STAGE_BYTES = 9 * SEG * (int)sizeof(T);
+    static constexpr int W = 32 * VEC;                       // strip width of one warp
+    // elements per population segment of a block of `warps` warps (a multiple
+    // of 16 bytes, so every segment starts 16-byte aligned)
+    __host__ __device__ static constexpr int seg(int warps) { return warps * W + 2 * HALO; }
+    __host__ __device__ static constexpr int stage_bytes(int warps) { return 9 * seg(warps) * (int)sizeof(T); }
 };
 
-// Issue the segment copies of destination row y into stage buffer `buf` and
-// arm its barrier (lane 0 arms).  A strip whose halos lie inside the row
-// (xs >= HALO, xe + HALO <= nx) takes one copy per population, lanes 0..8:
-// the left halo, the strip and the right halo are contiguous in the row and
-// in the segment.  A strip at the periodic edge takes three per population,
-// lanes 0..26.  Each copy is issued by one elected lane at a time, so fewer
-// copies is fewer issue slots.
+// Issue the segment copies of destination row y into stage buffer `buf` (seg
+// elements per population) and arm its barrier (lane 0 arms); executed by one
+// warp for the block, whose columns are xs .. xe-1.  Where the halos lie inside
+// the row (xs >= HALO, xe + HALO <= nx) each population takes one copy, lanes
+// 0..8: the left halo, the block's columns and the right halo are contiguous in
+// the row and in the segment.  At the periodic edge each takes three, lanes
+// 0..26.  Each copy is issued by one elected lane at a time.
 template <int ST, int VEC>
-__device__ __forceinline__ void issue_row(typename Store<ST>::T *buf, uint64_t *bar,
+__device__ __forceinline__ void issue_row(typename Store<ST>::T *buf, int seg_elems, uint64_t *bar,
                                           const typename Store<ST>::T *src, size_t plane, int pitch,
                                           int nx, int ny, int xs, int xe, int y, int lane)
 {
     using G = StageGeom<ST, VEC>;
     using T = typename Store<ST>::T;
     const uint32_t main_bytes = (uint32_t)(xe - xs) * (uint32_t)sizeof(T);
-    __syncwarp();  // every lane has finished reading this buffer's previous row
     if (lane == 0) mbar_arrive_expect_tx(bar, 9u * (main_bytes + 32u));
     __syncwarp();
     if (xs >= G::HALO && xe + G::HALO <= nx) {
         if (lane < 9) {
-            fence_proxy_async_smem();  // order those reads before the copy's writes
+            fence_proxy_async_smem();  // order the buffer's earlier reads before the copy's writes
             const int i = lane;
             const int dy = (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
             const int r = wrap_once(y - dy, ny);
             const T *row = src + (size_t)i * plane + (size_t)r * pitch;
-            bulk_copy_g2s(buf + i * G::SEG, row + (xs - G::HALO), main_bytes + 32u, bar);
+            bulk_copy_g2s(buf + i * seg_elems, row + (xs - G::HALO), main_bytes + 32u, bar);
         }
     } else if (lane < 27) {
-        fence_proxy_async_smem();  // order those reads before the copy's writes
+        fence_proxy_async_smem();  // order the buffer's earlier reads before the copy's writes
         const int i = lane / 3, part = lane % 3;
         const int dy = (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
         const int r = wrap_once(y - dy, ny);
         const T *row = src + (size_t)i * plane + (size_t)r * pitch;
-        T *seg = buf + i * G::SEG;
+        T *seg = buf + i * seg_elems;
         if (part == 0) {  // left halo: columns xs-HALO .. xs-1 (periodic)
             const int c = xs == 0 ? nx - G::HALO : xs - G::HALO;
             bulk_copy_g2s(seg, row + c, 16u, bar);
-        } else if (part == 1) {  // the strip itself
+        } else if (part == 1) {  // the block's columns
             bulk_copy_g2s(seg + G::HALO, row + xs, main_bytes, bar);
         } else {  // right halo: columns xe .. xe+HALO-1 (periodic)
             const int c = xe >= nx ? 0 : xe;
             bulk_copy_g2s(seg + G::HALO + (xe - xs), row + c, 16u, bar);
         }
     }
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
 // Pulled values of population I for this lane's VEC sites, from the stage:
@@ -159,28 +170,27 @@ __device__ __forceinline__ void stage_pop(const typename Store<ST>::T *seg, int 
 }
 
 template <int ST, int VEC>
-__device__ __forceinline__ void stage_row(const typename Store<ST>::T *buf, int b, const Shift3 &sh, float f[9][VEC])
+__device__ __forceinline__ void stage_row(const typename Store<ST>::T *buf, int sg, int b, const Shift3 &sh,
+                                          float f[9][VEC])
 {
-    using G = StageGeom<ST, VEC>;
-    stage_pop<ST, VEC, 0>(buf + 0 * G::SEG, b, sh.q9(0), f[0]);
-    stage_pop<ST, VEC, 1>(buf + 1 * G::SEG, b, sh.q9(1), f[1]);
-    stage_pop<ST, VEC, 2>(buf + 2 * G::SEG, b, sh.q9(2), f[2]);
-    stage_pop<ST, VEC, 3>(buf + 3 * G::SEG, b, sh.q9(3), f[3]);
-    stage_pop<ST, VEC, 4>(buf + 4 * G::SEG, b, sh.q9(4), f[4]);
-    stage_pop<ST, VEC, 5>(buf + 5 * G::SEG, b, sh.q9(5), f[5]);
-    stage_pop<ST, VEC, 6>(buf + 6 * G::SEG, b, sh.q9(6), f[6]);
-    stage_pop<ST, VEC, 7>(buf + 7 * G::SEG, b, sh.q9(7), f[7]);
-    stage_pop<ST, VEC, 8>(buf + 8 * G::SEG, b, sh.q9(8), f[8]);
+    stage_pop<ST, VEC, 0>(buf + 0 * sg, b, sh.q9(0), f[0]);
+    stage_pop<ST, VEC, 1>(buf + 1 * sg, b, sh.q9(1), f[1]);
+    stage_pop<ST, VEC, 2>(buf + 2 * sg, b, sh.q9(2), f[2]);
+    stage_pop<ST, VEC, 3>(buf + 3 * sg, b, sh.q9(3), f[3]);
+    stage_pop<ST, VEC, 4>(buf + 4 * sg, b, sh.q9(4), f[4]);
+    stage_pop<ST, VEC, 5>(buf + 5 * sg, b, sh.q9(5), f[5]);
+    stage_pop<ST, VEC, 6>(buf + 6 * sg, b, sh.q9(6), f[6]);
+    stage_pop<ST, VEC, 7>(buf + 7 * sg, b, sh.q9(7), f[7]);
+    stage_pop<ST, VEC, 8>(buf + 8 * sg, b, sh.q9(8), f[8]);
 }
 
 // Post-stream density at shared index c (one site) of a staged row.
 template <int ST, int VEC>
-__device__ __forceinline__ float stage_density_at(const typename Store<ST>::T *buf, int c, const Shift3 &sh)
+__device__ __forceinline__ float stage_density_at(const typename Store<ST>::T *buf, int sg, int c, const Shift3 &sh)
 {
-    using G = StageGeom<ST, VEC>;
     float v[9][1];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) v[i][0] = Store<ST>::get(buf[i * G::SEG + c - vx(i)], sh.q9(i));
+    for (int i = 0; i < 9; ++i) v[i][0] = Store<ST>::get(buf[i * sg + c - vx(i)], sh.q9(i));
     return density<1>(v, 0);
 }
 
@@ -191,13 +201,13 @@ __device__ __forceinline__ float stage_density_at(const typename Store<ST>::T *b
 // summed from shared memory in one pass, each lane summing the site its role
 // needs (the same values and order as its neighbour's own sum).
 template <int ST, int VEC>
-__device__ __forceinline__ void stage_density_window(const typename Store<ST>::T *buf, int b, const Shift3 &sh,
-                                                     int lane, float r[VEC + 2])
+__device__ __forceinline__ void stage_density_window(const typename Store<ST>::T *buf, int sg, int b,
+                                                     const Shift3 &sh, int lane, float r[VEC + 2])
 {
     float f[9][VEC];
-    stage_row<ST, VEC>(buf, b, sh, f);
+    stage_row<ST, VEC>(buf, sg, b, sh, f);
     densities<VEC, paired_sites<ST, VEC>()>(f, r + 1);
-    const float edge = stage_density_at<ST, VEC>(buf, lane == 0 ? b - 1 : b + VEC, sh);
+    const float edge = stage_density_at<ST, VEC>(buf, sg, lane == 0 ? b - 1 : b + VEC, sh);
     float left = __shfl_up_sync(FULL, r[VEC], 1);
     float right = __shfl_down_sync(FULL, r[1], 1);
     if (lane == 0) left = edge;
@@ -206,50 +216,70 @@ __device__ __forceinline__ void stage_density_window(const typename Store<ST>::T
     r[VEC + 1] = right;
 }
 
-// Minimum resident blocks of 128 threads per SM the compiler must allow for
-// (caps registers per thread at 65536 / (128 * blocks): 85, 102, 128, 128);
-// measured per VEC: these caps cost FP32 nothing and speed 16-bit storage up.
-#ifndef LBM_STAGED_MINB_1
-#define LBM_STAGED_MINB_1 6
+// Register cap per thread of the staged kernels per VEC (80, 96, 128, 128):
+// measured per VEC, these caps cost FP32 nothing and speed 16-bit storage up.
+// Blocks have up to 8 warps (256 threads).
+#ifndef LBM_STAGED_REGS_1
+#define LBM_STAGED_REGS_1 80
 #endif
-#ifndef LBM_STAGED_MINB_2
-#define LBM_STAGED_MINB_2 5
+#ifndef LBM_STAGED_REGS_2
+#define LBM_STAGED_REGS_2 96
 #endif
-#ifndef LBM_STAGED_MINB_4
-#define LBM_STAGED_MINB_4 4
+#ifndef LBM_STAGED_REGS_4
+#define LBM_STAGED_REGS_4 128
 #endif
-#ifndef LBM_STAGED_MINB_8
-#define LBM_STAGED_MINB_8 4
+#ifndef LBM_STAGED_REGS_8
+#define LBM_STAGED_REGS_8 128
 #endif
-template <int VEC> constexpr int staged_min_blocks()
+template <int VEC> constexpr int staged_max_regs()
 {
-    return VEC == 1 ? LBM_STAGED_MINB_1 : (VEC == 2 ? LBM_STAGED_MINB_2 : (VEC == 4 ? LBM_STAGED_MINB_4 : LBM_STAGED_MINB_8));
+    return VEC == 1 ? LBM_STAGED_REGS_1 : (VEC == 2 ? LBM_STAGED_REGS_2 : (VEC == 4 ? LBM_STAGED_REGS_4 : LBM_STAGED_REGS_8));
+}
+
+// The block's place in its lattice: strip row sy, first strip column sx0, and
+// the number of its warps whose strips lie inside the lattice (at least 1).
+struct StagedBlock {
+    const LatDesc *dp;
+    int sx0, sy, nact;
+};
+
+__device__ __forceinline__ StagedBlock staged_block(const StepArgs &a, int warps)
+{
+    StagedBlock g;
+    g.dp = a.desc + find_lattice(a.desc, a.nlat, blockIdx.x);
+    const int ncx = (g.dp->nsx + warps - 1) / warps;
+    const int bl = blockIdx.x - g.dp->block_begin;
+    g.sx0 = (bl % ncx) * warps;
+    g.sy = bl / ncx;
+    g.nact = min(warps, g.dp->nsx - g.sx0);
+    return g;
 }
 
 template <int MODEL, int ST, int VEC, bool SAMPLE, int NOISE>
-__global__ void __launch_bounds__(128, staged_min_blocks<VEC>()) step_staged_kernel(const StepArgs a)
+__global__ void __maxnreg__(staged_max_regs<VEC>()) step_staged_kernel(const StepArgs a)
 {
     using T = typename Store<ST>::T;
     using G = StageGeom<ST, VEC>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, warps = blockDim.x >> 5;
     const int S = a.stages;
-    // per-warp carve-out: S stage buffers, then S barriers
-    T *ring = reinterpret_cast<T *>(smem_raw + (size_t)warp * S * G::STAGE_BYTES);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw + (size_t)(blockDim.x >> 5) * S * G::STAGE_BYTES) +
-                     warp * S;
+    const int sg = G::seg(warps);  // elements per population segment
+    const int stage_elems = 9 * sg;
+    // carve-out: S stage buffers, then S "full" and S "empty" barriers
+    T *ring = reinterpret_cast<T *>(smem_raw);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + (size_t)S * stage_elems * sizeof(T));
+    uint64_t *empty = full + S;
 
-    const LatDesc *dp = a.desc + find_lattice(a.desc, a.nlat, blockIdx.x);
-    const int nsx = dp->nsx, nsy = dp->nsy;
-    const int s = (blockIdx.x - dp->block_begin) * (blockDim.x >> 5) + warp;
-    if (s >= nsx * nsy) return;  // whole warp leaves together; its barriers are never used
+    const StagedBlock blk = staged_block(a, warps);
+    const LatDesc *dp = blk.dp;
+    const int nsx = dp->nsx;
     const int nx = dp->nx, ny = dp->ny, pitch = dp->pitch, rows = dp->rows;
-    const SiteParams d = load_params(dp);
-    const int sx = s % nsx, sy = s / nsx;
-    const int xs = sx * G::W, xe = min(xs + G::W, nx);
-    const int x0 = xs + lane * VEC;
+    const int sx = blk.sx0 + warp, sy = blk.sy;
+    const int s = sy * nsx + sx;  // this warp's strip (observable partials)
+    const int xs = blk.sx0 * G::W, xe = min(xs + blk.nact * G::W, nx);  // the block's columns
+    const int x0 = sx * G::W + lane * VEC;
     const bool valid = x0 < nx;
-    const int b = G::HALO + lane * VEC;  // shared index of x0 within a segment
+    const int b = G::HALO + warp * G::W + lane * VEC;  // shared index of x0 within a segment
     const int y_begin = sy * rows, y_end = min(y_begin + rows, ny);
     const size_t plane = (size_t)ny * pitch;
     const T *src = reinterpret_cast<const T *>(dp->f[a.src]);
@@ -257,36 +287,53 @@ __global__ void __launch_bounds__(128, staged_min_blocks<VEC>()) step_staged_ker
     const Shift3 sh = load_shift(dp);
     const uint32_t id = (uint32_t)dp->id;
     const uint32_t t = *a.t_ptr + a.k;
+    const SiteParams d = load_params(dp);
     const bool noise = NOISE == 2 ? d.sigma_q > 0.f : NOISE == 1;
+    const bool leader = warp == 0;
 
-    if (lane == 0) {
-        for (int k = 0; k < S; ++k) mbar_init(&bars[k], 1);
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < S; ++k) {
+            mbar_init(&full[k], 1);
+            mbar_init(&empty[k], (uint32_t)blk.nact);
+        }
         mbar_init_fence();
     }
-    __syncwarp();
+    __syncthreads();
+    if (warp >= blk.nact) return;  // a strip past the lattice's last column: no work, no arrivals
 
     // rows in order of use: MIPS also needs y_begin-1 and y_end (density halo)
     constexpr bool MIPS = (MODEL == MODEL_MIPS);
     const int q_first_row = MIPS ? y_begin - 1 : y_begin;
     const int nq = (y_end - y_begin) + (MIPS ? 2 : 0);
-    int issued = 0;
-    auto issue_next = [&]() {
-        if (issued < nq) {
-            const int k = issued % S;
-            issue_row<ST, VEC>(ring + (size_t)k * (G::STAGE_BYTES / sizeof(T)), &bars[k], src, plane, pitch, nx, ny,
-                               xs, xe, wrap_once(q_first_row + issued, ny), lane);
-            ++issued;
+    auto stage_ptr = [&](int q) { return ring + (size_t)(q % S) * stage_elems; };
+    bool ok = true;
+    auto fail = [&]() {
+        ok = false;
+        if (lane == 0) atomicOr(a.err, (unsigned)DEVERR_TIMEOUT);
+    };
+    int issued = 0;  // rows issued (warp 0)
+    auto issue = [&]() {
+        const int k = issued % S;
+        issue_row<ST, VEC>(ring + (size_t)k * stage_elems, sg, &full[k], src, plane, pitch, nx, ny, xs, xe,
+                           wrap_once(q_first_row + issued, ny), lane);
+        ++issued;
+    };
+    if (leader)
+        while (issued < S && issued < nq) issue();
+
+    // Row q is consumed: every lane of the warp has finished its reads, and the
+    // warp tells warp 0, which refills the buffer with row q + S once all warps
+    // have done so.
+    auto release = [&](int q) {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[q % S]);
+        if (leader && ok && issued < nq) {
+            if (!stage_wait(&empty[q % S], (uint32_t)((q / S) & 1))) fail();
+            else issue();
         }
     };
-    for (int k = 0; k < S; ++k) issue_next();
-
-    auto stage_ptr = [&](int q) { return ring + (size_t)(q % S) * (G::STAGE_BYTES / sizeof(T)); };
-    bool ok = true;
     auto wait_q = [&](int q) {
-        if (ok && !stage_wait(&bars[q % S], (uint32_t)((q / S) & 1))) {
-            ok = false;
-            if (lane == 0) atomicOr(a.err, (unsigned)DEVERR_TIMEOUT);
-        }
+        if (ok && !stage_wait(&full[q % S], (uint32_t)((q / S) & 1))) fail();
         return ok;
     };
 
@@ -301,10 +348,12 @@ __global__ void __launch_bounds__(128, staged_min_blocks<VEC>()) step_staged_ker
     float rm[VEC + 2], rc[VEC + 2], rn[VEC + 2];
     int q = 0;  // next stage to consume
     if constexpr (MIPS) {
-        if (wait_q(0)) stage_density_window<ST, VEC>(stage_ptr(0), b, sh, lane, rm);
-        issue_next();
+        if (wait_q(0)) {
+            stage_density_window<ST, VEC>(stage_ptr(0), sg, b, sh, lane, rm);
+            release(0);
+        }
         q = 1;
-        if (wait_q(1)) stage_density_window<ST, VEC>(stage_ptr(1), b, sh, lane, rc);
+        if (wait_q(1)) stage_density_window<ST, VEC>(stage_ptr(1), sg, b, sh, lane, rc);
     }
 
     for (int y = y_begin; y < y_end && ok; ++y) {
@@ -312,12 +361,12 @@ __global__ void __launch_bounds__(128, staged_min_blocks<VEC>()) step_staged_ker
         float f[9][VEC];
         if constexpr (MIPS) {
             if (!wait_q(qc + 1)) break;
-            stage_density_window<ST, VEC>(stage_ptr(qc + 1), b, sh, lane, rn);
+            stage_density_window<ST, VEC>(stage_ptr(qc + 1), sg, b, sh, lane, rn);
         } else {
             if (!wait_q(qc)) break;
         }
-        stage_row<ST, VEC>(stage_ptr(qc), b, sh, f);
-        issue_next();  // refills this row's buffer (issue_row syncs the warp first)
+        stage_row<ST, VEC>(stage_ptr(qc), sg, b, sh, f);
+        release(qc);
         q = qc + 1;
 
         float gx[VEC], gy[VEC];
@@ -332,8 +381,8 @@ __global__ void __launch_bounds__(128, staged_min_blocks<VEC>()) step_staged_ker
         for (int i = 0; i < 9; ++i)
 #pragma unroll
             for (int j = 0; j < VEC; ++j) out[i][j] = f[i][j];
-        collide_sites<MODEL, VEC, paired_sites<ST, VEC>()>(out, gx, gy, d, noise, (uint32_t)x0, (uint32_t)y, t, id, a.rk,
-                                  MIPS ? rc + 1 : nullptr);
+        collide_sites<MODEL, VEC, paired_sites<ST, VEC>()>(out, gx, gy, d, noise, (uint32_t)x0, (uint32_t)y, t, id,
+                                                           a.rk, MIPS ? rc + 1 : nullptr);
         if (valid) {
 #pragma unroll
             for (int i = 0; i < 9; ++i)
@@ -356,21 +405,17 @@ __global__ void __launch_bounds__(128, staged_min_blocks<VEC>()) step_staged_ker
             }
         }
     }
-    if (!ok) {
-        // drain the copies still in flight (bounded) before the warp exits
-        for (int qq = q; qq < issued; ++qq) (void)stage_wait(&bars[qq % S], (uint32_t)((qq / S) & 1));
-        return;
+    if (leader) {
+        // every copy warp 0 issued must land before the block's shared memory
+        // is released: wait for the rows it has not waited for itself (the
+        // latest phase of each of their buffers; bounded)
+        for (int qq = q + (MIPS ? 1 : 0); qq < issued; ++qq)
+            (void)stage_wait(&full[qq % S], (uint32_t)((qq / S) & 1));
     }
-    // MIPS consumed its halo rows; make sure nothing is left in flight
-    for (int qq = q + (MIPS ? 1 : 0); qq < issued; ++qq) (void)stage_wait(&bars[qq % S], (uint32_t)((qq / S) & 1));
+    if (!ok) return;
     if constexpr (SAMPLE) observe_flush<VEC>(dp->colp, dp->scal, nx, s, sy, x0, valid, col, acc, lane);
 }
 
-template <int ST, int VEC>
-constexpr int staged_stage_bytes()
-{
-    return StageGeom<ST, VEC>::STAGE_BYTES;
-}
 
 }  // namespace lbm
 
@@ -382,7 +427,7 @@ namespace lbm {
 template <int MODEL, int ST, int VEC, bool SAMPLE, int NOISE>
 static cudaError_t launch_one_staged(const StepArgs &a, int blocks, int warps, cudaStream_t stream)
 {
-    const size_t bytes = (size_t)warps * a.stages * (StageGeom<ST, VEC>::STAGE_BYTES + sizeof(uint64_t));
+    const size_t bytes = (size_t)a.stages * (StageGeom<ST, VEC>::stage_bytes(warps) + 2 * sizeof(uint64_t));
     auto kern = step_staged_kernel<MODEL, ST, VEC, SAMPLE, NOISE>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;

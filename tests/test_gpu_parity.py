@@ -167,7 +167,7 @@ def test_ragged_sizes_default_shape(nx, ny):
 
 SHAPES_FIXED = [(1, 16), (2, 16), (4, 16), (4, 48), (2, 128), (8, 32),
                 (1, 16, 4, 3), (2, 32, 2, 4), (4, 64, 4, 6), (2, 48, 4, 3), (8, 32, 2, 4), (4, 16, 1, 3),
-                (2, 32, 1, 4)]
+                (2, 32, 1, 4), (4, 16, 8, 3), (1, 16, 8, 5), (8, 16, 8, 4)]
 
 
 @pytest.mark.parametrize("shape", SHAPES_FIXED, ids=lambda s: "x".join(map(str, s)))
@@ -197,7 +197,7 @@ def test_staged_kernel_small_and_ragged(nx, ny):
     for name, over, steps, spec in (("MIPS_RHO1", {}, 3, W.INIT_CONFIG1),
                                     ("CIL_RHO1", {}, 20, W.init_ordered(U0_CIL))):
         model, d = split_preset(name, **over)
-        for shape in ((1, 16, 4, 3), (4, 32, 2, 4)):
+        for shape in ((1, 16, 4, 3), (4, 32, 2, 4), (4, 16, 8, 3)):
             if nx % shape[0]:
                 continue
             got = gpu_run(model, d, nx, ny, steps, SEED, spec, tuning=shape)
