@@ -173,6 +173,10 @@ def workload_spec(name: str):
         d = W.preset("MIPS_RHO1")
         return dict(nx=4096, ny=4096, model=d.pop("model"), params=d, init=W.INIT_CONFIG1, sample_every=100,
                     seed=W.seed(3), label="mips_rho1_4096x4096")
+    if name == "cil8192":  # the CIL closure at the benchmark's size (FP32 copy-bound with noise)
+        d = W.preset("CIL_RHO1")
+        return dict(nx=8192, ny=8192, model=d.pop("model"), params=d, init=W.INIT_CONFIG2, sample_every=100,
+                    seed=W.seed(3), label="cil_rho1_8192x8192")
     if name == "cil1024":
         d = W.preset("CIL_RHO1")
         return dict(nx=1024, ny=1024, model=d.pop("model"), params=d, init=W.INIT_CONFIG2, sample_every=100,

@@ -48,15 +48,20 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t by
                  : "memory");
 }
 
+// Test a phase of the barrier; while it is incomplete the thread may be
+// suspended in hardware for up to WAIT_SUSPEND_NS (so a waiting warp takes no
+// issue slots from the others) before the test returns.
+constexpr uint32_t WAIT_SUSPEND_NS = 1000000u;
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
 {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(WAIT_SUSPEND_NS)
         : "memory");
     return ok != 0;
 }
@@ -80,6 +85,7 @@ constexpr long long WAIT_LIMIT_CYCLES = 2000000000LL;
 // Warp-uniform bounded wait for one phase of a stage barrier.
 __device__ __forceinline__ bool stage_wait(uint64_t *bar, uint32_t parity)
 {
+    if (__all_sync(FULL, mbar_try_wait(bar, parity))) return true;  // the usual case: no clock read
     const long long t0 = clock64();
     while (true) {
         const bool ok = mbar_try_wait(bar, parity);
