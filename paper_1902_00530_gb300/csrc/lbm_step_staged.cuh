@@ -252,9 +252,9 @@ struct StagedBlock {
 __device__ __forceinline__ StagedBlock staged_block(const StepArgs &a, int warps)
 {
     StagedBlock g;
-    g.dp = a.desc + find_lattice(a.desc, a.nlat, blockIdx.x);
+    g.dp = a.desc + find_lattice(a.desc, a.nlat, (int)blockIdx.x + a.block_base);
     const int ncx = (g.dp->nsx + warps - 1) / warps;
-    const int bl = blockIdx.x - g.dp->block_begin;
+    const int bl = (int)blockIdx.x + a.block_base - g.dp->block_begin;
     g.sx0 = (bl % ncx) * warps;
     g.sy = bl / ncx;
     g.nact = min(warps, g.dp->nsx - g.sx0);
@@ -332,6 +332,10 @@ __global__ void __maxnreg__(staged_max_regs<VEC>()) step_staged_kernel(const Ste
     // have done so.
     auto release = [&](int q) {
         __syncwarp();
+        if (blk.nact == 1) {  // a single warp: its own reads are all there is to wait for
+            if (ok && issued < nq) issue();
+            return;
+        }
         if (lane == 0) mbar_arrive(&empty[q % S]);
         if (leader && ok && issued < nq) {
             if (!stage_wait(&empty[q % S], (uint32_t)((q / S) & 1))) fail();
