@@ -231,19 +231,6 @@ lbm_status lbm_load(lbm_ctx *ctx, const char *path);
 lbm_status lbm_set_tuning(lbm_ctx *ctx, int32_t mode, int32_t vec, int32_t rows, int32_t warps,
                           int32_t stages);
 
-/* Order of a batch's steps.  Lattices are independent (App. C.3-C.4: many
- * independent runs), so a group of many lattices may be stepped in passes:
- * each pass of lattices takes a whole chunk of steps (up to 256, whole sample
- * periods) before the next pass starts.  This changes no result (states and
- * samples are bitwise those of the step-by-step order) and keeps a pass whose
- * populations fit in the L2 cache there, but a pass that small gives launches
- * too small to fill a GB300, so it is off by default.  lattices_per_pass: 0 =
- * off (every group step by step), > 0 = that many lattices per pass.
- * lbm_get_batch_passes reports the pass size of the group of `lattice` (0 =
- * not split).  Host only. */
-lbm_status lbm_set_batch_passes(lbm_ctx *ctx, int32_t lattices_per_pass);
-lbm_status lbm_get_batch_passes(const lbm_ctx *ctx, int32_t lattice, int32_t *lattices_per_pass);
-
 /* Run the tuner now (times candidate shapes on the bound buffers without
  * changing the state).  Syncs. */
 lbm_status lbm_tune(lbm_ctx *ctx);

@@ -221,16 +221,6 @@ class Simulation:
                                             ctypes.byref(s)))
         return v.value, r.value, w.value, s.value
 
-    def set_batch_passes(self, lattices_per_pass: int) -> None:
-        """Step a batch in passes of that many lattices (0: step by step, the default)."""
-        self._check(self.lib.lbm_set_batch_passes(self.ctx, int(lattices_per_pass)))
-
-    def batch_passes(self, lattice: int = 0) -> int:
-        """Lattices per pass of the group of `lattice` (0: stepped whole)."""
-        n = ctypes.c_int32()
-        self._check(self.lib.lbm_get_batch_passes(self.ctx, lattice, ctypes.byref(n)))
-        return n.value
-
     def set_graphs(self, enabled: bool) -> None:
         self._check(self.lib.lbm_set_graphs(self.ctx, 1 if enabled else 0))
 

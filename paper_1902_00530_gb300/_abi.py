@@ -62,8 +62,6 @@ SIGNATURES = {
     "lbm_load": (ctypes.c_int, [_CTX, ctypes.c_char_p]),
     "lbm_set_tuning": (ctypes.c_int, [_CTX, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                       ctypes.c_int32]),
-    "lbm_set_batch_passes": (ctypes.c_int, [_CTX, ctypes.c_int32]),
-    "lbm_get_batch_passes": (ctypes.c_int, [_CTX, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
     "lbm_tune": (ctypes.c_int, [_CTX]),
     "lbm_get_tuning": (ctypes.c_int, [_CTX, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
                                       ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),

@@ -53,7 +53,6 @@ struct GroupHost {
     int vec = 1, rows = 32, warps = 4, blocks = 0;
     int stages = 0;  // 0: direct-load kernel; >= 2: TMA-staged kernel with that many row buffers
     size_t desc_off = 0;
-    int pass = 0;    // lattices stepped together through a chunk of steps (0: all, step by step)
 };
 
 struct GraphKey {
@@ -85,7 +84,6 @@ struct lbm_ctx {
     bool tuned = false, use_graphs = true;
     std::map<GraphKey, std::pair<cudaGraphExec_t, int64_t>> graphs;  // graph and its kernel launches
     int64_t last_launches = 0;
-    int pass_mode = 0;  // lattices per pass: 0 off (step by step), > 0 fixed
     // kernel timing (lbm_set_profiling)
     bool profiling = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -299,8 +297,6 @@ LatDesc make_desc(const lbm_ctx *c, const LatHost &L, int block_begin, const Gro
     return d;
 }
 
-void choose_passes(lbm_ctx *c);
-
 // Recompute strip geometry from the group shapes and upload all descriptor
 // tables.  Syncs.
 lbm_status upload_descs(lbm_ctx *c)
@@ -337,7 +333,6 @@ lbm_status upload_descs(lbm_ctx *c)
                        cudaMemcpyHostToDevice, c->stream),
        "upload descriptors");
     CK(cudaStreamSynchronize(c->stream), "synchronise after descriptor upload");
-    choose_passes(c);
     return LBM_OK;
 }
 
@@ -348,18 +343,11 @@ const LatDesc *all_desc(const lbm_ctx *c)
 uint32_t *t_dev(const lbm_ctx *c) { return reinterpret_cast<uint32_t *>(c->scratch); }
 unsigned *err_dev(const lbm_ctx *c) { return reinterpret_cast<unsigned *>(c->scratch + 4); }
 
-// One step of members [m0, m1) of group g (a contiguous part of its
-// descriptor table; by default all of them).
-cudaError_t launch_group_step(const lbm_ctx *c, const GroupHost &g, int src, uint32_t k, bool sample, int m0 = 0,
-                              int m1 = -1)
+cudaError_t launch_group_step(const lbm_ctx *c, const GroupHost &g, int src, uint32_t k, bool sample)
 {
-    if (m1 < 0) m1 = (int)g.members.size();
-    const int b0 = c->lats[g.members[m0]].block_begin;
-    const int b1 = m1 < (int)g.members.size() ? c->lats[g.members[m1]].block_begin : g.blocks;
     StepArgs a;
-    a.desc = reinterpret_cast<const LatDesc *>(c->scratch + g.desc_off) + m0;
-    a.nlat = m1 - m0;
-    a.block_base = b0;
+    a.desc = reinterpret_cast<const LatDesc *>(c->scratch + g.desc_off);
+    a.nlat = (int)g.members.size();
     a.src = src;
     a.t_ptr = t_dev(c);
     a.k = k;
@@ -373,23 +361,21 @@ cudaError_t launch_group_step(const lbm_ctx *c, const GroupHost &g, int src, uin
     }
     // noise form of the launch: compile-time when the group is uniform in sigma
     int with = 0;
-    for (int m = m0; m < m1; ++m)
-        with += (float)(2.0 * c->lats[g.members[m]].p.sigma) > 0.f ? 1 : 0;  // as the kernel sees sigma_q
-    const int noise = with == 0 ? 0 : (with == m1 - m0 ? 1 : 2);
+    for (int m : g.members) with += (float)(2.0 * c->lats[m].p.sigma) > 0.f ? 1 : 0;  // as the kernel sees sigma_q
+    const int noise = with == 0 ? 0 : (with == (int)g.members.size() ? 1 : 2);
     const int kind = g.stages > 0 ? 1 : 0;
-    const int blocks = b1 - b0;
     if (g.q == 7) {
         if (g.storage == LBM_F32)
-            return launch_step_q7_f32(g.model, kind, g.vec, sample, noise, a, blocks, g.warps, c->stream);
+            return launch_step_q7_f32(g.model, kind, g.vec, sample, noise, a, g.blocks, g.warps, c->stream);
         if (g.storage == LBM_F16_SHIFTED)
-            return launch_step_q7_f16(g.model, kind, g.vec, sample, noise, a, blocks, g.warps, c->stream);
-        return launch_step_q7_bf16(g.model, kind, g.vec, sample, noise, a, blocks, g.warps, c->stream);
+            return launch_step_q7_f16(g.model, kind, g.vec, sample, noise, a, g.blocks, g.warps, c->stream);
+        return launch_step_q7_bf16(g.model, kind, g.vec, sample, noise, a, g.blocks, g.warps, c->stream);
     }
     if (g.storage == LBM_F32)
-        return launch_step_f32(g.model, kind, g.vec, sample, noise, a, blocks, g.warps, c->stream);
+        return launch_step_f32(g.model, kind, g.vec, sample, noise, a, g.blocks, g.warps, c->stream);
     if (g.storage == LBM_F16_SHIFTED)
-        return launch_step_f16(g.model, kind, g.vec, sample, noise, a, blocks, g.warps, c->stream);
-    return launch_step_bf16(g.model, kind, g.vec, sample, noise, a, blocks, g.warps, c->stream);
+        return launch_step_f16(g.model, kind, g.vec, sample, noise, a, g.blocks, g.warps, c->stream);
+    return launch_step_bf16(g.model, kind, g.vec, sample, noise, a, g.blocks, g.warps, c->stream);
 }
 
 cudaError_t launch_group_observe(const lbm_ctx *c, const GroupHost &g, int src)
@@ -397,7 +383,6 @@ cudaError_t launch_group_observe(const lbm_ctx *c, const GroupHost &g, int src)
     StepArgs a;
     a.desc = reinterpret_cast<const LatDesc *>(c->scratch + g.desc_off);
     a.nlat = (int)g.members.size();
-    a.block_base = 0;
     a.src = src;
     a.t_ptr = t_dev(c);
     a.k = 0;
@@ -437,44 +422,9 @@ cudaError_t prof_end(lbm_ctx *c)
     return cudaEventRecord(c->ev_pool[c->ev_marks.back().first + 1], c->stream);
 }
 
-// Enqueue n steps starting at host time t0 from buffer parity p0.  When a
-// group is split into passes (GroupHost::pass), each pass of lattices takes all
-// n steps before the next pass starts: lattices are independent, so the order
-// changes no result, and a pass whose populations fit in L2 is stepped from L2
-// instead of HBM.  Its sample steps are finalised per pass.
+// Enqueue n steps starting at host time t0 from buffer parity p0.
 lbm_status enqueue_steps(lbm_ctx *c, int64_t n, int64_t t0, int p0, int64_t *launches)
 {
-    bool passes = false;
-    for (const GroupHost &g : c->groups) passes = passes || (g.pass > 0 && g.pass < (int)g.members.size());
-    if (passes) {
-        for (const GroupHost &g : c->groups) {
-            const int nm = (int)g.members.size();
-            const int per = g.pass > 0 ? g.pass : nm;
-            for (int m0 = 0; m0 < nm; m0 += per) {
-                const int m1 = std::min(nm, m0 + per);
-                for (int64_t k = 0; k < n; ++k) {
-                    const bool sample = c->sample_every > 0 && ((t0 + k + 1) % c->sample_every == 0);
-                    CK(prof_begin(c, true), "record event");
-                    CK(launch_group_step(c, g, (int)((p0 + k) & 1), (uint32_t)k, sample, m0, m1), "launch step kernel");
-                    CK(prof_end(c), "record event");
-                    ++*launches;
-                    if (sample) {
-                        CK(prof_begin(c, false), "record event");
-                        CK(launch_finalize(reinterpret_cast<const LatDesc *>(c->scratch + g.desc_off) + m0, m1 - m0,
-                                           c->max_chunk, t_dev(c), (uint32_t)k, 1, err_dev(c), c->stream),
-                           "launch finaliser");
-                        CK(prof_end(c), "record event");
-                        ++*launches;
-                    }
-                }
-            }
-        }
-        CK(prof_begin(c, false), "record event");
-        CK(launch_advance_time(t_dev(c), (uint32_t)n, c->stream), "launch time advance");
-        CK(prof_end(c), "record event");
-        ++*launches;
-        return LBM_OK;
-    }
     for (int64_t k = 0; k < n; ++k) {
         const bool sample = c->sample_every > 0 && ((t0 + k + 1) % c->sample_every == 0);
         for (const GroupHost &g : c->groups) {
@@ -503,18 +453,6 @@ void drop_graphs(lbm_ctx *c)
 {
     for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second.first);
     c->graphs.clear();
-}
-
-// Lattices per pass of each group (pass_mode > 0; 0 steps every group whole).
-// Measured on the 256-lattice 256^2 batch: passes that fit L2 (13-26
-// lattices) give launches too small to fill the GPU, and the batch runs at a
-// third of the step-by-step rate, so passes are off unless asked for.
-void choose_passes(lbm_ctx *c)
-{
-    for (GroupHost &g : c->groups) {
-        const int nm = (int)g.members.size();
-        g.pass = (c->pass_mode > 0 && nm > 1) ? std::min(c->pass_mode, nm) : 0;
-    }
 }
 
 lbm_status read_error_flag(lbm_ctx *c)
@@ -917,11 +855,7 @@ lbm_status lbm_get_state(lbm_ctx *c, int32_t lattice, float *dst, int32_t dst_is
     const char *src = c->state + L.state_off + (c->parity ? L.buf_bytes : 0);
     const size_t eb = elem_bytes(L.lat.storage);
     const long long cells = (long long)L.lat.nx * L.lat.ny;
-    if (L.lat.storage == LBM_F32 && L.pitch == (size_t)L.lat.nx) {  // dense rows: one linear copy
-        CK(cudaMemcpyAsync(dst, src, (size_t)L.q * cells * 4,
-                           dst_is_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c->stream),
-           "copy populations");
-    } else if (L.lat.storage == LBM_F32) {
+    if (L.lat.storage == LBM_F32) {
         CK(cudaMemcpy2DAsync(dst, L.lat.nx * 4, src, L.pitch * 4, L.lat.nx * 4, (size_t)L.q * L.lat.ny,
                              dst_is_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c->stream),
            "copy populations");
@@ -970,11 +904,7 @@ lbm_status lbm_set_state(lbm_ctx *c, int32_t lattice, const float *src, int32_t 
     char *dstp = c->state + L.state_off + (c->parity ? L.buf_bytes : 0);
     const size_t eb = elem_bytes(L.lat.storage);
     const long long cells = (long long)L.lat.nx * L.lat.ny;
-    if (L.lat.storage == LBM_F32 && L.pitch == (size_t)L.lat.nx) {  // dense rows: one linear copy
-        CK(cudaMemcpyAsync(dstp, src, (size_t)L.q * cells * 4,
-                           src_is_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, c->stream),
-           "copy populations");
-    } else if (L.lat.storage == LBM_F32) {
+    if (L.lat.storage == LBM_F32) {
         CK(cudaMemcpy2DAsync(dstp, L.pitch * 4, src, L.lat.nx * 4, L.lat.nx * 4, (size_t)L.q * L.lat.ny,
                              src_is_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, c->stream),
            "copy populations");
@@ -1197,24 +1127,6 @@ lbm_status lbm_get_tuning(const lbm_ctx *c, int32_t lattice, int32_t *vec, int32
     *rows = g.rows;
     *warps = g.warps;
     *stages = g.stages;
-    return LBM_OK;
-}
-
-lbm_status lbm_set_batch_passes(lbm_ctx *c, int32_t lattices_per_pass)
-{
-    if (!c) return LBM_ERR_INVALID_ARG;
-    if (lattices_per_pass < 0) return fail(c, LBM_ERR_INVALID_ARG, "lattices_per_pass must be >= 0");
-    c->pass_mode = lattices_per_pass;
-    drop_graphs(c);
-    choose_passes(c);
-    return LBM_OK;
-}
-
-lbm_status lbm_get_batch_passes(const lbm_ctx *c, int32_t lattice, int32_t *lattices_per_pass)
-{
-    if (!c || !lattices_per_pass || lattice < 0 || lattice >= (int32_t)c->lats.size()) return LBM_ERR_INVALID_ARG;
-    const GroupHost &g = c->groups[c->lats[lattice].group];
-    *lattices_per_pass = g.pass > 0 && g.pass < (int)g.members.size() ? g.pass : 0;
     return LBM_OK;
 }
 

@@ -108,9 +108,8 @@ inline float storage_shift(int storage, double w, float rho0)
 }
 
 struct StepArgs {
-    const LatDesc *desc;  // lattices of this launch (a group, or a contiguous part of one)
+    const LatDesc *desc;  // lattices of this launch group
     int nlat;
-    int block_base;       // block offset of desc[0] in its group (block_begin of desc[0])
     int src;              // index of the buffer holding the current state
     const uint32_t *t_ptr;
     uint32_t k;           // step offset of this launch from *t_ptr

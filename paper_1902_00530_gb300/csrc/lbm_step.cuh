@@ -634,9 +634,9 @@ __global__ void __launch_bounds__(256, direct_min_blocks<MODEL, ST, VEC, SAMPLE>
 {
     using T = typename Store<ST>::T;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const LatDesc *dp = a.desc + find_lattice(a.desc, a.nlat, (int)blockIdx.x + a.block_base);
+    const LatDesc *dp = a.desc + find_lattice(a.desc, a.nlat, blockIdx.x);
     const int nsx = dp->nsx, nsy = dp->nsy;
-    const int s = ((int)blockIdx.x + a.block_base - dp->block_begin) * (blockDim.x >> 5) + warp;
+    const int s = (blockIdx.x - dp->block_begin) * (blockDim.x >> 5) + warp;
     if (s >= nsx * nsy) return;  // whole warp leaves together
     const int nx = dp->nx, ny = dp->ny, pitch = dp->pitch, rows = dp->rows;
     const SiteParams d = load_params(dp);
@@ -754,9 +754,9 @@ __global__ void __launch_bounds__(256) observe_kernel(const StepArgs a)
 {
     using T = typename Store<ST>::T;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, warps = blockDim.x >> 5;
-    const LatDesc *dp = a.desc + find_lattice(a.desc, a.nlat, (int)blockIdx.x + a.block_base);
+    const LatDesc *dp = a.desc + find_lattice(a.desc, a.nlat, blockIdx.x);
     const int nsx = dp->nsx, nsy = dp->nsy;
-    const int bl = (int)blockIdx.x + a.block_base - dp->block_begin;
+    const int bl = blockIdx.x - dp->block_begin;
     int sx, sy;
     if (a.stages > 0) {  // a staged group's blocks hold `warps` adjacent strips of one strip row
         const int ncx = (nsx + warps - 1) / warps;

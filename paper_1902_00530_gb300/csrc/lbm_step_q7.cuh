@@ -315,9 +315,9 @@ __global__ void __launch_bounds__(256) step_kernel_q7(const StepArgs a)
 {
     using T = typename Store<ST>::T;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const LatDesc *dp = a.desc + find_lattice(a.desc, a.nlat, (int)blockIdx.x + a.block_base);
+    const LatDesc *dp = a.desc + find_lattice(a.desc, a.nlat, blockIdx.x);
     const int nsx = dp->nsx, nsy = dp->nsy;
-    const int s = ((int)blockIdx.x + a.block_base - dp->block_begin) * (blockDim.x >> 5) + warp;
+    const int s = (blockIdx.x - dp->block_begin) * (blockDim.x >> 5) + warp;
     if (s >= nsx * nsy) return;
     const int nx = dp->nx, ny = dp->ny, pitch = dp->pitch, rows = dp->rows;
     const SiteParams d = load_params(dp);
@@ -365,9 +365,9 @@ __global__ void __launch_bounds__(256) observe_kernel_q7(const StepArgs a)
 {
     using T = typename Store<ST>::T;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const LatDesc *dp = a.desc + find_lattice(a.desc, a.nlat, (int)blockIdx.x + a.block_base);
+    const LatDesc *dp = a.desc + find_lattice(a.desc, a.nlat, blockIdx.x);
     const int nsx = dp->nsx, nsy = dp->nsy;
-    const int s = ((int)blockIdx.x + a.block_base - dp->block_begin) * (blockDim.x >> 5) + warp;
+    const int s = (blockIdx.x - dp->block_begin) * (blockDim.x >> 5) + warp;
     if (s >= nsx * nsy) return;
     const int nx = dp->nx, ny = dp->ny, pitch = dp->pitch, rows = dp->rows;
     const Shift3 sh = load_shift(dp);

@@ -149,9 +149,9 @@ __global__ void __launch_bounds__(128, staged7_min_blocks<VEC>()) step_staged_ke
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw + (size_t)(blockDim.x >> 5) * S * G::STAGE_BYTES) +
                      warp * S;
 
-    const LatDesc *dp = a.desc + find_lattice(a.desc, a.nlat, (int)blockIdx.x + a.block_base);
+    const LatDesc *dp = a.desc + find_lattice(a.desc, a.nlat, blockIdx.x);
     const int nsx = dp->nsx, nsy = dp->nsy;
-    const int s = ((int)blockIdx.x + a.block_base - dp->block_begin) * (blockDim.x >> 5) + warp;
+    const int s = (blockIdx.x - dp->block_begin) * (blockDim.x >> 5) + warp;
     if (s >= nsx * nsy) return;
     const int nx = dp->nx, ny = dp->ny, pitch = dp->pitch, rows = dp->rows;
     const SiteParams d = load_params(dp);

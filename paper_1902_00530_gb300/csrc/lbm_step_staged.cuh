@@ -252,9 +252,9 @@ struct StagedBlock {
 __device__ __forceinline__ StagedBlock staged_block(const StepArgs &a, int warps)
 {
     StagedBlock g;
-    g.dp = a.desc + find_lattice(a.desc, a.nlat, (int)blockIdx.x + a.block_base);
+    g.dp = a.desc + find_lattice(a.desc, a.nlat, blockIdx.x);
     const int ncx = (g.dp->nsx + warps - 1) / warps;
-    const int bl = (int)blockIdx.x + a.block_base - g.dp->block_begin;
+    const int bl = blockIdx.x - g.dp->block_begin;
     g.sx0 = (bl % ncx) * warps;
     g.sy = bl / ncx;
     g.nact = min(warps, g.dp->nsx - g.sx0);

@@ -110,27 +110,6 @@ def test_staged_block_width_limits(lib):
         lib.lbm_destroy(ctx)
 
 
-def test_batch_passes_calls(lib):
-    from paper_1902_00530_gb300 import _abi
-    n = 4
-    lats = (_abi.lbm_lattice * n)(*[_abi.lbm_lattice(64, 32, 0, k) for k in range(n)])
-    mods = (ctypes.c_int * n)(2, 2, 2, 2)
-    prms = (_abi.lbm_params * n)(*[_prm(tau=1.0) for _ in range(n)])
-    ctx = ctypes.c_void_p()
-    assert lib.lbm_create_batch(n, lats, mods, prms, ctypes.byref(ctx)) == 0
-    per = ctypes.c_int32(-5)
-    assert lib.lbm_get_batch_passes(ctx, 0, ctypes.byref(per)) == 0 and per.value == 0  # default: whole
-    assert lib.lbm_set_batch_passes(ctx, -1) == 1
-    assert lib.lbm_set_batch_passes(ctx, 3) == 0
-    assert lib.lbm_get_batch_passes(ctx, 2, ctypes.byref(per)) == 0 and per.value == 3
-    assert lib.lbm_set_batch_passes(ctx, 9) == 0       # more than the group: one pass, i.e. not split
-    assert lib.lbm_get_batch_passes(ctx, 0, ctypes.byref(per)) == 0 and per.value == 0
-    assert lib.lbm_set_batch_passes(ctx, 0) == 0
-    assert lib.lbm_get_batch_passes(ctx, 1, ctypes.byref(per)) == 0 and per.value == 0
-    assert lib.lbm_get_batch_passes(ctx, 4, ctypes.byref(per)) == 1
-    lib.lbm_destroy(ctx)
-
-
 def test_batch_create_groups(lib):
     from paper_1902_00530_gb300 import _abi
     n = 4

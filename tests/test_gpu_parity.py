@@ -206,31 +206,6 @@ def test_staged_kernel_small_and_ragged(nx, ny):
             assert_parity(got, model, d, nx, ny, steps, SEED, spec)
 
 
-def test_batch_passes_give_identical_states_and_series():
-    """A batch stepped in passes of lattices (each pass takes a whole chunk of
-    steps before the next) equals the step-by-step order bit for bit, states
-    and sampled observables alike, across chunk and sample boundaries."""
-    from paper_1902_00530_gb300 import Lattice, Simulation
-    model, d = split_preset("CIL_RHO1")
-    lats = [Lattice(96 + 16 * (k % 3), 40, "f32", k) for k in range(8)]
-    runs = []
-    for per in (0, 3, 1):
-        sim = Simulation(lats, [model] * 8, [dict(d, B=0.3 - 0.01 * k) for k in range(8)], sample_every=5,
-                         ring_capacity=64)
-        sim.set_batch_passes(per)
-        assert sim.batch_passes(0) == per
-        sim.init(SEED, [W.INIT_CONFIG2] * 8)
-        sim.step(23)
-        sim.step(300)  # beyond one graph chunk (256 steps)
-        runs.append(([sim.get_state(k, host=True).numpy().copy() for k in range(8)],
-                     [sim.observable_series(k) for k in range(8)]))
-        sim.close()
-    for states, series in runs[1:]:
-        for k in range(8):
-            np.testing.assert_array_equal(states[k], runs[0][0][k])
-            assert series[k] == runs[0][1][k]
-
-
 # ---------------------------------------------------------- noise stream ---
 def _write_state_file(path, f, t, seed, lattice_id, model, storage=0, rho0=1.0):
     """A state file as lbm_save writes it (one lattice): magic, (count, t,
