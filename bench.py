@@ -320,6 +320,21 @@ def secondary_lines(args, wl):
         sim.close()
         del sim
         torch.cuda.empty_cache()
+    # the CIL closure at the same size, where FP32 storage runs at the copy
+    # bandwidth: the case 16-bit storage is for
+    if wl.get("velocity_set", "d2q9") == "d2q9" and wl["nx"] == 8192:
+        wc = workload_spec("cil8192")
+        peak, _ = measured_peak()
+        for st in ("f32", "f16s", "bf16s"):
+            sim = Simulation([Lattice(wc["nx"], wc["ny"], st)], [wc["model"]], [wc["params"]],
+                             sample_every=wc["sample_every"], ring_capacity=16)
+            sim.init(wc["seed"], [wc["init"]])
+            g = time_sim(sim, wc["nx"] * wc["ny"], steps)
+            out[f"cil8192_{st}_glups"] = round(g, 2)
+            out[f"cil8192_{st}_frac_hbm"] = round(g * bytes_per_update(st) / peak, 4)
+            sim.close()
+            del sim
+            torch.cuda.empty_cache()
     # uniform batch: 256 CIL lattices of 256^2, rho-bar x activity (B) grid
     c4 = W.CONFIG4
     d = W.preset(c4["preset"])
