@@ -218,7 +218,7 @@ lbm_status lbm_load(lbm_ctx *ctx, const char *path);
 /* Launch-shape tuning.  mode 0: automatic on the first lbm_step (default);
  * mode 1: off, use the fixed shape given for every lattice: vec = sites per
  * thread along x (1, 2 or 4 for FP32; 1, 2, 4 or 8 for 16-bit storage; must
- * divide nx), rows = rows per warp strip (16..4096), warps = warps per block
+ * divide nx), rows = rows per warp strip (8..4096), warps = warps per block
  * (1..8), stages = 0 for the kernel that loads populations straight from
  * global memory, or 2..8 (MIPS: 3..8) for the kernel that stages population
  * rows in shared memory with bulk copies, that many rows in flight (D2Q9: per

@@ -24,7 +24,7 @@ using namespace lbm;
 
 namespace {
 
-constexpr int ROWS_MIN = 16;       // smallest strip height; scratch is sized for it
+constexpr int ROWS_MIN = 8;        // smallest strip height; scratch is sized for it
 constexpr int CHUNK_COLS = 256;    // columns / rows / strips per finaliser block
 constexpr int NCHUNK_MAX = 1024;
 constexpr int GRAPH_CHUNK_MAX = 256;
@@ -496,7 +496,7 @@ lbm_status tune_group(lbm_ctx *c, GroupHost &g)
         bool ok = true;
         for (int m : g.members) ok = ok && (c->lats[m].lat.nx % v == 0);
         if (!ok) continue;
-        for (int r : {16, 32, 64, 128}) {
+        for (int r : {8, 16, 32, 64, 128}) {
             if (r > 16 && r > 2 * max_ny) continue;
             if (direct)
                 for (int w : {4, 8}) cands.push_back({v, r, w, 0});
@@ -1073,7 +1073,7 @@ lbm_status lbm_set_tuning(lbm_ctx *c, int32_t mode, int32_t vec, int32_t rows, i
         return LBM_OK;
     }
     if (mode != 1) return fail(c, LBM_ERR_INVALID_ARG, "mode must be 0 or 1");
-    if (rows < ROWS_MIN || rows > 4096) return fail(c, LBM_ERR_INVALID_ARG, "rows must be in [16, 4096]");
+    if (rows < ROWS_MIN || rows > 4096) return fail(c, LBM_ERR_INVALID_ARG, "rows must be in [8, 4096]");
     if (warps < 1 || warps > 8) return fail(c, LBM_ERR_INVALID_ARG, "warps must be in [1, 8]");
     if (stages != 0 && (stages < 2 || stages > 8))
         return fail(c, LBM_ERR_INVALID_ARG, "stages must be 0 (direct) or 2..8");

@@ -79,7 +79,7 @@ def test_host_only_calls_and_status_codes(lib):
     assert b"bound" in lib.lbm_last_error(ctx)
     assert lib.lbm_observables(ctx, 0, None) == 2
     assert lib.lbm_set_tuning(ctx, 1, 4, 32, 4, 0) == 1   # 4 does not divide 37
-    assert lib.lbm_set_tuning(ctx, 1, 1, 8, 4, 0) == 1    # rows below 16
+    assert lib.lbm_set_tuning(ctx, 1, 1, 4, 4, 0) == 1    # rows below 8
     assert lib.lbm_set_tuning(ctx, 1, 1, 32, 9, 0) == 1   # too many warps
     assert lib.lbm_set_tuning(ctx, 1, 1, 32, 2, 3) == 1   # staged needs nx % 4 == 0 (37)
     assert lib.lbm_set_tuning(ctx, 1, 1, 32, 2, 0) == 0
