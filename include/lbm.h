@@ -255,6 +255,14 @@ lbm_status lbm_last_launch_count(const lbm_ctx *ctx, int64_t *count);
 lbm_status lbm_set_profiling(lbm_ctx *ctx, int32_t enabled);
 lbm_status lbm_profile_read(lbm_ctx *ctx, double *step_ms, int64_t *step_launches, double *other_ms);
 
+/* Check of the device-side failure path (the bounded waits of the staged
+ * kernels, App. A.2's step being the work they wait for): runs one warp that
+ * waits on a barrier phase nothing completes.  The wait gives up after its
+ * limit (about 1 s) and raises the device error flag, which this call reads and
+ * clears, so it returns LBM_ERR_TIMEOUT; the context stays usable.  Syncs the
+ * bound stream.  LBM_ERR_UNBOUND before lbm_bind. */
+lbm_status lbm_check_wait_timeout(lbm_ctx *ctx);
+
 /* Observables of a population field, allocating nothing.
  *
  * The paper has no counterpart: this is a service for callers that cannot

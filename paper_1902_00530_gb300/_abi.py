@@ -71,6 +71,7 @@ SIGNATURES = {
     "lbm_set_profiling": (ctypes.c_int, [_CTX, ctypes.c_int32]),
     "lbm_profile_read": (ctypes.c_int, [_CTX, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
                                         ctypes.POINTER(ctypes.c_double)]),
+    "lbm_check_wait_timeout": (ctypes.c_int, [_CTX]),
     "lbm_observables_noalloc": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                                ctypes.POINTER(lbm_obs), _P]),
     "lbm_last_error": (ctypes.c_char_p, [_CTX]),

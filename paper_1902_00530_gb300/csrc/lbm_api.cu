@@ -1130,6 +1130,14 @@ lbm_status lbm_get_tuning(const lbm_ctx *c, int32_t lattice, int32_t *vec, int32
     return LBM_OK;
 }
 
+lbm_status lbm_check_wait_timeout(lbm_ctx *c)
+{
+    lbm_status st = require_ready(c, false);
+    if (st != LBM_OK) return st;
+    CK(launch_wait_timeout(err_dev(c), c->stream), "launch wait check");
+    return read_error_flag(c);
+}
+
 lbm_status lbm_set_graphs(lbm_ctx *c, int32_t enabled)
 {
     if (!c) return LBM_ERR_INVALID_ARG;

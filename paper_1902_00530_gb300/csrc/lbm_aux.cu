@@ -1,6 +1,7 @@
 // lbm_aux.cu -- initialisation, moment output, state exchange and the
 // observable finaliser.  Small kernels around the fused step.
 #include "lbm_internal.h"
+#include "lbm_step_staged.cuh"  // the bounded barrier wait of the staged kernels
 
 namespace lbm {
 
@@ -283,6 +284,21 @@ __global__ void advance_time_kernel(uint32_t *t_ptr, uint32_t n) { *t_ptr += n; 
 
 __global__ void set_time_kernel(uint32_t *t_ptr, uint32_t t) { *t_ptr = t; }
 
+// The failure path of the staged kernels' waits, exercised on purpose: one
+// warp waits, with the same bounded wait, on a barrier phase that nothing
+// completes; the wait gives up after its limit (about 1 s) and the warp raises
+// the timeout flag, as a step kernel does when a staged row never arrives.
+__global__ void wait_timeout_kernel(unsigned *err)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_init_fence();
+    }
+    __syncwarp();
+    if (!stage_wait(&bar, 0u) && threadIdx.x == 0) atomicOr(err, (unsigned)DEVERR_TIMEOUT);
+}
+
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
@@ -374,6 +390,12 @@ cudaError_t launch_finalize(const LatDesc *desc, int nlat, int max_chunk, const 
 cudaError_t launch_advance_time(uint32_t *t_ptr, uint32_t n, cudaStream_t s)
 {
     advance_time_kernel<<<1, 1, 0, s>>>(t_ptr, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wait_timeout(unsigned *err, cudaStream_t s)
+{
+    wait_timeout_kernel<<<1, 32, 0, s>>>(err);
     return cudaGetLastError();
 }
 

@@ -49,5 +49,6 @@ cudaError_t launch_advance_time(uint32_t *t_ptr, uint32_t n, cudaStream_t s);
 cudaError_t launch_add_density(int storage, const LatDesc *desc, int lat, long long cells, int buf, float per_pop,
                                cudaStream_t s);
 cudaError_t launch_set_time(uint32_t *t_ptr, uint32_t t, cudaStream_t s);
+cudaError_t launch_wait_timeout(unsigned *err, cudaStream_t s);
 
 }  // namespace lbm

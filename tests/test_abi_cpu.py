@@ -90,6 +90,7 @@ def test_host_only_calls_and_status_codes(lib):
     assert lib.lbm_get_tuning(ctx, 1, *args) == 1
     t = ctypes.c_int64(-1)
     assert lib.lbm_get_time(ctx, ctypes.byref(t)) == 0 and t.value == 0
+    assert lib.lbm_check_wait_timeout(ctx) == 2            # the failure-path check needs bound buffers
     assert lib.lbm_bind(ctx, None, None, None) == 1
     assert lib.lbm_bind(ctx, ctypes.c_void_p(0x1001), ctypes.c_void_p(0x2000), None) == 1  # misaligned
     lib.lbm_destroy(ctx)
