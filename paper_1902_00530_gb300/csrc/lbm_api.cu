@@ -314,9 +314,9 @@ lbm_status upload_descs(lbm_ctx *c)
             L.nsy = d.nsy;
             L.nchunk = d.nchunk;
             L.block_begin = blocks;
-            // the D2Q9 staged kernel gives a block `warps` adjacent strips of one
-            // strip row; the other kernels take `warps` consecutive strips
-            if (g.stages > 0 && g.q == 9)
+            // a staged kernel gives a block `warps` adjacent strips of one strip
+            // row; the direct kernels take `warps` consecutive strips
+            if (g.stages > 0)
                 blocks += ceil_div(d.nsx, g.warps) * d.nsy;
             else
                 blocks += ceil_div((long long)d.nsx * d.nsy, g.warps);
@@ -503,10 +503,8 @@ lbm_status tune_group(lbm_ctx *c, GroupHost &g)
             if (staged && v >= 2) {
                 // MIPS also tries 3, the least its ring needs (less shared memory, more warps)
                 const int sts[3] = {base_stages, base_stages + 2, 3};
-                for (int w : {1, 2, 4, 8}) {
-                    if (w > 4 && g.q == 7) continue;  // the D2Q7 staged kernel: per-warp rings, up to 4 warps
+                for (int w : {1, 2, 4, 8})
                     for (int k = 0; k < (base_stages > 3 ? 3 : 2); ++k) cands.push_back({v, r, w, sts[k]});
-                }
             }
         }
     }
@@ -1077,9 +1075,6 @@ lbm_status lbm_set_tuning(lbm_ctx *c, int32_t mode, int32_t vec, int32_t rows, i
     if (warps < 1 || warps > 8) return fail(c, LBM_ERR_INVALID_ARG, "warps must be in [1, 8]");
     if (stages != 0 && (stages < 2 || stages > 8))
         return fail(c, LBM_ERR_INVALID_ARG, "stages must be 0 (direct) or 2..8");
-    if (stages != 0 && warps > 4)
-        for (auto &g : c->groups)
-            if (g.q == 7) return fail(c, LBM_ERR_INVALID_ARG, "the D2Q7 staged kernel takes at most 4 warps");
     if (stages != 0)
         for (auto &g : c->groups)
             if (g.model == LBM_MIPS && stages < 3) return fail(c, LBM_ERR_INVALID_ARG, "MIPS needs at least 3 stages");

@@ -364,14 +364,25 @@ template <int ST, int VEC>
 __global__ void __launch_bounds__(256) observe_kernel_q7(const StepArgs a)
 {
     using T = typename Store<ST>::T;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, warps = blockDim.x >> 5;
     const LatDesc *dp = a.desc + find_lattice(a.desc, a.nlat, blockIdx.x);
     const int nsx = dp->nsx, nsy = dp->nsy;
-    const int s = (blockIdx.x - dp->block_begin) * (blockDim.x >> 5) + warp;
-    if (s >= nsx * nsy) return;
+    const int bl = blockIdx.x - dp->block_begin;
+    int sx, sy;
+    if (a.stages > 0) {  // a staged group's blocks hold `warps` adjacent strips of one strip row
+        const int ncx = (nsx + warps - 1) / warps;
+        sx = (bl % ncx) * warps + warp;
+        sy = bl / ncx;
+        if (sx >= nsx) return;
+    } else {
+        const int s0 = bl * warps + warp;
+        if (s0 >= nsx * nsy) return;
+        sx = s0 % nsx;
+        sy = s0 / nsx;
+    }
+    const int s = sy * nsx + sx;
     const int nx = dp->nx, ny = dp->ny, pitch = dp->pitch, rows = dp->rows;
     const Shift3 sh = load_shift(dp);
-    const int sx = s % nsx, sy = s / nsx;
     const int x0 = sx * 32 * VEC + lane * VEC;
     const bool valid = x0 < nx;
     const int y_begin = sy * rows, y_end = min(y_begin + rows, ny);

@@ -1,16 +1,18 @@
 // lbm_step_q7_staged.cuh -- the D2Q7 step with bulk-copied population rows.
 //
 // The data movement of step_staged_kernel (lbm_step_staged.cuh) applied to the
-// paper's triangular lattice: each warp owns a ring of `stages` shared-memory
-// buffers; buffer q holds, for destination row r(q), the seven source-row
-// segments it pulls from (row r + q7_src_dy(i) of population i), each covering
-// the warp's 32*VEC columns plus 16 bytes of periodic halo on both sides, and
-// arrives by cp.async.bulk copies completing on the buffer's mbarrier, issued
-// rows ahead of use.  The half-site column offsets of the brick layout (-1/0
-// from an even row, 0/+1 from an odd one) become shared-memory index offsets;
-// rows are walked in (even, odd) pairs so the parity is a template argument.
-// The per-site arithmetic is collide7 / negative_correction7 / noise_u7 of
-// lbm_step_q7.cuh, so states are bitwise those of step_kernel_q7.
+// paper's triangular lattice: a block of W warps owns W adjacent warp strips
+// of one strip row and a ring of `stages` shared-memory buffers; buffer q
+// holds, for destination row r(q), the seven source-row segments it pulls from
+// (row r + q7_src_dy(i) of population i), each covering the block's columns
+// plus 16 bytes of periodic halo on both sides, and arrives by cp.async.bulk
+// copies completing on the buffer's "full" mbarrier, issued by warp 0 rows
+// ahead of use once every warp has released the buffer ("empty" mbarrier).
+// The half-site column offsets of the brick layout (-1/0 from an even row, 0/+1
+// from an odd one) become shared-memory index offsets; rows are walked in
+// (even, odd) pairs so the parity is a template argument.  The per-site
+// arithmetic is collide7 / negative_correction7 / noise_u7 of lbm_step_q7.cuh,
+// so states are bitwise those of step_kernel_q7.
 //
 // Requirements (checked on the host): nx a multiple of the 16-byte halo width
 // and at least that wide; rows even.  Every wait is bounded as in the D2Q9
@@ -28,21 +30,23 @@ template <int ST, int VEC> struct StageGeom7 {
     using T = typename Store<ST>::T;
     static constexpr int HALO = 16 / (int)sizeof(T);
     static constexpr int W = 32 * VEC;
-    static constexpr int SEG = W + 2 * HALO;
-    static constexpr int STAGE_BYTES = 7 * SEG * (int)sizeof(T);
+    // elements per population segment of a block of `warps` warps (16-byte multiple)
+    __host__ __device__ static constexpr int seg(int warps) { return warps * W + 2 * HALO; }
+    __host__ __device__ static constexpr int stage_bytes(int warps) { return 7 * seg(warps) * (int)sizeof(T); }
 };
 
-// Issue the segment copies of destination row y and arm the barrier: one copy
-// per population (lanes 0..6) for a strip whose halos lie inside the row,
-// else three (lanes 0..20: left halo, strip, right halo), as in issue_row.
+// Issue the segment copies of destination row y into buffer `buf` (seg
+// elements per population) and arm its barrier, for the block's columns xs ..
+// xe-1: one copy per population (lanes 0..6) where the halos lie inside the
+// row, else three (lanes 0..20: left halo, columns, right halo), as issue_row.
 template <int ST, int VEC>
-__device__ __forceinline__ void issue_row7(typename Store<ST>::T *buf, uint64_t *bar, const typename Store<ST>::T *src,
-                                           size_t plane, int pitch, int nx, int ny, int xs, int xe, int y, int lane)
+__device__ __forceinline__ void issue_row7(typename Store<ST>::T *buf, int seg_elems, uint64_t *bar,
+                                           const typename Store<ST>::T *src, size_t plane, int pitch, int nx, int ny,
+                                           int xs, int xe, int y, int lane)
 {
     using G = StageGeom7<ST, VEC>;
     using T = typename Store<ST>::T;
     const uint32_t main_bytes = (uint32_t)(xe - xs) * (uint32_t)sizeof(T);
-    __syncwarp();  // every lane has finished reading this buffer's previous row
     if (lane == 0) mbar_arrive_expect_tx(bar, 7u * (main_bytes + 32u));
     __syncwarp();
     if (xs >= G::HALO && xe + G::HALO <= nx) {
@@ -51,14 +55,14 @@ __device__ __forceinline__ void issue_row7(typename Store<ST>::T *buf, uint64_t 
             const int i = lane;
             const int r = wrap_once(y + ((i == 2 || i == 3) ? -1 : ((i == 5 || i == 6) ? 1 : 0)), ny);
             const T *row = src + (size_t)i * plane + (size_t)r * pitch;
-            bulk_copy_g2s(buf + i * G::SEG, row + (xs - G::HALO), main_bytes + 32u, bar);
+            bulk_copy_g2s(buf + i * seg_elems, row + (xs - G::HALO), main_bytes + 32u, bar);
         }
     } else if (lane < 21) {
         fence_proxy_async_smem();
         const int i = lane / 3, part = lane % 3;
         const int r = wrap_once(y + ((i == 2 || i == 3) ? -1 : ((i == 5 || i == 6) ? 1 : 0)), ny);
         const T *row = src + (size_t)i * plane + (size_t)r * pitch;
-        T *seg = buf + i * G::SEG;
+        T *seg = buf + i * seg_elems;
         if (part == 0) {
             const int c = xs == 0 ? nx - G::HALO : xs - G::HALO;
             bulk_copy_g2s(seg, row + c, 16u, bar);
@@ -94,72 +98,75 @@ __device__ __forceinline__ void stage_pop7(const typename Store<ST>::T *seg, int
 }
 
 template <int ST, int VEC, int P>
-__device__ __forceinline__ void stage_row7(const typename Store<ST>::T *buf, int b, const Shift3 &sh, float f[7][VEC])
+__device__ __forceinline__ void stage_row7(const typename Store<ST>::T *buf, int sg, int b, const Shift3 &sh,
+                                           float f[7][VEC])
 {
-    using G = StageGeom7<ST, VEC>;
-    stage_pop7<ST, VEC, 0, P>(buf + 0 * G::SEG, b, sh.q7(0), f[0]);
-    stage_pop7<ST, VEC, 1, P>(buf + 1 * G::SEG, b, sh.q7(1), f[1]);
-    stage_pop7<ST, VEC, 2, P>(buf + 2 * G::SEG, b, sh.q7(2), f[2]);
-    stage_pop7<ST, VEC, 3, P>(buf + 3 * G::SEG, b, sh.q7(3), f[3]);
-    stage_pop7<ST, VEC, 4, P>(buf + 4 * G::SEG, b, sh.q7(4), f[4]);
-    stage_pop7<ST, VEC, 5, P>(buf + 5 * G::SEG, b, sh.q7(5), f[5]);
-    stage_pop7<ST, VEC, 6, P>(buf + 6 * G::SEG, b, sh.q7(6), f[6]);
+    stage_pop7<ST, VEC, 0, P>(buf + 0 * sg, b, sh.q7(0), f[0]);
+    stage_pop7<ST, VEC, 1, P>(buf + 1 * sg, b, sh.q7(1), f[1]);
+    stage_pop7<ST, VEC, 2, P>(buf + 2 * sg, b, sh.q7(2), f[2]);
+    stage_pop7<ST, VEC, 3, P>(buf + 3 * sg, b, sh.q7(3), f[3]);
+    stage_pop7<ST, VEC, 4, P>(buf + 4 * sg, b, sh.q7(4), f[4]);
+    stage_pop7<ST, VEC, 5, P>(buf + 5 * sg, b, sh.q7(5), f[5]);
+    stage_pop7<ST, VEC, 6, P>(buf + 6 * sg, b, sh.q7(6), f[6]);
 }
 
 // Post-stream density at shared index c of a staged row of parity P.
 template <int ST, int VEC, int P>
-__device__ __forceinline__ float stage_density_at7(const typename Store<ST>::T *buf, int c, const Shift3 &sh)
+__device__ __forceinline__ float stage_density_at7(const typename Store<ST>::T *buf, int sg, int c, const Shift3 &sh)
 {
-    using G = StageGeom7<ST, VEC>;
     float v[7];
 #pragma unroll
-    for (int i = 0; i < 7; ++i) v[i] = Store<ST>::get(buf[i * G::SEG + c + q7_src_dx(i, P)], sh.q7(i));
+    for (int i = 0; i < 7; ++i) v[i] = Store<ST>::get(buf[i * sg + c + q7_src_dx(i, P)], sh.q7(i));
     return density7(v);
 }
 
+// Density window of a staged row (r[0] at x0-1, r[1..VEC] the lane's sites,
+// r[VEC+1] at x0+VEC): neighbours by shuffle, the two sites outside the warp's
+// columns summed from shared memory in one pass (lane 0 the left one, every
+// other lane the right one, which lane 31 keeps).
 template <int ST, int VEC, int P>
-__device__ __forceinline__ void stage_density_window7(const typename Store<ST>::T *buf, int b, const Shift3 &sh, int lane,
-                                                      float r[VEC + 2])
+__device__ __forceinline__ void stage_density_window7(const typename Store<ST>::T *buf, int sg, int b,
+                                                      const Shift3 &sh, int lane, float r[VEC + 2])
 {
     float f[7][VEC];
-    stage_row7<ST, VEC, P>(buf, b, sh, f);
+    stage_row7<ST, VEC, P>(buf, sg, b, sh, f);
 #pragma unroll
     for (int j = 0; j < VEC; ++j) r[j + 1] = density7_at<VEC>(f, j);
-    const float right = stage_density_at7<ST, VEC, P>(buf, b + VEC, sh);
+    const float edge = stage_density_at7<ST, VEC, P>(buf, sg, lane == 0 ? b - 1 : b + VEC, sh);
     float left = __shfl_up_sync(FULL, r[VEC], 1);
-    if (lane == 0) left = stage_density_at7<ST, VEC, P>(buf, b - 1, sh);
+    float right = __shfl_down_sync(FULL, r[1], 1);
+    if (lane == 0) left = edge;
+    if (lane == 31) right = edge;
     r[0] = left;
     r[VEC + 1] = right;
 }
 
-template <int VEC> constexpr int staged7_min_blocks()
-{
-    return VEC == 1 ? 6 : (VEC == 2 ? 5 : 4);
-}
-
 template <int MODEL, int ST, int VEC, bool SAMPLE, int NOISE>
-__global__ void __launch_bounds__(128, staged7_min_blocks<VEC>()) step_staged_kernel_q7(const StepArgs a)
+__global__ void __maxnreg__(staged_max_regs<VEC>()) step_staged_kernel_q7(const StepArgs a)
 {
     using T = typename Store<ST>::T;
     using G = StageGeom7<ST, VEC>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, warps = blockDim.x >> 5;
     const int S = a.stages;
-    T *ring = reinterpret_cast<T *>(smem_raw + (size_t)warp * S * G::STAGE_BYTES);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw + (size_t)(blockDim.x >> 5) * S * G::STAGE_BYTES) +
-                     warp * S;
+    const int sg = G::seg(warps);
+    const int stage_elems = 7 * sg;
+    // carve-out: S stage buffers, then S "full" and S "empty" barriers
+    T *ring = reinterpret_cast<T *>(smem_raw);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + (size_t)S * stage_elems * sizeof(T));
+    uint64_t *empty = full + S;
 
-    const LatDesc *dp = a.desc + find_lattice(a.desc, a.nlat, blockIdx.x);
-    const int nsx = dp->nsx, nsy = dp->nsy;
-    const int s = (blockIdx.x - dp->block_begin) * (blockDim.x >> 5) + warp;
-    if (s >= nsx * nsy) return;
+    const StagedBlock blk = staged_block(a, warps);
+    const LatDesc *dp = blk.dp;
+    const int nsx = dp->nsx;
     const int nx = dp->nx, ny = dp->ny, pitch = dp->pitch, rows = dp->rows;
     const SiteParams d = load_params(dp);
-    const int sx = s % nsx, sy = s / nsx;
-    const int xs = sx * G::W, xe = min(xs + G::W, nx);
-    const int x0 = xs + lane * VEC;
+    const int sx = blk.sx0 + warp, sy = blk.sy;
+    const int s = sy * nsx + sx;
+    const int xs = blk.sx0 * G::W, xe = min(xs + blk.nact * G::W, nx);  // the block's columns
+    const int x0 = sx * G::W + lane * VEC;
     const bool valid = x0 < nx;
-    const int b = G::HALO + lane * VEC;
+    const int b = G::HALO + warp * G::W + lane * VEC;
     const int y_begin = sy * rows, y_end = min(y_begin + rows, ny);  // even, even
     const size_t plane = (size_t)ny * pitch;
     const T *src = reinterpret_cast<const T *>(dp->f[a.src]);
@@ -168,34 +175,53 @@ __global__ void __launch_bounds__(128, staged7_min_blocks<VEC>()) step_staged_ke
     const uint32_t id = (uint32_t)dp->id;
     const uint32_t t = *a.t_ptr + a.k;
     const bool noise = NOISE == 2 ? d.sigma_q > 0.f : NOISE == 1;
+    const bool leader = warp == 0;
 
-    if (lane == 0) {
-        for (int k = 0; k < S; ++k) mbar_init(&bars[k], 1);
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < S; ++k) {
+            mbar_init(&full[k], 1);
+            mbar_init(&empty[k], (uint32_t)blk.nact);
+        }
         mbar_init_fence();
     }
-    __syncwarp();
+    __syncthreads();
+    if (warp >= blk.nact) return;  // a strip past the lattice's last column
 
     constexpr bool MIPS = (MODEL == MODEL_MIPS);
     const int q_first_row = MIPS ? y_begin - 1 : y_begin;
     const int nq = (y_end - y_begin) + (MIPS ? 2 : 0);
-    int issued = 0;
-    auto issue_next = [&]() {
-        if (issued < nq) {
-            const int k = issued % S;
-            issue_row7<ST, VEC>(ring + (size_t)k * (G::STAGE_BYTES / sizeof(T)), &bars[k], src, plane, pitch, nx, ny,
-                                xs, xe, wrap_once(q_first_row + issued, ny), lane);
-            ++issued;
+    auto stage_ptr = [&](int q) { return ring + (size_t)(q % S) * stage_elems; };
+    bool ok = true;
+    auto fail = [&]() {
+        ok = false;
+        if (lane == 0) atomicOr(a.err, (unsigned)DEVERR_TIMEOUT);
+    };
+    int issued = 0;  // rows issued (warp 0)
+    auto issue = [&]() {
+        const int k = issued % S;
+        issue_row7<ST, VEC>(ring + (size_t)k * stage_elems, sg, &full[k], src, plane, pitch, nx, ny, xs, xe,
+                            wrap_once(q_first_row + issued, ny), lane);
+        ++issued;
+    };
+    if (leader)
+        while (issued < S && issued < nq) issue();
+
+    // Row q is consumed by this warp; warp 0 refills its buffer with row q + S
+    // once every warp has (a single warp needs no barrier for that).
+    auto release = [&](int q) {
+        __syncwarp();
+        if (blk.nact == 1) {
+            if (ok && issued < nq) issue();
+            return;
+        }
+        if (lane == 0) mbar_arrive(&empty[q % S]);
+        if (leader && ok && issued < nq) {
+            if (!stage_wait(&empty[q % S], (uint32_t)((q / S) & 1))) fail();
+            else issue();
         }
     };
-    for (int k = 0; k < S; ++k) issue_next();
-
-    auto stage_ptr = [&](int q) { return ring + (size_t)(q % S) * (G::STAGE_BYTES / sizeof(T)); };
-    bool ok = true;
     auto wait_q = [&](int q) {
-        if (ok && !stage_wait(&bars[q % S], (uint32_t)((q / S) & 1))) {
-            ok = false;
-            if (lane == 0) atomicOr(a.err, (unsigned)DEVERR_TIMEOUT);
-        }
+        if (ok && !stage_wait(&full[q % S], (uint32_t)((q / S) & 1))) fail();
         return ok;
     };
 
@@ -211,10 +237,12 @@ __global__ void __launch_bounds__(128, staged7_min_blocks<VEC>()) step_staged_ke
     float rm[VEC + 2], rc[VEC + 2], rn[VEC + 2];
     int q = 0;
     if constexpr (MIPS) {
-        if (wait_q(0)) stage_density_window7<ST, VEC, 1>(stage_ptr(0), b, sh, lane, rm);  // row y_begin-1: odd
-        issue_next();
+        if (wait_q(0)) {
+            stage_density_window7<ST, VEC, 1>(stage_ptr(0), sg, b, sh, lane, rm);  // row y_begin-1: odd
+            release(0);
+        }
         q = 1;
-        if (wait_q(1)) stage_density_window7<ST, VEC, 0>(stage_ptr(1), b, sh, lane, rc);
+        if (wait_q(1)) stage_density_window7<ST, VEC, 0>(stage_ptr(1), sg, b, sh, lane, rc);
     }
 
     // one row of parity P; returns false if a wait gave up
@@ -224,12 +252,12 @@ __global__ void __launch_bounds__(128, staged7_min_blocks<VEC>()) step_staged_ke
         float f[7][VEC];
         if constexpr (MIPS) {
             if (!wait_q(qc + 1)) return false;
-            stage_density_window7<ST, VEC, 1 - P>(stage_ptr(qc + 1), b, sh, lane, rn);
+            stage_density_window7<ST, VEC, 1 - P>(stage_ptr(qc + 1), sg, b, sh, lane, rn);
         } else {
             if (!wait_q(qc)) return false;
         }
-        stage_row7<ST, VEC, P>(stage_ptr(qc), b, sh, f);
-        issue_next();
+        stage_row7<ST, VEC, P>(stage_ptr(qc), sg, b, sh, f);
+        release(qc);
         q = qc + 1;
         float gx[VEC], gy[VEC];
         if constexpr (MIPS) {
@@ -278,18 +306,20 @@ __global__ void __launch_bounds__(128, staged7_min_blocks<VEC>()) step_staged_ke
         if (!do_row(std::integral_constant<int, 0>{}, y)) break;
         if (!do_row(std::integral_constant<int, 1>{}, y + 1)) break;
     }
-    if (!ok) {
-        for (int qq = q; qq < issued; ++qq) (void)stage_wait(&bars[qq % S], (uint32_t)((qq / S) & 1));
-        return;
+    if (leader) {
+        // the copies warp 0 issued must land before the block's shared memory is
+        // released: wait for the rows it has not waited for itself (bounded)
+        for (int qq = q + (MIPS ? 1 : 0); qq < issued; ++qq)
+            (void)stage_wait(&full[qq % S], (uint32_t)((qq / S) & 1));
     }
-    for (int qq = q + (MIPS ? 1 : 0); qq < issued; ++qq) (void)stage_wait(&bars[qq % S], (uint32_t)((qq / S) & 1));
+    if (!ok) return;
     if constexpr (SAMPLE) observe_flush<VEC>(dp->colp, dp->scal, nx, s, sy, x0, valid, col, acc, lane);
 }
 
 template <int MODEL, int ST, int VEC, bool SAMPLE, int NOISE>
 static cudaError_t launch_one_staged7(const StepArgs &a, int blocks, int warps, cudaStream_t stream)
 {
-    const size_t bytes = (size_t)warps * a.stages * (StageGeom7<ST, VEC>::STAGE_BYTES + sizeof(uint64_t));
+    const size_t bytes = (size_t)a.stages * (StageGeom7<ST, VEC>::stage_bytes(warps) + 2 * sizeof(uint64_t));
     auto kern = step_staged_kernel_q7<MODEL, ST, VEC, SAMPLE, NOISE>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;

@@ -98,16 +98,17 @@ def test_host_only_calls_and_status_codes(lib):
 
 
 def test_staged_block_width_limits(lib):
-    """D2Q9 staged blocks take up to 8 warps (they share each staged row); the
-    D2Q7 staged kernel keeps per-warp rows and at most 4 warps."""
+    """Staged blocks of both velocity sets take 1..8 warps (the warps share each
+    staged row); 9 is refused."""
     from paper_1902_00530_gb300 import _abi
     prm = _prm(tau=1.0, sigma=0.01)
-    for vs, ok8 in ((0, 0), (1, 1)):
+    for vs in (0, 1):
         ctx = ctypes.c_void_p()
         lat = _abi.lbm_lattice(64, 32, 0, 0, vs)
         assert lib.lbm_create(ctypes.byref(lat), 0, ctypes.byref(prm), ctypes.byref(ctx)) == 0
-        assert lib.lbm_set_tuning(ctx, 1, 1, 16, 8, 3) == ok8
+        assert lib.lbm_set_tuning(ctx, 1, 1, 16, 8, 3) == 0
         assert lib.lbm_set_tuning(ctx, 1, 1, 16, 4, 3) == 0
+        assert lib.lbm_set_tuning(ctx, 1, 1, 16, 9, 3) == 1
         lib.lbm_destroy(ctx)
 
 

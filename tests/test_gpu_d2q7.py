@@ -120,7 +120,8 @@ def test_ragged_sizes_default_shape7(nx, ny):
 
 
 SHAPES_FIXED7 = [(1, 16), (2, 16), (4, 16), (4, 48), (2, 128), (8, 32), (1, 16, 2), (2, 32, 8),
-                 (1, 16, 4, 3), (2, 32, 2, 4), (4, 64, 4, 6), (2, 48, 4, 3), (8, 32, 2, 4), (4, 32, 1, 3)]
+                 (1, 16, 4, 3), (2, 32, 2, 4), (4, 64, 4, 6), (2, 48, 4, 3), (8, 32, 2, 4), (4, 32, 1, 3),
+                 (4, 32, 8, 4), (2, 16, 8, 3), (8, 16, 8, 5)]
 
 
 @pytest.mark.parametrize("shape", SHAPES_FIXED7, ids=lambda s: "x".join(map(str, s)))
@@ -150,7 +151,7 @@ def test_staged_kernel_small_and_ragged7(nx, ny):
     for name, over, steps, spec in (("MIPS_Q7_RHO1", {}, 3, W.INIT_CONFIG1),
                                     ("CIL_Q7_RHO1", {}, 20, W.init_ordered(U0_CIL7))):
         model, d = split_preset(name, **over)
-        for shape in ((1, 16, 4, 3), (4, 32, 2, 4)):
+        for shape in ((1, 16, 4, 3), (4, 32, 2, 4), (4, 32, 8, 4)):
             if nx % shape[0]:
                 continue
             got = gpu_run(model, d, nx, ny, steps, SEED, spec, tuning=shape, **Q7)
