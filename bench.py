@@ -36,17 +36,23 @@ BYTES_PER_UPDATE = {"f32": 72, "f16s": 36, "bf16s": 36}   # 9 reads + 9 writes p
 def bytes_per_update(storage: str, q: int = 9) -> int:
     """Algorithmic HBM bytes of one site update: q populations read and written."""
     return BYTES_PER_UPDATE[storage] * q // 9
-KERNEL_SOURCES = ["paper_1902_00530_gb300/csrc/lbm_step.cuh", "paper_1902_00530_gb300/csrc/lbm_step_staged.cuh",
-                  "paper_1902_00530_gb300/csrc/lbm_step_q7.cuh", "paper_1902_00530_gb300/csrc/lbm_step_q7_staged.cuh",
-                  "paper_1902_00530_gb300/csrc/lbm_device.cuh"]
+# The sources each velocity set's step kernels are compiled from (the D2Q7
+# kernels include the D2Q9 headers).
+KERNEL_SOURCES = {
+    9: ["paper_1902_00530_gb300/csrc/lbm_device.cuh", "paper_1902_00530_gb300/csrc/lbm_step.cuh",
+        "paper_1902_00530_gb300/csrc/lbm_step_staged.cuh"],
+    7: ["paper_1902_00530_gb300/csrc/lbm_device.cuh", "paper_1902_00530_gb300/csrc/lbm_step.cuh",
+        "paper_1902_00530_gb300/csrc/lbm_step_staged.cuh", "paper_1902_00530_gb300/csrc/lbm_step_q7.cuh",
+        "paper_1902_00530_gb300/csrc/lbm_step_q7_staged.cuh"],
+}
 
 
-def kernel_hash() -> str:
-    """Hash of the step-kernel sources with comments removed and whitespace
-    collapsed: the recorded DRAM traffic stays valid across comment and layout
-    edits, not across code changes."""
+def kernel_hash(q: int = 9) -> str:
+    """Hash of the velocity set's step-kernel sources with comments removed and
+    whitespace collapsed: the recorded DRAM traffic stays valid across comment
+    and layout edits, not across code changes."""
     h = hashlib.sha256()
-    for p in KERNEL_SOURCES:
+    for p in KERNEL_SOURCES[q]:
         with open(os.path.join(ROOT, p), encoding="utf-8") as f:
             code = re.sub(r"/\*.*?\*/", " ", f.read(), flags=re.S)
         code = re.sub(r"//[^\n]*", " ", code)
@@ -73,7 +79,7 @@ def ncu_traffic(workload: str):
     except Exception:
         return None
     entry = rec.get(workload)
-    if not entry or entry.get("kernel_hash") != kernel_hash():
+    if not entry or entry.get("kernel_hash") != kernel_hash(entry.get("q", 9)):
         return None
     return entry.get("dram_bytes_per_launch")
 
