@@ -223,7 +223,9 @@ lbm_status lbm_load(lbm_ctx *ctx, const char *path);
  * global memory, or 2..8 (MIPS: 3..8) for the kernel that stages population
  * rows in shared memory with bulk copies, that many rows in flight per block,
  * whose warps share each staged row (needs nx a multiple of 16 bytes of
- * storage; D2Q7 lattices also need rows even).  stages = 0 is refused (LBM_ERR_INVALID_ARG) while a D2Q9
+ * storage; D2Q7 lattices also need rows even; the buffers, stages x Q x
+ * (32 vec warps + 2 halo) values, must fit the 227 KB of shared memory a
+ * block can have, else LBM_ERR_INVALID_ARG).  stages = 0 is refused (LBM_ERR_INVALID_ARG) while a D2Q9
  * lattice exceeds 2^32 elements per buffer (see lbm_create); such lattices
  * start on a staged shape and the tuner tries only staged shapes for them.
  * Host only; re-uploads descriptors (syncs) when bound. */

@@ -504,7 +504,9 @@ lbm_status tune_group(lbm_ctx *c, GroupHost &g)
                 // MIPS also tries 3, the least its ring needs (less shared memory, more warps)
                 const int sts[3] = {base_stages, base_stages + 2, 3};
                 for (int w : {1, 2, 4, 8})
-                    for (int k = 0; k < (base_stages > 3 ? 3 : 2); ++k) cands.push_back({v, r, w, sts[k]});
+                    for (int k = 0; k < (base_stages > 3 ? 3 : 2); ++k)
+                        if (staged_smem_bytes(g.q, (int)elem_bytes(g.storage), v, w, sts[k]) <= STAGED_SMEM_MAX)
+                            cands.push_back({v, r, w, sts[k]});
             }
         }
     }
@@ -1081,6 +1083,11 @@ lbm_status lbm_set_tuning(lbm_ctx *c, int32_t mode, int32_t vec, int32_t rows, i
     if (stages != 0)
         for (auto &g : c->groups)
             if (!staged_ok(c, g)) return fail(c, LBM_ERR_INVALID_ARG, "staged kernel needs nx a multiple of 16 bytes");
+    if (stages != 0)
+        for (auto &g : c->groups)
+            if (staged_smem_bytes(g.q, (int)elem_bytes(g.storage), vec, warps, stages) > STAGED_SMEM_MAX)
+                return fail(c, LBM_ERR_INVALID_ARG,
+                            "staged shape needs more than the 227 KB of shared memory a block can have");
     if (stages == 0)
         for (auto &g : c->groups)
             if (!direct_ok(c, g))

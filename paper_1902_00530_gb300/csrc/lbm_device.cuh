@@ -107,6 +107,16 @@ inline float storage_shift(int storage, double w, float rho0)
     return s;
 }
 
+// Dynamic shared memory of a staged block: `stages` row buffers of q
+// population segments, each the block's 32 vec warps columns plus a 16-byte
+// halo on both sides, and a "full" and an "empty" barrier per buffer.
+__host__ __device__ constexpr size_t staged_smem_bytes(int q, int elem_bytes, int vec, int warps, int stages)
+{
+    return (size_t)stages * ((size_t)q * (size_t)(warps * 32 * vec + 2 * (16 / elem_bytes)) * (size_t)elem_bytes + 16);
+}
+// The most dynamic shared memory one block can have on sm_103a (227 KB).
+constexpr size_t STAGED_SMEM_MAX = 232448;
+
 struct StepArgs {
     const LatDesc *desc;  // lattices of this launch group
     int nlat;

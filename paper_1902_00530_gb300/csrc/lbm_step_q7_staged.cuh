@@ -32,8 +32,8 @@ template <int ST, int VEC> struct StageGeom7 {
     static constexpr int W = 32 * VEC;
     // elements per population segment of a block of `warps` warps (16-byte multiple)
     __host__ __device__ static constexpr int seg(int warps) { return warps * W + 2 * HALO; }
-    __host__ __device__ static constexpr int stage_bytes(int warps) { return 7 * seg(warps) * (int)sizeof(T); }
 };
+static_assert(staged_smem_bytes(7, 4, 4, 8, 4) == 4 * (7 * StageGeom7<ST_F32, 4>::seg(8) * 4 + 2 * sizeof(uint64_t)), "");
 
 // Issue the segment copies of destination row y into buffer `buf` (seg
 // elements per population) and arm its barrier, for the block's columns xs ..
@@ -319,7 +319,7 @@ __global__ void __maxnreg__(staged_max_regs<VEC>()) step_staged_kernel_q7(const 
 template <int MODEL, int ST, int VEC, bool SAMPLE, int NOISE>
 static cudaError_t launch_one_staged7(const StepArgs &a, int blocks, int warps, cudaStream_t stream)
 {
-    const size_t bytes = (size_t)a.stages * (StageGeom7<ST, VEC>::stage_bytes(warps) + 2 * sizeof(uint64_t));
+    const size_t bytes = staged_smem_bytes(7, (int)sizeof(typename Store<ST>::T), VEC, warps, a.stages);
     auto kern = step_staged_kernel_q7<MODEL, ST, VEC, SAMPLE, NOISE>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;

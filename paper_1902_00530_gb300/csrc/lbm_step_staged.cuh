@@ -101,8 +101,10 @@ template <int ST, int VEC> struct StageGeom {
     // elements per population segment of a block of `warps` warps (a multiple
     // of 16 bytes, so every segment starts 16-byte aligned)
     __host__ __device__ static constexpr int seg(int warps) { return warps * W + 2 * HALO; }
-    __host__ __device__ static constexpr int stage_bytes(int warps) { return 9 * seg(warps) * (int)sizeof(T); }
 };
+// the launcher's shared-memory size is the kernel's carve-out (ring, then barriers)
+static_assert(staged_smem_bytes(9, 4, 4, 4, 3) == 3 * (9 * StageGeom<ST_F32, 4>::seg(4) * 4 + 2 * sizeof(uint64_t)), "");
+static_assert(staged_smem_bytes(9, 2, 8, 8, 5) == 5 * (9 * StageGeom<ST_F16, 8>::seg(8) * 2 + 2 * sizeof(uint64_t)), "");
 
 // Issue the segment copies of destination row y into stage buffer `buf` (seg
 // elements per population) and arm its barrier (lane 0 arms); executed by one
@@ -437,7 +439,7 @@ namespace lbm {
 template <int MODEL, int ST, int VEC, bool SAMPLE, int NOISE>
 static cudaError_t launch_one_staged(const StepArgs &a, int blocks, int warps, cudaStream_t stream)
 {
-    const size_t bytes = (size_t)a.stages * (StageGeom<ST, VEC>::stage_bytes(warps) + 2 * sizeof(uint64_t));
+    const size_t bytes = staged_smem_bytes(9, (int)sizeof(typename Store<ST>::T), VEC, warps, a.stages);
     auto kern = step_staged_kernel<MODEL, ST, VEC, SAMPLE, NOISE>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;

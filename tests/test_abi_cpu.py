@@ -112,6 +112,22 @@ def test_staged_block_width_limits(lib):
         lib.lbm_destroy(ctx)
 
 
+def test_staged_shared_memory_limit(lib):
+    """A staged shape whose row buffers exceed the 227 KB of shared memory a
+    block can have is refused when it is set, not at launch: D2Q9 FP32 with 8
+    warps of vec 4 takes 37 168 B per buffer, so 6 buffers fit and 7 do not;
+    the D2Q7 buffer (28 912 B) fits 8."""
+    from paper_1902_00530_gb300 import _abi
+    prm = _prm(tau=1.0, sigma=0.01)
+    for vs, fits in ((0, 6), (1, 8)):
+        ctx = ctypes.c_void_p()
+        lat = _abi.lbm_lattice(1024, 64, 0, 0, vs)
+        assert lib.lbm_create(ctypes.byref(lat), 0, ctypes.byref(prm), ctypes.byref(ctx)) == 0
+        for stages in range(2, 9):
+            assert lib.lbm_set_tuning(ctx, 1, 4, 16, 8, stages) == (0 if stages <= fits else 1), (vs, stages)
+        lib.lbm_destroy(ctx)
+
+
 def test_batch_create_groups(lib):
     from paper_1902_00530_gb300 import _abi
     n = 4
