@@ -142,6 +142,12 @@ bool staged_fits(const lbm_lattice &l)
     return l.nx % halo == 0 && l.nx >= halo;
 }
 
+// Whether the group's staged kernel keeps a converted FP32 row (the D2Q9
+// MIPS kernel with 16-bit storage), and the fewest row buffers its ring needs:
+// MIPS holds two rows in use (one with the converted row) plus one in flight.
+bool conv_rows(const GroupHost &g) { return g.q == 9 && staged_conv_rows(g.model, g.storage); }
+int min_stages(const GroupHost &g) { return g.model == LBM_MIPS ? (conv_rows(g) ? 2 : 3) : 2; }
+
 bool staged_ok(const lbm_ctx *c, const GroupHost &g)
 {
     for (int m : g.members)
@@ -501,11 +507,16 @@ lbm_status tune_group(lbm_ctx *c, GroupHost &g)
             if (direct)
                 for (int w : {4, 8}) cands.push_back({v, r, w, 0});
             if (staged && v >= 2) {
-                // MIPS also tries 3, the least its ring needs (less shared memory, more warps)
-                const int sts[3] = {base_stages, base_stages + 2, 3};
+                // MIPS also tries the least its ring needs (less shared memory, more
+                // warps); with the converted row a ring of 2 fetches as far ahead
+                // as one of 3 without it
+                const bool mips = g.model == LBM_MIPS;
+                const int sts[3] = {conv_rows(g) ? 3 : base_stages, conv_rows(g) ? 4 : base_stages + 2,
+                                    min_stages(g)};
                 for (int w : {1, 2, 4, 8})
-                    for (int k = 0; k < (base_stages > 3 ? 3 : 2); ++k)
-                        if (staged_smem_bytes(g.q, (int)elem_bytes(g.storage), v, w, sts[k]) <= STAGED_SMEM_MAX)
+                    for (int k = 0; k < (mips ? 3 : 2); ++k)
+                        if (staged_smem_bytes(g.q, (int)elem_bytes(g.storage), v, w, sts[k],
+                                              conv_rows(g)) <= STAGED_SMEM_MAX)
                             cands.push_back({v, r, w, sts[k]});
             }
         }
@@ -1079,13 +1090,15 @@ lbm_status lbm_set_tuning(lbm_ctx *c, int32_t mode, int32_t vec, int32_t rows, i
         return fail(c, LBM_ERR_INVALID_ARG, "stages must be 0 (direct) or 2..8");
     if (stages != 0)
         for (auto &g : c->groups)
-            if (g.model == LBM_MIPS && stages < 3) return fail(c, LBM_ERR_INVALID_ARG, "MIPS needs at least 3 stages");
+            if (stages < min_stages(g))
+                return fail(c, LBM_ERR_INVALID_ARG, "MIPS needs at least 3 stages (2 with 16-bit storage)");
     if (stages != 0)
         for (auto &g : c->groups)
             if (!staged_ok(c, g)) return fail(c, LBM_ERR_INVALID_ARG, "staged kernel needs nx a multiple of 16 bytes");
     if (stages != 0)
         for (auto &g : c->groups)
-            if (staged_smem_bytes(g.q, (int)elem_bytes(g.storage), vec, warps, stages) > STAGED_SMEM_MAX)
+            if (staged_smem_bytes(g.q, (int)elem_bytes(g.storage), vec, warps, stages,
+                                  conv_rows(g)) > STAGED_SMEM_MAX)
                 return fail(c, LBM_ERR_INVALID_ARG,
                             "staged shape needs more than the 227 KB of shared memory a block can have");
     if (stages == 0)

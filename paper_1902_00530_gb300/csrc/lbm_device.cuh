@@ -109,10 +109,24 @@ inline float storage_shift(int storage, double w, float rho0)
 
 // Dynamic shared memory of a staged block: `stages` row buffers of q
 // population segments, each the block's 32 vec warps columns plus a 16-byte
-// halo on both sides, and a "full" and an "empty" barrier per buffer.
-__host__ __device__ constexpr size_t staged_smem_bytes(int q, int elem_bytes, int vec, int warps, int stages)
+// halo on both sides, and a "full" and an "empty" barrier per buffer; with
+// `conv`, also two FP32 rows of the q pulled populations of the block's sites
+// (the converted rows the MIPS update of 16-bit storage reads).
+__host__ __device__ constexpr size_t staged_smem_bytes(int q, int elem_bytes, int vec, int warps, int stages,
+                                                       bool conv = false)
 {
-    return (size_t)stages * ((size_t)q * (size_t)(warps * 32 * vec + 2 * (16 / elem_bytes)) * (size_t)elem_bytes + 16);
+    return (size_t)stages * ((size_t)q * (size_t)(warps * 32 * vec + 2 * (16 / elem_bytes)) * (size_t)elem_bytes + 16) +
+           (conv ? 2 * (size_t)q * (size_t)(warps * 32 * vec) * 4 : 0);
+}
+
+// Whether a staged MIPS kernel keeps the converted row (above): 16-bit
+// storage, where it saves converting each staged value a second time.
+#ifndef LBM_CONV_ROWS_F32
+#define LBM_CONV_ROWS_F32 0
+#endif
+__host__ __device__ constexpr bool staged_conv_rows(int model, int storage)
+{
+    return model == MODEL_MIPS && (storage != ST_F32 || LBM_CONV_ROWS_F32 != 0);
 }
 // The most dynamic shared memory one block can have on sm_103a (227 KB).
 constexpr size_t STAGED_SMEM_MAX = 232448;

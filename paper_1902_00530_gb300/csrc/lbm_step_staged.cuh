@@ -102,9 +102,12 @@ template <int ST, int VEC> struct StageGeom {
     // of 16 bytes, so every segment starts 16-byte aligned)
     __host__ __device__ static constexpr int seg(int warps) { return warps * W + 2 * HALO; }
 };
-// the launcher's shared-memory size is the kernel's carve-out (ring, then barriers)
+// the launcher's shared-memory size is the kernel's carve-out (ring, barriers,
+// then the converted row)
 static_assert(staged_smem_bytes(9, 4, 4, 4, 3) == 3 * (9 * StageGeom<ST_F32, 4>::seg(4) * 4 + 2 * sizeof(uint64_t)), "");
-static_assert(staged_smem_bytes(9, 2, 8, 8, 5) == 5 * (9 * StageGeom<ST_F16, 8>::seg(8) * 2 + 2 * sizeof(uint64_t)), "");
+static_assert(staged_smem_bytes(9, 2, 8, 8, 5, true) == 5 * (9 * StageGeom<ST_F16, 8>::seg(8) * 2 + 2 * sizeof(uint64_t)) +
+                                                            2 * 8 * 9 * StageGeom<ST_F16, 8>::W * 4,
+              "");
 
 // Issue the segment copies of destination row y into stage buffer `buf` (seg
 // elements per population) and arm its barrier (lane 0 arms); executed by one
@@ -202,18 +205,58 @@ __device__ __forceinline__ float stage_density_at(const typename Store<ST>::T *b
     return density<1>(v, 0);
 }
 
+// The lane's VEC FP32 values at p (16-byte aligned for VEC >= 4).
+template <int VEC> __device__ __forceinline__ void put_f32(float *p, const float v[VEC])
+{
+    if constexpr (VEC % 4 == 0) {
+#pragma unroll
+        for (int k = 0; k < VEC / 4; ++k)
+            reinterpret_cast<float4 *>(p)[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+    } else if constexpr (VEC == 2) {
+        *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
+    } else {
+        p[0] = v[0];
+    }
+}
+template <int VEC> __device__ __forceinline__ void get_f32(const float *p, float v[VEC])
+{
+    if constexpr (VEC % 4 == 0) {
+#pragma unroll
+        for (int k = 0; k < VEC / 4; ++k) {
+            const float4 w = reinterpret_cast<const float4 *>(p)[k];
+            v[4 * k] = w.x;
+            v[4 * k + 1] = w.y;
+            v[4 * k + 2] = w.z;
+            v[4 * k + 3] = w.w;
+        }
+    } else if constexpr (VEC == 2) {
+        const float2 w = *reinterpret_cast<const float2 *>(p);
+        v[0] = w.x;
+        v[1] = w.y;
+    } else {
+        v[0] = p[0];
+    }
+}
+
 // Density window of a staged row: r[0] at x0-1, r[1..VEC] the lane's sites,
 // r[VEC+1] at x0+VEC.  Neighbours come by shuffle (a lane past a ragged strip
 // end sums the right halo's site, which its segment index reaches); the two
 // sites outside the warp's columns, lane 0's left and lane 31's right, are
 // summed from shared memory in one pass, each lane summing the site its role
-// needs (the same values and order as its neighbour's own sum).
+// needs (the same values and order as its neighbour's own sum).  With a
+// converted row `cv` (population i of the lane's sites at cv + i * cs), the
+// pulled FP32 values are also left there for the row's update.
 template <int ST, int VEC>
 __device__ __forceinline__ void stage_density_window(const typename Store<ST>::T *buf, int sg, int b,
-                                                     const Shift3 &sh, int lane, float r[VEC + 2])
+                                                     const Shift3 &sh, int lane, float r[VEC + 2],
+                                                     float *cv = nullptr, int cs = 0)
 {
     float f[9][VEC];
     stage_row<ST, VEC>(buf, sg, b, sh, f);
+    if (cv) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) put_f32<VEC>(cv + i * cs, f[i]);
+    }
     densities<VEC, paired_sites<ST, VEC>()>(f, r + 1);
     const float edge = stage_density_at<ST, VEC>(buf, sg, lane == 0 ? b - 1 : b + VEC, sh);
     float left = __shfl_up_sync(FULL, r[VEC], 1);
@@ -273,10 +316,15 @@ __global__ void __maxnreg__(staged_max_regs<VEC>()) step_staged_kernel(const Ste
     const int S = a.stages;
     const int sg = G::seg(warps);  // elements per population segment
     const int stage_elems = 9 * sg;
-    // carve-out: S stage buffers, then S "full" and S "empty" barriers
+    // carve-out: S stage buffers, then S "full" and S "empty" barriers, then
+    // (CONV) two converted rows per warp, row q in cv(q): population i of the
+    // warp's sites at i * W
+    constexpr bool CONV = staged_conv_rows(MODEL, ST);
     T *ring = reinterpret_cast<T *>(smem_raw);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + (size_t)S * stage_elems * sizeof(T));
     uint64_t *empty = full + S;
+    float *const cv0 = reinterpret_cast<float *>(empty + S) + (size_t)warp * 9 * G::W + (threadIdx.x & 31) * VEC;
+    auto cv = [&](int q) { return cv0 + (size_t)(q & 1) * warps * 9 * G::W; };
 
     const StagedBlock blk = staged_block(a, warps);
     const LatDesc *dp = blk.dp;
@@ -357,6 +405,10 @@ __global__ void __maxnreg__(staged_max_regs<VEC>()) step_staged_kernel(const Ste
         for (int q = 0; q < 5; ++q) acc[q] = 0.0;
     }
 
+    // MIPS: row q+1's densities are taken one row ahead of its update.  With
+    // CONV its pulled populations are converted then too, into the warp's
+    // converted row, so the update reads them from there and the staged row is
+    // released one row earlier.
     float rm[VEC + 2], rc[VEC + 2], rn[VEC + 2];
     int q = 0;  // next stage to consume
     if constexpr (MIPS) {
@@ -365,20 +417,31 @@ __global__ void __maxnreg__(staged_max_regs<VEC>()) step_staged_kernel(const Ste
             release(0);
         }
         q = 1;
-        if (wait_q(1)) stage_density_window<ST, VEC>(stage_ptr(1), sg, b, sh, lane, rc);
+        if (wait_q(1)) {
+            stage_density_window<ST, VEC>(stage_ptr(1), sg, b, sh, lane, rc, CONV ? cv(1) : nullptr, G::W);
+            if constexpr (CONV) release(1);
+        }
     }
 
     for (int y = y_begin; y < y_end && ok; ++y) {
         const int qc = q;  // stage of row y
         float f[9][VEC];
-        if constexpr (MIPS) {
+        if constexpr (CONV) {
+            if (!wait_q(qc + 1)) break;
+            stage_density_window<ST, VEC>(stage_ptr(qc + 1), sg, b, sh, lane, rn, cv(qc + 1), G::W);
+            release(qc + 1);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) get_f32<VEC>(cv(qc) + i * G::W, f[i]);
+        } else if constexpr (MIPS) {
             if (!wait_q(qc + 1)) break;
             stage_density_window<ST, VEC>(stage_ptr(qc + 1), sg, b, sh, lane, rn);
+            stage_row<ST, VEC>(stage_ptr(qc), sg, b, sh, f);
+            release(qc);
         } else {
             if (!wait_q(qc)) break;
+            stage_row<ST, VEC>(stage_ptr(qc), sg, b, sh, f);
+            release(qc);
         }
-        stage_row<ST, VEC>(stage_ptr(qc), sg, b, sh, f);
-        release(qc);
         q = qc + 1;
 
         float gx[VEC], gy[VEC];
@@ -439,7 +502,8 @@ namespace lbm {
 template <int MODEL, int ST, int VEC, bool SAMPLE, int NOISE>
 static cudaError_t launch_one_staged(const StepArgs &a, int blocks, int warps, cudaStream_t stream)
 {
-    const size_t bytes = staged_smem_bytes(9, (int)sizeof(typename Store<ST>::T), VEC, warps, a.stages);
+    const size_t bytes =
+        staged_smem_bytes(9, (int)sizeof(typename Store<ST>::T), VEC, warps, a.stages, staged_conv_rows(MODEL, ST));
     auto kern = step_staged_kernel<MODEL, ST, VEC, SAMPLE, NOISE>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;

@@ -112,6 +112,21 @@ def test_staged_block_width_limits(lib):
         lib.lbm_destroy(ctx)
 
 
+def test_mips_ring_depth(lib):
+    """A staged MIPS ring holds its density halo: 3 row buffers at least with
+    FP32 storage, 2 with 16-bit storage (whose kernel keeps the rows it has
+    converted); the other closures take 2."""
+    from paper_1902_00530_gb300 import _abi
+    for model, storage, least in ((1, 0, 3), (1, 1, 2), (1, 2, 2), (2, 0, 2), (0, 1, 2)):
+        prm = _prm(tau=1.0, sigma=0.01, C=6.0, rho_star=5.0 / 3.0, u_max=0.3, A=0.06845, B=0.3)
+        ctx = ctypes.c_void_p()
+        lat = _abi.lbm_lattice(256, 64, storage, 0)
+        assert lib.lbm_create(ctypes.byref(lat), model, ctypes.byref(prm), ctypes.byref(ctx)) == 0
+        for stages in (2, 3):
+            assert lib.lbm_set_tuning(ctx, 1, 4, 16, 4, stages) == (0 if stages >= least else 1), (model, storage)
+        lib.lbm_destroy(ctx)
+
+
 def test_staged_shared_memory_limit(lib):
     """A staged shape whose row buffers exceed the 227 KB of shared memory a
     block can have is refused when it is set, not at launch: D2Q9 FP32 with 8
