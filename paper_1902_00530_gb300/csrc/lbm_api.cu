@@ -142,10 +142,10 @@ bool staged_fits(const lbm_lattice &l)
     return l.nx % halo == 0 && l.nx >= halo;
 }
 
-// Whether the group's staged kernel keeps a converted FP32 row (the D2Q9
-// MIPS kernel with 16-bit storage), and the fewest row buffers its ring needs:
-// MIPS holds two rows in use (one with the converted row) plus one in flight.
-bool conv_rows(const GroupHost &g) { return g.q == 9 && staged_conv_rows(g.model, g.storage); }
+// Whether the group's staged kernel keeps converted FP32 rows (MIPS with
+// 16-bit storage), and the fewest row buffers its ring needs: MIPS holds two
+// rows in use (one with the converted rows) plus one in flight.
+bool conv_rows(const GroupHost &g) { return staged_conv_rows(g.model, g.storage); }
 int min_stages(const GroupHost &g) { return g.model == LBM_MIPS ? (conv_rows(g) ? 2 : 3) : 2; }
 
 bool staged_ok(const lbm_ctx *c, const GroupHost &g)

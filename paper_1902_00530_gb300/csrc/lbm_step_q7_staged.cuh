@@ -34,6 +34,9 @@ template <int ST, int VEC> struct StageGeom7 {
     __host__ __device__ static constexpr int seg(int warps) { return warps * W + 2 * HALO; }
 };
 static_assert(staged_smem_bytes(7, 4, 4, 8, 4) == 4 * (7 * StageGeom7<ST_F32, 4>::seg(8) * 4 + 2 * sizeof(uint64_t)), "");
+static_assert(staged_smem_bytes(7, 2, 4, 8, 2, true) ==
+                  2 * (7 * StageGeom7<ST_BF16, 4>::seg(8) * 2 + 2 * sizeof(uint64_t)) + 2 * 8 * 7 * StageGeom7<ST_BF16, 4>::W * 4,
+              "");
 
 // Issue the segment copies of destination row y into buffer `buf` (seg
 // elements per population) and arm its barrier, for the block's columns xs ..
@@ -123,13 +126,19 @@ __device__ __forceinline__ float stage_density_at7(const typename Store<ST>::T *
 // Density window of a staged row (r[0] at x0-1, r[1..VEC] the lane's sites,
 // r[VEC+1] at x0+VEC): neighbours by shuffle, the two sites outside the warp's
 // columns summed from shared memory in one pass (lane 0 the left one, every
-// other lane the right one, which lane 31 keeps).
+// other lane the right one, which lane 31 keeps).  With a converted row `cv`
+// the pulled FP32 values are also left there (population i at cv + i * cs).
 template <int ST, int VEC, int P>
 __device__ __forceinline__ void stage_density_window7(const typename Store<ST>::T *buf, int sg, int b,
-                                                      const Shift3 &sh, int lane, float r[VEC + 2])
+                                                      const Shift3 &sh, int lane, float r[VEC + 2],
+                                                      float *cv = nullptr, int cs = 0)
 {
     float f[7][VEC];
     stage_row7<ST, VEC, P>(buf, sg, b, sh, f);
+    if (cv) {
+#pragma unroll
+        for (int i = 0; i < 7; ++i) put_f32<VEC>(cv + i * cs, f[i]);
+    }
 #pragma unroll
     for (int j = 0; j < VEC; ++j) r[j + 1] = density7_at<VEC>(f, j);
     const float edge = stage_density_at7<ST, VEC, P>(buf, sg, lane == 0 ? b - 1 : b + VEC, sh);
@@ -152,9 +161,14 @@ __global__ void __maxnreg__(staged_max_regs<VEC>()) step_staged_kernel_q7(const 
     const int sg = G::seg(warps);
     const int stage_elems = 7 * sg;
     // carve-out: S stage buffers, then S "full" and S "empty" barriers
+    // carve-out: S stage buffers, S "full" and S "empty" barriers, then (CONV,
+    // as in step_staged_kernel) two converted rows per warp
+    constexpr bool CONV = staged_conv_rows(MODEL, ST);
     T *ring = reinterpret_cast<T *>(smem_raw);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + (size_t)S * stage_elems * sizeof(T));
     uint64_t *empty = full + S;
+    float *const cv0 = reinterpret_cast<float *>(empty + S) + (size_t)warp * 7 * G::W + (threadIdx.x & 31) * VEC;
+    auto cv = [&](int q) { return cv0 + (size_t)(q & 1) * warps * 7 * G::W; };
 
     const StagedBlock blk = staged_block(a, warps);
     const LatDesc *dp = blk.dp;
@@ -242,7 +256,10 @@ __global__ void __maxnreg__(staged_max_regs<VEC>()) step_staged_kernel_q7(const 
             release(0);
         }
         q = 1;
-        if (wait_q(1)) stage_density_window7<ST, VEC, 0>(stage_ptr(1), sg, b, sh, lane, rc);
+        if (wait_q(1)) {
+            stage_density_window7<ST, VEC, 0>(stage_ptr(1), sg, b, sh, lane, rc, CONV ? cv(1) : nullptr, G::W);
+            if constexpr (CONV) release(1);
+        }
     }
 
     // one row of parity P; returns false if a wait gave up
@@ -250,14 +267,22 @@ __global__ void __maxnreg__(staged_max_regs<VEC>()) step_staged_kernel_q7(const 
         constexpr int P = decltype(parity)::value;
         const int qc = q;
         float f[7][VEC];
-        if constexpr (MIPS) {
+        if constexpr (CONV) {
+            if (!wait_q(qc + 1)) return false;
+            stage_density_window7<ST, VEC, 1 - P>(stage_ptr(qc + 1), sg, b, sh, lane, rn, cv(qc + 1), G::W);
+            release(qc + 1);
+#pragma unroll
+            for (int i = 0; i < 7; ++i) get_f32<VEC>(cv(qc) + i * G::W, f[i]);
+        } else if constexpr (MIPS) {
             if (!wait_q(qc + 1)) return false;
             stage_density_window7<ST, VEC, 1 - P>(stage_ptr(qc + 1), sg, b, sh, lane, rn);
+            stage_row7<ST, VEC, P>(stage_ptr(qc), sg, b, sh, f);
+            release(qc);
         } else {
             if (!wait_q(qc)) return false;
+            stage_row7<ST, VEC, P>(stage_ptr(qc), sg, b, sh, f);
+            release(qc);
         }
-        stage_row7<ST, VEC, P>(stage_ptr(qc), sg, b, sh, f);
-        release(qc);
         q = qc + 1;
         float gx[VEC], gy[VEC];
         if constexpr (MIPS) {
@@ -319,7 +344,8 @@ __global__ void __maxnreg__(staged_max_regs<VEC>()) step_staged_kernel_q7(const 
 template <int MODEL, int ST, int VEC, bool SAMPLE, int NOISE>
 static cudaError_t launch_one_staged7(const StepArgs &a, int blocks, int warps, cudaStream_t stream)
 {
-    const size_t bytes = staged_smem_bytes(7, (int)sizeof(typename Store<ST>::T), VEC, warps, a.stages);
+    const size_t bytes =
+        staged_smem_bytes(7, (int)sizeof(typename Store<ST>::T), VEC, warps, a.stages, staged_conv_rows(MODEL, ST));
     auto kern = step_staged_kernel_q7<MODEL, ST, VEC, SAMPLE, NOISE>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;

@@ -121,7 +121,22 @@ def test_ragged_sizes_default_shape7(nx, ny):
 
 SHAPES_FIXED7 = [(1, 16), (2, 16), (4, 16), (4, 48), (2, 128), (8, 32), (1, 16, 2), (2, 32, 8),
                  (1, 16, 4, 3), (2, 32, 2, 4), (4, 64, 4, 6), (2, 48, 4, 3), (8, 32, 2, 4), (4, 32, 1, 3),
-                 (4, 32, 8, 4), (2, 16, 8, 3), (8, 16, 8, 5)]
+                 (4, 32, 8, 4), (2, 16, 8, 3), (8, 16, 8, 5), (4, 32, 8, 2), (4, 16, 4, 2)]
+
+
+def staged_refusal7(model, storage, shape):
+    """Why lbm_set_tuning refuses a staged D2Q7 shape, or None (as on D2Q9:
+    MIPS needs 3 row buffers, 2 with 16-bit storage and its two converted FP32
+    rows per warp; the buffers must fit a block's 227 KB)."""
+    if len(shape) < 4:
+        return None
+    vec, _, warps, stages = shape
+    eb = 4 if storage == "f32" else 2
+    conv = model == "mips" and eb == 2
+    if model == "mips" and stages < (2 if conv else 3):
+        return "stages"
+    smem = stages * (7 * (warps * 32 * vec + 2 * (16 // eb)) * eb + 16) + (2 * 7 * warps * 32 * vec * 4 if conv else 0)
+    return "shared memory" if smem > 232448 else None
 
 
 @pytest.mark.parametrize("shape", SHAPES_FIXED7, ids=lambda s: "x".join(map(str, s)))
@@ -137,6 +152,11 @@ def test_launch_shapes_give_identical_states7(shape, storage, name):
     model, d = split_preset(name, **(dict(sigma=0.01) if name == "PASSIVE" else {}))
     nx, ny = 264, 70
     spec = W.INIT_CONFIG1 if model != "cil" else W.init_ordered(U0_CIL7)
+    if staged_refusal7(model, storage, shape):
+        from paper_1902_00530_gb300 import LBMError
+        with pytest.raises(LBMError, match="INVALID_ARG"):
+            gpu_run(model, d, nx, ny, 9, SEED, spec, storage=storage, tuning=shape, **Q7)
+        return
     base = gpu_run(model, d, nx, ny, 9, SEED, spec, storage=storage, tuning=(1, 16), **Q7)
     got = gpu_run(model, d, nx, ny, 9, SEED, spec, storage=storage, tuning=shape, **Q7)
     np.testing.assert_array_equal(got, base)
@@ -158,6 +178,21 @@ def test_staged_kernel_small_and_ragged7(nx, ny):
             base = gpu_run(model, d, nx, ny, steps, SEED, spec, tuning=(1, 16), **Q7)
             np.testing.assert_array_equal(got, base)
             assert_parity(got, model, d, nx, ny, steps, SEED, spec)
+
+
+@pytest.mark.parametrize("storage", ["f16s", "bf16s"])
+@pytest.mark.parametrize("nx,ny", [(8, 2), (64, 64), (96, 34), (520, 18)])
+def test_staged_mips_16bit_small_and_ragged7(nx, ny, storage):
+    """The 16-bit D2Q7 MIPS staged kernel (converted FP32 rows, each staged
+    row released a row early) on small and ragged lattices, rings of 2 to 4:
+    bitwise the direct kernel's states."""
+    model, d = split_preset("MIPS_Q7_RHO1")
+    for shape in ((1, 16, 4, 2), (4, 16, 4, 2), (2, 8, 8, 3), (4, 32, 2, 4), (8, 16, 1, 2)):
+        if nx % shape[0]:
+            continue
+        got = gpu_run(model, d, nx, ny, 5, SEED, W.INIT_CONFIG1, storage=storage, tuning=shape, **Q7)
+        base = gpu_run(model, d, nx, ny, 5, SEED, W.INIT_CONFIG1, storage=storage, tuning=(1, 16), **Q7)
+        np.testing.assert_array_equal(got, base)
 
 
 # ---------------------------------------------------------- noise stream ---

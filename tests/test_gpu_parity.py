@@ -227,6 +227,22 @@ def test_staged_kernel_small_and_ragged(nx, ny):
             assert_parity(got, model, d, nx, ny, steps, SEED, spec)
 
 
+@pytest.mark.parametrize("storage", ["f16s", "bf16s"])
+@pytest.mark.parametrize("nx,ny", [(8, 3), (64, 64), (96, 33), (520, 17)])
+def test_staged_mips_16bit_small_and_ragged(nx, ny, storage):
+    """The 16-bit MIPS staged kernel, which keeps converted FP32 rows and
+    releases each staged row a row early, on lattices narrower than a strip and
+    with a ragged last strip (idle lanes and warps), rings of 2 to 4: bitwise
+    the direct kernel's states."""
+    model, d = split_preset("MIPS_RHO1")
+    for shape in ((1, 16, 4, 2), (4, 16, 4, 2), (2, 8, 8, 3), (4, 32, 2, 4), (8, 16, 1, 2)):
+        if nx % shape[0]:
+            continue
+        got = gpu_run(model, d, nx, ny, 5, SEED, W.INIT_CONFIG1, storage=storage, tuning=shape)
+        base = gpu_run(model, d, nx, ny, 5, SEED, W.INIT_CONFIG1, storage=storage, tuning=(1, 16))
+        np.testing.assert_array_equal(got, base)
+
+
 # ---------------------------------------------------------- noise stream ---
 def _write_state_file(path, f, t, seed, lattice_id, model, storage=0, rho0=1.0):
     """A state file as lbm_save writes it (one lattice): magic, (count, t,
