@@ -89,6 +89,10 @@ struct lbm_ctx {
     std::vector<cudaEvent_t> ev_pool;
     std::vector<std::pair<int, bool>> ev_marks;  // (first event index, is step kernel)
     size_t ev_used = 0;
+    // launch groups after the first run on their own streams, forked from and
+    // joined back into the bound stream (parallel branches of the step graph)
+    std::vector<cudaStream_t> aux;
+    std::vector<cudaEvent_t> aux_ev;  // [0]: fork, [1 + i]: join of aux[i]
 };
 
 namespace {
@@ -349,7 +353,8 @@ const LatDesc *all_desc(const lbm_ctx *c)
 uint32_t *t_dev(const lbm_ctx *c) { return reinterpret_cast<uint32_t *>(c->scratch); }
 unsigned *err_dev(const lbm_ctx *c) { return reinterpret_cast<unsigned *>(c->scratch + 4); }
 
-cudaError_t launch_group_step(const lbm_ctx *c, const GroupHost &g, int src, uint32_t k, bool sample)
+cudaError_t launch_group_step(const lbm_ctx *c, const GroupHost &g, int src, uint32_t k, bool sample,
+                              cudaStream_t stream)
 {
     StepArgs a;
     a.desc = reinterpret_cast<const LatDesc *>(c->scratch + g.desc_off);
@@ -372,16 +377,16 @@ cudaError_t launch_group_step(const lbm_ctx *c, const GroupHost &g, int src, uin
     const int kind = g.stages > 0 ? 1 : 0;
     if (g.q == 7) {
         if (g.storage == LBM_F32)
-            return launch_step_q7_f32(g.model, kind, g.vec, sample, noise, a, g.blocks, g.warps, c->stream);
+            return launch_step_q7_f32(g.model, kind, g.vec, sample, noise, a, g.blocks, g.warps, stream);
         if (g.storage == LBM_F16_SHIFTED)
-            return launch_step_q7_f16(g.model, kind, g.vec, sample, noise, a, g.blocks, g.warps, c->stream);
-        return launch_step_q7_bf16(g.model, kind, g.vec, sample, noise, a, g.blocks, g.warps, c->stream);
+            return launch_step_q7_f16(g.model, kind, g.vec, sample, noise, a, g.blocks, g.warps, stream);
+        return launch_step_q7_bf16(g.model, kind, g.vec, sample, noise, a, g.blocks, g.warps, stream);
     }
     if (g.storage == LBM_F32)
-        return launch_step_f32(g.model, kind, g.vec, sample, noise, a, g.blocks, g.warps, c->stream);
+        return launch_step_f32(g.model, kind, g.vec, sample, noise, a, g.blocks, g.warps, stream);
     if (g.storage == LBM_F16_SHIFTED)
-        return launch_step_f16(g.model, kind, g.vec, sample, noise, a, g.blocks, g.warps, c->stream);
-    return launch_step_bf16(g.model, kind, g.vec, sample, noise, a, g.blocks, g.warps, c->stream);
+        return launch_step_f16(g.model, kind, g.vec, sample, noise, a, g.blocks, g.warps, stream);
+    return launch_step_bf16(g.model, kind, g.vec, sample, noise, a, g.blocks, g.warps, stream);
 }
 
 cudaError_t launch_group_observe(const lbm_ctx *c, const GroupHost &g, int src)
@@ -429,17 +434,66 @@ cudaError_t prof_end(lbm_ctx *c)
 }
 
 // Enqueue n steps starting at host time t0 from buffer parity p0.
+// Streams and events for running the launch groups side by side (created
+// once, outside any capture; destroyed with the context).
+lbm_status ensure_aux(lbm_ctx *c)
+{
+    const size_t need = c->groups.size() - 1;
+    if (c->aux_ev.empty()) {
+        cudaEvent_t e;
+        CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "create event");
+        c->aux_ev.push_back(e);
+    }
+    while (c->aux.size() < need) {
+        cudaStream_t s;
+        CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "create stream");
+        c->aux.push_back(s);
+        cudaEvent_t e;
+        CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "create event");
+        c->aux_ev.push_back(e);
+    }
+    return LBM_OK;
+}
+
+// The groups hold disjoint lattices, so their step launches are independent:
+// with several groups (and no per-launch timing) group i > 0 runs on aux[i-1],
+// forked from the bound stream, and the branches join before each finaliser
+// (which reads every lattice's partials) and at the end.  In a captured graph
+// these are parallel branches, so one group's launch fills the other's tail.
 lbm_status enqueue_steps(lbm_ctx *c, int64_t n, int64_t t0, int p0, int64_t *launches)
 {
+    const bool par = c->groups.size() > 1 && !c->profiling && c->aux.size() + 1 >= c->groups.size();
+    bool forked = false;
+    auto fork = [&]() -> cudaError_t {
+        cudaError_t e = cudaEventRecord(c->aux_ev[0], c->stream);
+        for (size_t i = 0; e == cudaSuccess && i + 1 < c->groups.size(); ++i)
+            e = cudaStreamWaitEvent(c->aux[i], c->aux_ev[0], 0);
+        forked = e == cudaSuccess;
+        return e;
+    };
+    auto join = [&]() -> cudaError_t {
+        cudaError_t e = cudaSuccess;
+        for (size_t i = 0; e == cudaSuccess && i + 1 < c->groups.size(); ++i) {
+            e = cudaEventRecord(c->aux_ev[1 + i], c->aux[i]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->aux_ev[1 + i], 0);
+        }
+        forked = false;
+        return e;
+    };
     for (int64_t k = 0; k < n; ++k) {
         const bool sample = c->sample_every > 0 && ((t0 + k + 1) % c->sample_every == 0);
-        for (const GroupHost &g : c->groups) {
+        if (par && !forked) CK(fork(), "fork launch groups");
+        for (size_t gi = 0; gi < c->groups.size(); ++gi) {
+            const GroupHost &g = c->groups[gi];
             CK(prof_begin(c, true), "record event");
-            CK(launch_group_step(c, g, (int)((p0 + k) & 1), (uint32_t)k, sample), "launch step kernel");
+            CK(launch_group_step(c, g, (int)((p0 + k) & 1), (uint32_t)k, sample,
+                                 par && gi > 0 ? c->aux[gi - 1] : c->stream),
+               "launch step kernel");
             CK(prof_end(c), "record event");
             ++*launches;
         }
         if (sample) {
+            if (par) CK(join(), "join launch groups");
             CK(prof_begin(c, false), "record event");
             CK(launch_finalize(all_desc(c), (int)c->lats.size(), c->max_chunk, t_dev(c), (uint32_t)k, 1,
                                err_dev(c), c->stream),
@@ -448,6 +502,7 @@ lbm_status enqueue_steps(lbm_ctx *c, int64_t n, int64_t t0, int p0, int64_t *lau
             ++*launches;
         }
     }
+    if (forked) CK(join(), "join launch groups");
     CK(prof_begin(c, false), "record event");
     CK(launch_advance_time(t_dev(c), (uint32_t)n, c->stream), "launch time advance");
     CK(prof_end(c), "record event");
@@ -533,14 +588,14 @@ lbm_status tune_group(lbm_ctx *c, GroupHost &g)
         g.stages = sh.stages;
         lbm_status st = upload_descs(c);
         if (st != LBM_OK) return st;
-        cudaError_t e = launch_group_step(c, g, c->parity, 0, false);
+        cudaError_t e = launch_group_step(c, g, c->parity, 0, false, c->stream);
         if (e != cudaSuccess) {  // a shape this device cannot launch (e.g. shared memory): skip it
             cudaGetLastError();
             continue;
         }
         CK(cudaEventRecord(e0, c->stream), "record event");
         const int reps = 3;
-        for (int q = 0; q < reps; ++q) CK(launch_group_step(c, g, c->parity, 0, false), "tuning launch");
+        for (int q = 0; q < reps; ++q) CK(launch_group_step(c, g, c->parity, 0, false, c->stream), "tuning launch");
         CK(cudaEventRecord(e1, c->stream), "record event");
         CK(cudaEventSynchronize(e1), "synchronise event");
         float ms = 0.f;
@@ -738,6 +793,10 @@ lbm_status lbm_step(lbm_ctx *c, int64_t n)
         if (st != LBM_OK) return st;
     }
     const bool graphs = c->use_graphs && c->stream != nullptr && !c->profiling;
+    if (c->groups.size() > 1 && !c->profiling) {
+        st = ensure_aux(c);
+        if (st != LBM_OK) return st;
+    }
     int64_t done = 0;
     while (done < n) {
         int64_t chunk = n - done;
@@ -1212,6 +1271,8 @@ void lbm_destroy(lbm_ctx *c)
     if (!c) return;
     drop_graphs(c);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->aux_ev) cudaEventDestroy(e);
+    for (cudaStream_t s : c->aux) cudaStreamDestroy(s);
     delete c;
 }
 

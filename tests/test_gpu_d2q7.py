@@ -195,6 +195,29 @@ def test_staged_mips_16bit_small_and_ragged7(nx, ny, storage):
         np.testing.assert_array_equal(got, base)
 
 
+@pytest.mark.parametrize("storage", ["f16s", "bf16s"])
+def test_sampled_observables_16bit_mips_staged7(storage):
+    """Sample steps of the 16-bit D2Q7 MIPS staged kernel (converted rows):
+    states bitwise those of the direct kernel, records equal to FP32 rounding
+    (each thread's partial sums depend on the launch shape)."""
+    model, d = split_preset("MIPS_Q7_RHO1")
+    nx, ny, every, steps = 264, 70, 3, 12
+    runs = []
+    for tuning in ((1, 16), (4, 16, 4, 2), (4, 32, 8, 2)):
+        sim = gpu_sim(model, d, nx, ny, SEED, W.INIT_CONFIG1, storage=storage, sample_every=every, ring=16,
+                      tuning=tuning, **Q7)
+        sim.step(steps)
+        runs.append((sim.observable_series(), sim.get_state(host=True).numpy()))
+        sim.close()
+    (s0, f0) = runs[0]
+    assert [r["t"] for r in s0] == list(range(every, steps + 1, every))
+    for series, f in runs[1:]:
+        np.testing.assert_array_equal(f, f0)
+        for a, b in zip(series, s0):
+            for key in ("mass", "phi", "drho_y", "drho_x", "var_rho", "zeta"):
+                assert a[key] == pytest.approx(b[key], rel=1e-6, abs=1e-6), (key, a[key], b[key])
+
+
 # ---------------------------------------------------------- noise stream ---
 @pytest.mark.parametrize("t,lattice_id,seed", [(0, 0, SEED), (7, 3, 12345), (2 ** 31 + 12345, 2 ** 24 - 1,
                                                                                   2 ** 63 + 99)])

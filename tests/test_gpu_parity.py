@@ -308,6 +308,33 @@ def test_sampled_observables_match_oracle():
         assert now[key] == pytest.approx(series[-1][key], rel=1e-12, abs=1e-15)
 
 
+@pytest.mark.parametrize("storage", ["f16s", "bf16s"])
+def test_sampled_observables_16bit_mips_staged(storage):
+    """Sample steps of the 16-bit MIPS staged kernel (converted rows, ring of
+    2): the states stay bitwise those of the direct kernel, and every sampled
+    record agrees with the direct kernel's to FP32 rounding (the same stored
+    values; each thread first sums its vec sites in FP32, so the partial sums
+    depend on the launch shape)."""
+    model, d = split_preset("MIPS_RHO1")
+    nx, ny, every, steps = 264, 70, 3, 12
+    runs = []
+    for tuning in ((1, 16), (4, 16, 4, 2), (2, 8, 8, 3)):
+        sim = gpu_sim(model, d, nx, ny, SEED, W.INIT_CONFIG1, storage=storage, sample_every=every, ring=16,
+                      tuning=tuning)
+        sim.step(steps)
+        runs.append((sim.observable_series(), sim.get_state(host=True).numpy()))
+        sim.close()
+    (s0, f0) = runs[0]
+    assert [r["t"] for r in s0] == list(range(every, steps + 1, every))
+    for series, f in runs[1:]:
+        np.testing.assert_array_equal(f, f0)
+        assert len(series) == len(s0)
+        for a, b in zip(series, s0):
+            assert a["t"] == b["t"]
+            for key in ("mass", "phi", "drho_y", "drho_x", "var_rho", "zeta"):
+                assert a[key] == pytest.approx(b[key], rel=1e-6, abs=1e-6), (key, a[key], b[key])
+
+
 def test_observables_16bit_storage():
     model, d = split_preset("MIPS_PAPER_LITERAL")
     nx, ny = 128, 64
@@ -426,6 +453,38 @@ def test_graphs_on_off_identical(tuning):
     a = gpu_run(model, d, 64, 64, 77, SEED, W.INIT_CONFIG2, graphs=True, sample_every=10, ring=8, tuning=tuning)
     b = gpu_run(model, d, 64, 64, 77, SEED, W.INIT_CONFIG2, graphs=False, sample_every=10, ring=8, tuning=tuning)
     np.testing.assert_array_equal(a, b)
+
+
+def test_parallel_launch_groups_identical():
+    """A batch of several launch groups (models, storages and both lattices)
+    runs its groups as parallel branches, forked from the bound stream and
+    joined before each sample step's finaliser: the states and the sampled
+    records equal those of the same batch launched one group after another
+    (per-launch timing on), with graphs and without."""
+    from paper_1902_00530_gb300 import Lattice, Simulation
+    mips, dm = split_preset("MIPS_RHO1")
+    cil, dc = split_preset("CIL_RHO1")
+    mips7, dm7 = split_preset("MIPS_Q7_RHO1")
+    lats = [Lattice(128, 64, "f32", 0), Lattice(96, 40, "bf16s", 1), Lattice(256, 32, "f32", 2),
+            Lattice(64, 64, "f16s", 3), Lattice(128, 48, "f32", 4, "d2q7")]
+    mods = [mips, cil, cil, mips, mips7]
+    prms = [dm, dc, dc, dm, dm7]
+    specs = [W.INIT_CONFIG1, W.init_ordered(U0_CIL), W.init_ordered(U0_CIL), W.INIT_CONFIG1, W.INIT_CONFIG1]
+    runs = []
+    for graphs, profiling in ((True, False), (False, False), (False, True)):
+        sim = Simulation(lats, mods, prms, sample_every=7, ring_capacity=16)
+        sim.set_graphs(graphs)
+        sim.set_profiling(profiling)
+        sim.init(SEED, specs)
+        sim.step(30)
+        states = [sim.get_state(k, host=True).numpy() for k in range(len(lats))]
+        series = [sim.observable_series(k) for k in range(len(lats))]
+        sim.close()
+        runs.append((states, series))
+    for states, series in runs[1:]:
+        for a, b in zip(states, runs[0][0]):
+            np.testing.assert_array_equal(a, b)
+        assert series == runs[0][1]
 
 
 def test_rotation_equivariance_gpu():
