@@ -15,9 +15,13 @@
  *  - Ownership.  The caller owns all device memory and the CUDA stream: it
  *    allocates the state and scratch buffers whose sizes lbm_buffer_bytes
  *    reports and hands them over with lbm_bind.  The context owns only host
- *    descriptors, tuning results and cached CUDA graphs.  Every call that
- *    launches device work enqueues it on the bound stream; calls documented as
- *    "syncs" wait for that stream before returning.
+ *    descriptors, tuning results, cached CUDA graphs and, for a batch of
+ *    several launch groups (lattices differing in model, storage or velocity
+ *    set), one auxiliary stream per extra group and their events, created on
+ *    the first lbm_step and destroyed by lbm_destroy.  Every call that launches
+ *    device work enqueues it on the bound stream or on work forked from it and
+ *    joined back into it before the call returns; calls documented as "syncs"
+ *    wait for that stream before returning.
  *  - Errors.  Every call returns an lbm_status.  Nothing throws across the ABI
  *    and nothing exits.  lbm_last_error(ctx) describes the last failure.
  *    Device-side conditions (non-finite observables, a barrier that timed out)
