@@ -345,33 +345,36 @@ def secondary_lines(args, wl):
     c4 = W.CONFIG4
     d = W.preset(c4["preset"])
     model = d.pop("model")
-    lats, prms, specs = [], [], []
-    for i, rm in enumerate(c4["rho_means"]):
-        for j, act in enumerate(c4["activities"]):
-            lats.append(Lattice(c4["side"], c4["side"], "f32", i * 16 + j))
-            prms.append(dict(d, B=act))
-            specs.append(dict(c4["init"], rho_mean=rm))
-    sim = Simulation(lats, [model] * len(lats), prms, sample_every=100, ring_capacity=16)
-    sim.init(W.seed(4), specs)
-    out["batch256_cil_f32_glups"] = round(time_sim(sim, len(lats) * c4["side"] ** 2, steps), 2)
-    sim.close()
-    del sim
-    torch.cuda.empty_cache()
-    # ragged batch: 64 lattices, sides from {128..2048}, mixed MIPS/CIL, 16-bit storage
+    for st in ("f32", "f16s"):
+        lats, prms, specs = [], [], []
+        for i, rm in enumerate(c4["rho_means"]):
+            for j, act in enumerate(c4["activities"]):
+                lats.append(Lattice(c4["side"], c4["side"], st, i * 16 + j))
+                prms.append(dict(d, B=act))
+                specs.append(dict(c4["init"], rho_mean=rm))
+        sim = Simulation(lats, [model] * len(lats), prms, sample_every=100, ring_capacity=16)
+        sim.init(W.seed(4), specs)
+        out[f"batch256_cil_{st}_glups"] = round(time_sim(sim, len(lats) * c4["side"] ** 2, steps), 2)
+        sim.close()
+        del sim
+        torch.cuda.empty_cache()
+    # ragged batch: 64 lattices, sides from {128..2048}, mixed MIPS/CIL (two
+    # launch groups, run as parallel graph branches)
     rag = W.ragged_batch()
-    lats, mods, prms, specs = [], [], [], []
-    for k, (side, pname) in enumerate(rag):
-        dd = W.preset(pname)
-        mods.append(dd.pop("model"))
-        prms.append(dd)
-        lats.append(Lattice(side, side, "bf16s", k))
-        specs.append(W.INIT_CONFIG1 if mods[-1] == "mips" else W.INIT_CONFIG2)
-    sim = Simulation(lats, mods, prms, sample_every=100, ring_capacity=16)
-    sim.init(W.seed(5), specs)
-    out["ragged64_bf16s_glups"] = round(time_sim(sim, sum(s * s for s, _ in rag), steps), 2)
-    sim.close()
-    del sim
-    torch.cuda.empty_cache()
+    for st in ("bf16s", "f16s", "f32"):
+        lats, mods, prms, specs = [], [], [], []
+        for k, (side, pname) in enumerate(rag):
+            dd = W.preset(pname)
+            mods.append(dd.pop("model"))
+            prms.append(dd)
+            lats.append(Lattice(side, side, st, k))
+            specs.append(W.INIT_CONFIG1 if mods[-1] == "mips" else W.INIT_CONFIG2)
+        sim = Simulation(lats, mods, prms, sample_every=100, ring_capacity=16)
+        sim.init(W.seed(5), specs)
+        out[f"ragged64_{st}_glups"] = round(time_sim(sim, sum(s * s for s, _ in rag), steps), 2)
+        sim.close()
+        del sim
+        torch.cuda.empty_cache()
     # the paper's own lattice: D2Q7 at the same size and physics (56 B per FP32 update)
     if wl.get("velocity_set", "d2q9") == "d2q9" and wl["nx"] == 8192:
         w7 = workload_spec("mips7_8192")
