@@ -10,9 +10,10 @@
 // ahead of use once every warp has released the buffer ("empty" mbarrier).
 // The half-site column offsets of the brick layout (-1/0 from an even row, 0/+1
 // from an odd one) become shared-memory index offsets; rows are walked in
-// (even, odd) pairs so the parity is a template argument.  The per-site
-// arithmetic is collide7 / negative_correction7 / noise_u7 of lbm_step_q7.cuh,
-// so states are bitwise those of step_kernel_q7.
+// (even, odd) pairs so the parity is a template argument.  As on D2Q9, the
+// MIPS kernel with 16-bit storage converts each staged row once into two FP32
+// rows per warp.  The per-site arithmetic is collide7 / negative_correction7 /
+// noise_u7 of lbm_step_q7.cuh, so states are bitwise those of step_kernel_q7.
 //
 // Requirements (checked on the host): nx a multiple of the 16-byte halo width
 // and at least that wide; rows even.  Every wait is bounded as in the D2Q9

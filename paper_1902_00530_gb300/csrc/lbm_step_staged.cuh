@@ -14,7 +14,10 @@
 // row costs nine copies per block rather than per warp, and the memory
 // latency is hidden without holding rows in registers.  Lanes read their
 // pulled values straight from shared memory, halo included: no shuffles and no
-// lane-divergent edge loads.
+// lane-divergent edge loads.  The MIPS kernel with 16-bit storage converts
+// each staged row once, in its density pass, into two FP32 rows per warp that
+// the update then reads; its staged rows are released a row earlier, so it
+// fetches `stages - 1` rows ahead as well.
 //
 // Requirements (checked on the host): nx a multiple of the 16-byte halo width
 // (4 FP32 / 8 16-bit values) and at least that wide.  Every wait is bounded:
@@ -406,8 +409,8 @@ __global__ void __maxnreg__(staged_max_regs<VEC>()) step_staged_kernel(const Ste
     }
 
     // MIPS: row q+1's densities are taken one row ahead of its update.  With
-    // CONV its pulled populations are converted then too, into the warp's
-    // converted row, so the update reads them from there and the staged row is
+    // CONV its pulled populations are converted then too, into converted row
+    // cv(q+1), so the update reads them from there and the staged row is
     // released one row earlier.
     float rm[VEC + 2], rc[VEC + 2], rn[VEC + 2];
     int q = 0;  // next stage to consume
