@@ -460,25 +460,36 @@ lbm_status ensure_aux(lbm_ctx *c)
 // forked from the bound stream, and the branches join before each finaliser
 // (which reads every lattice's partials) and at the end.  In a captured graph
 // these are parallel branches, so one group's launch fills the other's tail.
+cudaError_t fork_groups(lbm_ctx *c)
+{
+    cudaError_t e = cudaEventRecord(c->aux_ev[0], c->stream);
+    for (size_t i = 0; e == cudaSuccess && i + 1 < c->groups.size(); ++i)
+        e = cudaStreamWaitEvent(c->aux[i], c->aux_ev[0], 0);
+    return e;
+}
+
+cudaError_t join_groups(lbm_ctx *c)
+{
+    cudaError_t e = cudaSuccess;
+    for (size_t i = 0; e == cudaSuccess && i + 1 < c->groups.size(); ++i) {
+        e = cudaEventRecord(c->aux_ev[1 + i], c->aux[i]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->aux_ev[1 + i], 0);
+    }
+    return e;
+}
+
 lbm_status enqueue_steps(lbm_ctx *c, int64_t n, int64_t t0, int p0, int64_t *launches)
 {
     const bool par = c->groups.size() > 1 && !c->profiling && c->aux.size() + 1 >= c->groups.size();
     bool forked = false;
     auto fork = [&]() -> cudaError_t {
-        cudaError_t e = cudaEventRecord(c->aux_ev[0], c->stream);
-        for (size_t i = 0; e == cudaSuccess && i + 1 < c->groups.size(); ++i)
-            e = cudaStreamWaitEvent(c->aux[i], c->aux_ev[0], 0);
+        const cudaError_t e = fork_groups(c);
         forked = e == cudaSuccess;
         return e;
     };
     auto join = [&]() -> cudaError_t {
-        cudaError_t e = cudaSuccess;
-        for (size_t i = 0; e == cudaSuccess && i + 1 < c->groups.size(); ++i) {
-            e = cudaEventRecord(c->aux_ev[1 + i], c->aux[i]);
-            if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->aux_ev[1 + i], 0);
-        }
         forked = false;
-        return e;
+        return join_groups(c);
     };
     for (int64_t k = 0; k < n; ++k) {
         const bool sample = c->sample_every > 0 && ((t0 + k + 1) % c->sample_every == 0);
@@ -543,7 +554,10 @@ struct Shape {
     int vec, rows, warps, stages;
 };
 
-lbm_status tune_group(lbm_ctx *c, GroupHost &g)
+// Times the launch-shape candidates of one group on its own and keeps the
+// fastest; *alt receives the fastest candidate of the other kernel kind
+// (direct or staged), if any, for the joint check of a batch's groups.
+lbm_status tune_group(lbm_ctx *c, GroupHost &g, Shape *alt, bool *has_alt)
 {
     std::vector<Shape> cands;
     long long max_ny = 1;
@@ -579,8 +593,8 @@ lbm_status tune_group(lbm_ctx *c, GroupHost &g)
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0), "create event");
     CK(cudaEventCreate(&e1), "create event");
-    float best = 1e30f;
-    Shape bs{g.vec, g.rows, g.warps, g.stages};
+    float best = 1e30f, best_kind[2] = {1e30f, 1e30f};
+    Shape bs{g.vec, g.rows, g.warps, g.stages}, bk[2] = {bs, bs};
     for (const Shape &sh : cands) {
         g.vec = sh.vec;
         g.rows = sh.rows;
@@ -604,9 +618,17 @@ lbm_status tune_group(lbm_ctx *c, GroupHost &g)
             best = ms;
             bs = sh;
         }
+        const int kind = sh.stages > 0 ? 1 : 0;
+        if (ms < best_kind[kind]) {
+            best_kind[kind] = ms;
+            bk[kind] = sh;
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    const int other = bs.stages > 0 ? 0 : 1;
+    *has_alt = best_kind[other] < 1e29f;
+    *alt = bk[other];
     g.vec = bs.vec;
     g.rows = bs.rows;
     g.warps = bs.warps;
@@ -616,10 +638,77 @@ lbm_status tune_group(lbm_ctx *c, GroupHost &g)
     return read_error_flag(c);
 }
 
+void set_shape(GroupHost &g, const Shape &sh)
+{
+    g.vec = sh.vec;
+    g.rows = sh.rows;
+    g.warps = sh.warps;
+    g.stages = sh.stages;
+}
+
+// One step of every group as lbm_step runs a batch (forked, side by side,
+// joined), repeated: its time in ms.  Writes only the spare buffers.
+lbm_status time_joint_step(lbm_ctx *c, float *ms)
+{
+    lbm_status st = upload_descs(c);
+    if (st != LBM_OK) return st;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0), "create event");
+    CK(cudaEventCreate(&e1), "create event");
+    for (int rep = 0; rep < 4; ++rep) {
+        if (rep == 1) CK(cudaEventRecord(e0, c->stream), "record event");  // the first is a warm-up
+        CK(fork_groups(c), "fork launch groups");
+        for (size_t gi = 0; gi < c->groups.size(); ++gi)
+            CK(launch_group_step(c, c->groups[gi], c->parity, 0, false, gi > 0 ? c->aux[gi - 1] : c->stream),
+               "tuning launch");
+        CK(join_groups(c), "join launch groups");
+    }
+    CK(cudaEventRecord(e1, c->stream), "record event");
+    CK(cudaEventSynchronize(e1), "synchronise event");
+    CK(cudaEventElapsedTime(ms, e0, e1), "event time");
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return LBM_OK;
+}
+
+// Each group's shape is chosen on its own, but a batch runs its groups side by
+// side, where kernels of the two kinds can slow each other (measured on a
+// 64-lattice ragged MIPS/CIL batch: a staged MIPS group beside a direct CIL
+// group ran at 71 GLUPS, slower than the same launches one after the other,
+// 73; both direct, about 79).  So each group's best shape of the other kind
+// is tried in turn with the whole batch running, and kept where the batch
+// step is faster.
 lbm_status do_tune(lbm_ctx *c)
 {
-    for (auto &g : c->groups) {
-        lbm_status st = tune_group(c, g);
+    const size_t ng = c->groups.size();
+    std::vector<Shape> alt(ng);
+    std::vector<char> has_alt(ng, 0);
+    for (size_t gi = 0; gi < ng; ++gi) {
+        bool h = false;
+        lbm_status st = tune_group(c, c->groups[gi], &alt[gi], &h);
+        if (st != LBM_OK) return st;
+        has_alt[gi] = h;
+    }
+    if (ng > 1) {
+        lbm_status st = ensure_aux(c);
+        if (st != LBM_OK) return st;
+        float best = 0.f;
+        st = time_joint_step(c, &best);
+        if (st != LBM_OK) return st;
+        for (size_t gi = 0; gi < ng; ++gi) {
+            if (!has_alt[gi]) continue;
+            GroupHost &g = c->groups[gi];
+            const Shape keep{g.vec, g.rows, g.warps, g.stages};
+            set_shape(g, alt[gi]);
+            float ms = 0.f;
+            st = time_joint_step(c, &ms);
+            if (st != LBM_OK) return st;
+            if (ms < best) best = ms;
+            else set_shape(g, keep);
+        }
+        st = upload_descs(c);
+        if (st != LBM_OK) return st;
+        st = read_error_flag(c);
         if (st != LBM_OK) return st;
     }
     drop_graphs(c);

@@ -458,9 +458,9 @@ def test_graphs_on_off_identical(tuning):
 def test_parallel_launch_groups_identical():
     """A batch of several launch groups (models, storages and both lattices)
     runs its groups as parallel branches, forked from the bound stream and
-    joined before each sample step's finaliser: the states and the sampled
-    records equal those of the same batch launched one group after another
-    (per-launch timing on), with graphs and without."""
+    joined before each sample step's finaliser: the states equal those of the
+    same batch launched one group after another (per-launch timing on), with
+    graphs and without, and so do the sampled records (to FP32 rounding)."""
     from paper_1902_00530_gb300 import Lattice, Simulation
     mips, dm = split_preset("MIPS_RHO1")
     cil, dc = split_preset("CIL_RHO1")
@@ -484,7 +484,14 @@ def test_parallel_launch_groups_identical():
     for states, series in runs[1:]:
         for a, b in zip(states, runs[0][0]):
             np.testing.assert_array_equal(a, b)
-        assert series == runs[0][1]
+        # each run tunes its own shapes (the joint check of the groups may pick
+        # others when timings are close), and a thread's partial sums depend on
+        # the shape: records agree to FP32 rounding
+        for sa, sb in zip(series, runs[0][1]):
+            assert [r["t"] for r in sa] == [r["t"] for r in sb]
+            for ra, rb in zip(sa, sb):
+                for key in ("mass", "phi", "drho_y", "drho_x", "var_rho", "zeta"):
+                    assert ra[key] == pytest.approx(rb[key], rel=1e-6, abs=1e-6), (key, ra[key], rb[key])
 
 
 def test_rotation_equivariance_gpu():
