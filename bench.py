@@ -187,6 +187,16 @@ def workload_spec(name: str):
         d = W.preset("CIL_RHO1")
         return dict(nx=1024, ny=1024, model=d.pop("model"), params=d, init=W.INIT_CONFIG2, sample_every=100,
                     seed=W.seed(2), label="cil_rho1_1024x1024")
+    if name == "batch256":  # 256 CIL lattices of 256^2 on the rho-bar x activity grid, one launch per step
+        c4 = W.CONFIG4
+        d = W.preset(c4["preset"])
+        model = d.pop("model")
+        members = [dict(params=dict(d, B=act), init=dict(c4["init"], rho_mean=rm), lattice_id=i * 16 + j)
+                   for i, rm in enumerate(c4["rho_means"]) for j, act in enumerate(c4["activities"])]
+        mid = members[8 * 16 + 8]  # the grid's centre: the lattice the oracle legs step
+        return dict(nx=c4["side"], ny=c4["side"], model=model, params=mid["params"], init=mid["init"],
+                    lattice_id=mid["lattice_id"], sample_every=100, seed=W.seed(4),
+                    label="cil_rho1_batch256x256x256", members=members)
     if name in ("mips7_8192", "mips7_4096"):  # the paper's D2Q7 lattice, same physics and sizes
         n = 8192 if name == "mips7_8192" else 4096
         d = W.preset("MIPS_Q7_RHO1")
@@ -207,9 +217,13 @@ def run_gpu(args, world, rank, local):
     storage = args.storage
     vs = wl.get("velocity_set", "d2q9")
     q = 7 if vs == "d2q7" else 9
-    sim = Simulation([Lattice(wl["nx"], wl["ny"], storage, rank, vs)], [wl["model"]], [wl["params"]],
+    members = wl.get("members") or [dict(params=wl["params"], init=wl["init"], lattice_id=0)]
+    nlat = len(members)
+    # replicas (one per rank) take disjoint lattice ids
+    lats = [Lattice(wl["nx"], wl["ny"], storage, rank * nlat + m["lattice_id"], vs) for m in members]
+    sim = Simulation(lats, [wl["model"]] * nlat, [m["params"] for m in members],
                      sample_every=wl["sample_every"], ring_capacity=max(16, args.steps // wl["sample_every"] + 4))
-    sim.init(wl["seed"], [wl["init"]])
+    sim.init(wl["seed"], [m["init"] for m in members])
     if args.shape:
         sh = [int(x) for x in args.shape.split(",")]
         sim.set_tuning(1, *sh)
@@ -218,7 +232,7 @@ def run_gpu(args, world, rank, local):
     shape = sim.get_tuning()
     sim.step(args.warmup)
     sim.synchronize()
-    cells = wl["nx"] * wl["ny"]
+    cells = wl["nx"] * wl["ny"] * nlat
 
     # ---------------- timed region: K steps, events on the library's stream --
     sim.set_profiling(True)
@@ -260,28 +274,30 @@ def run_gpu(args, world, rank, local):
                 "frac_of_8TBps": round(achieved / 8000.0, 4)}
 
     # ---------------- end to end through the C ABI with host buffers ---------
-    host_state = sim.get_state(host=True)  # pinned input prepared outside the timed region
-    out_state = torch.empty_like(host_state).pin_memory()
-    state_bytes = host_state.numel() * 4
+    host_state = [sim.get_state(k, host=True) for k in range(nlat)]  # pinned inputs, outside the timed region
+    out_state = [torch.empty_like(h).pin_memory() for h in host_state]
+    state_bytes = sum(h.numel() for h in host_state) * 4
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    sim.set_state(host_state)              # H2D of the populations (returns when the copy is done)
+    for k in range(nlat):
+        sim.set_state(host_state[k], k)    # H2D of the populations (returns when the copy is done)
     t_h2d = time.perf_counter()
     sim.step(args.steps)
     sim.synchronize()
     t_d2h = time.perf_counter()
-    sim.get_state(host=True, out=out_state)  # D2H of the result
+    for k in range(nlat):
+        sim.get_state(k, host=True, out=out_state[k])  # D2H of the result
     t_d2h_end = time.perf_counter()
     obs = sim.observables()                # D2H of the observables (syncs)
     t1 = time.perf_counter()
     e2e_value, _ = aggregate_over_ranks(cells, args.steps, (t1 - t0) * 1e3, world, dist if world > 1 else None)
     e2e = {"value": round(e2e_value, 3), "unit": UNIT,
            "h2d_bytes_per_step": round(state_bytes / args.steps, 1),
-           "d2h_bytes_per_step": round((out_state.numel() * 4 + 56) / args.steps, 1),
+           "d2h_bytes_per_step": round((state_bytes + 56) / args.steps, 1),
            "h2d_gbs": round(state_bytes / (t_h2d - t0) / 1e9, 1),
-           "d2h_gbs": round(out_state.numel() * 4 / (t_d2h_end - t_d2h) / 1e9, 1),
+           "d2h_gbs": round(state_bytes / (t_d2h_end - t_d2h) / 1e9, 1),
            "note": "one upload of the populations, the K steps, one download and the observables: "
                    "the copies are spread over K steps"}
     del out_state, host_state
@@ -293,7 +309,7 @@ def run_gpu(args, world, rank, local):
     if rank == 0 and not args.quick:
         extra = secondary_lines(args, wl)
     return dict(value=value, ms=ms_max, clocks=clocks, roofline=roofline, e2e=e2e, launches=launches,
-                obs=obs, extra=extra, wl=wl, shape=shape)
+                obs=obs, extra=extra, wl=wl, shape=shape, cells=cells, nlat=nlat, q=q)
 
 
 def secondary_lines(args, wl):
@@ -405,12 +421,14 @@ def _oracle_rate(wl, n: int, threads: int, budget_s: float):
     import oracle as O
     init, run = _oracle_pair(wl)
     p = O.params(**wl["params"])
+    n = min(n, wl["nx"], wl["ny"])  # a batch's lattice: the whole (periodic) lattice
     win = (0, 0, wl["nx"], wl["ny"])
-    f = init(n, n, wl["seed"], **wl["init"], prm=p, window=win)
-    f = run(f, wl["model"], p, wl["seed"], 0, 1, window=win, threads=threads)  # load and warm the build
+    lid = wl.get("lattice_id", 0)
+    f = init(n, n, wl["seed"], lattice_id=lid, **wl["init"], prm=p, window=win)
+    f = run(f, wl["model"], p, wl["seed"], 0, 1, lattice_id=lid, window=win, threads=threads)  # load, warm
     steps, t0 = 1, time.perf_counter()
     while time.perf_counter() - t0 < budget_s:
-        f = run(f, wl["model"], p, wl["seed"], steps, 2, window=win, threads=threads)
+        f = run(f, wl["model"], p, wl["seed"], steps, 2, lattice_id=lid, window=win, threads=threads)
         steps += 2
     dt = time.perf_counter() - t0
     return n * n * (steps - 1) / dt, steps - 1, dt
@@ -425,11 +443,12 @@ def cpu_baseline(wl, budget_s: float = 10.0):
     cores = O.host_cores()
     used = O.threads_in_use(cores)
     rn, sn, tn = _oracle_rate(wl, 1024, used, budget_s)
+    nn, n1 = min(1024, wl["nx"], wl["ny"]), min(512, wl["nx"], wl["ny"])
     return {"value": round(rn / 1e9, 6), "unit": UNIT, "cores": used, "kind": "oracle",
-            "sample": f"1024x1024 window of the {wl['label']} workload, {sn} steps, FP64, {used} threads, "
+            "sample": f"{nn}x{nn} window of the {wl['label']} workload, {sn} steps, FP64, {used} threads, "
                       f"{tn:.1f} s",
             "single_thread": {"value": round(r1 / 1e9, 6), "unit": UNIT, "cores": 1,
-                              "sample": f"512x512 window, {s1} steps, FP64, 1 thread, {t1:.1f} s"},
+                              "sample": f"{n1}x{n1} window, {s1} steps, FP64, 1 thread, {t1:.1f} s"},
             "host_cores": cores}
 
 
@@ -443,16 +462,17 @@ def run_reference(args, world, rank):
     wl = workload_spec(args.workload)
     cores = O.host_cores()
     threads = O.threads_in_use(cores)
-    n = 1024
+    n = min(1024, wl["nx"], wl["ny"])
     while n > 64 and n * n * (args.steps + args.warmup) > 2.0e7 * max(threads, 1):
         n //= 2
     init, run = _oracle_pair(wl)
     p = O.params(**wl["params"])
     win = (0, 0, wl["nx"], wl["ny"])
-    f = init(n, n, wl["seed"], **wl["init"], prm=p, window=win)
-    f = run(f, wl["model"], p, wl["seed"], 0, args.warmup, window=win, threads=threads)
+    lid = wl.get("lattice_id", 0)
+    f = init(n, n, wl["seed"], lattice_id=lid, **wl["init"], prm=p, window=win)
+    f = run(f, wl["model"], p, wl["seed"], 0, args.warmup, lattice_id=lid, window=win, threads=threads)
     t0 = time.perf_counter()
-    f = run(f, wl["model"], p, wl["seed"], args.warmup, args.steps, window=win, threads=threads)
+    f = run(f, wl["model"], p, wl["seed"], args.warmup, args.steps, lattice_id=lid, window=win, threads=threads)
     dt = time.perf_counter() - t0
     value = n * n * args.steps / dt / 1e9
     line = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world,
@@ -492,14 +512,19 @@ def main():
     base = None if args.no_cpu_baseline or world > 1 else cpu_baseline(r["wl"])
     clocks = r["clocks"]
     wl = r["wl"]
+    pop_bytes = r["cells"] * r["q"] * (4 if args.storage == "f32" else 2)
     line = {
         "metric": METRIC, "value": round(r["value"], 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(r["ms"] / args.steps, 5), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.storage == "f32" else args.storage,
         "data": "synthetic (seeded lattice, paper-shaped parameters)",
         "config": {"workload": wl["label"] + "_" + args.storage, "nx": wl["nx"], "ny": wl["ny"],
+                   "lattices": r["nlat"],
                    "closure": wl["model"], "storage": args.storage, "sample_every": wl["sample_every"],
-                   "replicas": world, "l2": "inputs larger than L2 (populations 4.8 GB FP32); no flush",
+                   "replicas": world,
+                   "l2": f"inputs larger than L2 (populations {2 * pop_bytes / 1e9:.1f} GB, both buffers, "
+                         f"against 0.13 GB of L2); no flush" if 2 * pop_bytes > 129e6 else
+                         "inputs fit L2: effective, not HBM, rates",
                    "timing": "CUDA events on the library stream around lbm_step(K); per-kernel event pairs",
                    "launch_shape": {"vec": r["shape"][0], "rows": r["shape"][1], "warps": r["shape"][2],
                                     "stages": r["shape"][3],

@@ -41,3 +41,26 @@ def test_reference_arm_under_torchrun_ranks():
     assert r0.returncode == 0, r0.stderr[-2000:]
     d = json.loads([ln for ln in r0.stdout.splitlines() if ln.startswith("{")][-1])
     assert d["impl"] == "reference" and d["n_gpus"] == 2
+
+
+def test_batch_workload_spec_and_oracle_legs():
+    """The 256-lattice CIL batch as a benchmark workload: 256 members on the
+    rho-bar x activity grid with distinct lattice ids; the oracle legs (the
+    reference arm and the CPU baseline) step its centre lattice whole."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import workloads as W
+    wl = bench.workload_spec("batch256")
+    ms = wl["members"]
+    assert len(ms) == 256 and len({m["lattice_id"] for m in ms}) == 256
+    assert wl["nx"] == wl["ny"] == W.CONFIG4["side"]
+    assert sorted({m["init"]["rho_mean"] for m in ms}) == sorted(W.CONFIG4["rho_means"])
+    assert sorted({m["params"]["B"] for m in ms}) == sorted(W.CONFIG4["activities"])
+    assert wl["lattice_id"] == 136 and wl["params"]["B"] == W.CONFIG4["activities"][8]
+    rate, steps, dt = bench._oracle_rate(wl, 1024, 1, 0.05)
+    assert rate > 0 and steps >= 1
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--workload", "batch256", "--steps", "1",
+                        "--warmup", "3"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    d = json.loads([ln for ln in r.stdout.splitlines() if ln.startswith("{")][0])
+    assert d["config"]["workload"] == "cil_rho1_batch256x256x256" and "256x256" in d["config"]["sample"]
