@@ -554,6 +554,21 @@ struct Shape {
     int vec, rows, warps, stages;
 };
 
+// A pair of timing events, destroyed on every way out of the tuner.
+struct EventPair {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t create()
+    {
+        cudaError_t e = cudaEventCreate(&e0);
+        return e == cudaSuccess ? cudaEventCreate(&e1) : e;
+    }
+    ~EventPair()
+    {
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    }
+};
+
 // Times the launch-shape candidates of one group on its own and keeps the
 // fastest; *alt receives the fastest candidate of the other kernel kind
 // (direct or staged), if any, for the joint check of a batch's groups.
@@ -590,9 +605,9 @@ lbm_status tune_group(lbm_ctx *c, GroupHost &g, Shape *alt, bool *has_alt)
             }
         }
     }
-    cudaEvent_t e0, e1;
-    CK(cudaEventCreate(&e0), "create event");
-    CK(cudaEventCreate(&e1), "create event");
+    EventPair ev;
+    CK(ev.create(), "create event");
+    cudaEvent_t e0 = ev.e0, e1 = ev.e1;
     float best = 1e30f, best_kind[2] = {1e30f, 1e30f};
     Shape bs{g.vec, g.rows, g.warps, g.stages}, bk[2] = {bs, bs};
     for (const Shape &sh : cands) {
@@ -624,8 +639,6 @@ lbm_status tune_group(lbm_ctx *c, GroupHost &g, Shape *alt, bool *has_alt)
             bk[kind] = sh;
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     const int other = bs.stages > 0 ? 0 : 1;
     *has_alt = best_kind[other] < 1e29f;
     *alt = bk[other];
@@ -652,9 +665,9 @@ lbm_status time_joint_step(lbm_ctx *c, float *ms)
 {
     lbm_status st = upload_descs(c);
     if (st != LBM_OK) return st;
-    cudaEvent_t e0, e1;
-    CK(cudaEventCreate(&e0), "create event");
-    CK(cudaEventCreate(&e1), "create event");
+    EventPair ev;
+    CK(ev.create(), "create event");
+    cudaEvent_t e0 = ev.e0, e1 = ev.e1;
     for (int rep = 0; rep < 4; ++rep) {
         if (rep == 1) CK(cudaEventRecord(e0, c->stream), "record event");  // the first is a warm-up
         CK(fork_groups(c), "fork launch groups");
@@ -666,8 +679,6 @@ lbm_status time_joint_step(lbm_ctx *c, float *ms)
     CK(cudaEventRecord(e1, c->stream), "record event");
     CK(cudaEventSynchronize(e1), "synchronise event");
     CK(cudaEventElapsedTime(ms, e0, e1), "event time");
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     return LBM_OK;
 }
 
