@@ -249,6 +249,30 @@ lbm_status lbm_get_tuning(const lbm_ctx *ctx, int32_t lattice, int32_t *vec, int
  * and replay it (default), 0 = launch kernels directly. */
 lbm_status lbm_set_graphs(lbm_ctx *ctx, int32_t enabled);
 
+/* Persistent launches (the paper's many independent runs per parameter point,
+ * App. C.3-C.4, advanced together; each step is App. A.2's update, unchanged).
+ * enabled = 1: every launch group on the direct D2Q9 kernel (stages = 0 in
+ * lbm_get_tuning) runs each stretch of two or more consecutive steps without a
+ * sample step as ONE kernel launch, of at most 4096 steps (fewer for very
+ * large groups, so that steps x blocks stays below 2^31); sample steps, staged
+ * groups and D2Q7 groups launch once per step as before.  Inside the launch,
+ * blocks take (step, block) work items from a counter, lattice group by
+ * lattice group (consecutive lattices whose two population buffers together
+ * fit l2_group_mib MiB; 0 = the default of 64, at least one lattice per
+ * group) and step by step inside a group, and each item waits only for the
+ * strip rows it reads to finish the previous step: the populations of a
+ * lattice group stay in L2 across its steps, and steps overlap with no barrier
+ * between them.  States, samples and observables are bitwise those of the
+ * per-step launches.  The waits are bounded (about 1 s, then the error flag is
+ * raised and the call that reads it returns LBM_ERR_TIMEOUT).  Each launch
+ * clears its counters in the context's scratch first (a memset on the bound
+ * stream, a graph node when graphs are on), so launches of one context must
+ * not overlap on the GPU, as for every other call.  enabled = 0 (default):
+ * one launch per step.  l2_group_mib outside [0, 2^20] gives
+ * LBM_ERR_INVALID_ARG.  Host only; drops captured graphs and re-uploads
+ * descriptors (syncs) when bound. */
+lbm_status lbm_set_persistent(lbm_ctx *ctx, int32_t enabled, int32_t l2_group_mib);
+
 /* Number of kernels the last lbm_step call enqueued (graph nodes included). */
 lbm_status lbm_last_launch_count(const lbm_ctx *ctx, int64_t *count);
 

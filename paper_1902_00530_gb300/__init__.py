@@ -224,6 +224,12 @@ class Simulation:
     def set_graphs(self, enabled: bool) -> None:
         self._check(self.lib.lbm_set_graphs(self.ctx, 1 if enabled else 0))
 
+    def set_persistent(self, enabled: bool, l2_group_mib: int = 0) -> None:
+        """Run stretches of steps without a sample step as one persistent launch
+        per launch group on the direct D2Q9 kernel (lattice groups of
+        l2_group_mib MiB of populations; 0 = the library default)."""
+        self._check(self.lib.lbm_set_persistent(self.ctx, 1 if enabled else 0, int(l2_group_mib)))
+
     def last_launch_count(self) -> int:
         c = ctypes.c_int64()
         self._check(self.lib.lbm_last_launch_count(self.ctx, ctypes.byref(c)))

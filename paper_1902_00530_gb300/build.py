@@ -19,8 +19,8 @@ ROOT = os.path.dirname(HERE)
 LIB = os.path.join(BUILD, "liblbm.so")
 UNITS = ["lbm_step_f32.cu", "lbm_step_f16.cu", "lbm_step_bf16.cu", "lbm_step_q7_f32.cu", "lbm_step_q7_f16.cu",
          "lbm_step_q7_bf16.cu", "lbm_aux.cu", "lbm_api.cu", "lbm_noalloc.cu"]
-HEADERS = ["lbm_device.cuh", "lbm_step.cuh", "lbm_step_staged.cuh", "lbm_step_q7.cuh", "lbm_step_q7_staged.cuh",
-           "lbm_internal.h"]
+HEADERS = ["lbm_device.cuh", "lbm_step.cuh", "lbm_step_staged.cuh", "lbm_step_persistent.cuh", "lbm_step_q7.cuh",
+           "lbm_step_q7_staged.cuh", "lbm_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"] + \
     os.environ.get("LBM_NVCC_EXTRA", "").split()

@@ -4,8 +4,10 @@
 // buffers and scratch) belongs to the caller.  Scratch layout (256-byte
 // aligned regions): control words (step counter t, error flag), per-lattice
 // counters, descriptor tables (all lattices, then one table per launch group),
-// initial-state specs, and per lattice the reduction partials, the finaliser
-// partials, the observable ring and the on-demand record.
+// per launch group the persistent launch's work counter, strip-row progress
+// counters and lattice-group table, initial-state specs, and per lattice the
+// reduction partials, the finaliser partials, the observable ring and the
+// on-demand record.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -28,6 +30,8 @@ constexpr int ROWS_MIN = 8;        // smallest strip height; scratch is sized fo
 constexpr int CHUNK_COLS = 256;    // columns / rows / strips per finaliser block
 constexpr int NCHUNK_MAX = 1024;
 constexpr int GRAPH_CHUNK_MAX = 256;
+constexpr int PERSIST_STEPS_MAX = 4096;  // steps of one persistent launch
+constexpr int PERSIST_L2_MIB_DEFAULT = 64;  // population bytes of a lattice group stepped together
 
 size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
@@ -44,6 +48,7 @@ struct LatHost {
     size_t scal_off = 0, colp_off = 0, rowp_off = 0, finp_off = 0, ring_off = 0, now_off = 0, ctr_off = 0;
     int nsx = 0, nsy = 0, nchunk = 1, nchunk_max = 1;
     int group = 0, block_begin = 0;
+    int prog_off = 0;  // first strip-row progress counter in its group's persistent region
     int64_t consumed = 0;
 };
 
@@ -53,6 +58,10 @@ struct GroupHost {
     int vec = 1, rows = 32, warps = 4, blocks = 0;
     int stages = 0;  // 0: direct-load kernel; >= 2: TMA-staged kernel with that many row buffers
     size_t desc_off = 0;
+    // persistent launch: work counter, then progress counters (persist_bytes
+    // in all, zeroed before each launch); lattice-group table at pg_off
+    size_t persist_off = 0, persist_bytes = 0, pg_off = 0;
+    int npg = 0;
 };
 
 struct GraphKey {
@@ -87,7 +96,15 @@ struct lbm_ctx {
     // kernel timing (lbm_set_profiling)
     bool profiling = false;
     std::vector<cudaEvent_t> ev_pool;
-    std::vector<std::pair<int, bool>> ev_marks;  // (first event index, is step kernel)
+    struct ProfMark {
+        int ev;         // first event of the pair
+        bool step;      // a fused step kernel
+        int64_t steps;  // steps it ran (a persistent launch runs several)
+    };
+    std::vector<ProfMark> ev_marks;
+    // persistent launches (lbm_set_persistent)
+    bool persistent = false;
+    int persist_l2_mib = PERSIST_L2_MIB_DEFAULT;
     size_t ev_used = 0;
     // launch groups after the first run on their own streams, forked from and
     // joined back into the bound stream (parallel branches of the step graph)
@@ -225,6 +242,20 @@ void layout(lbm_ctx *c)
         g.desc_off = o;
         o = align256(o + g.members.size() * sizeof(LatDesc));
     }
+    for (auto &g : c->groups) {
+        // the work counter in a slot of its own, then the progress counters of
+        // every strip row at the smallest strip height
+        g.persist_off = o;
+        size_t nctr = 0;
+        for (int m : g.members) {
+            c->lats[m].prog_off = (int)nctr;
+            nctr += (size_t)ceil_div(c->lats[m].lat.ny, ROWS_MIN);
+        }
+        g.persist_bytes = 256 + nctr * sizeof(unsigned);
+        o = align256(o + g.persist_bytes);
+        g.pg_off = o;
+        o = align256(o + (g.members.size() + 1) * sizeof(int));
+    }
     c->spec_off = o;
     o = align256(o + nl * init_spec_bytes());
     for (auto &L : c->lats) {
@@ -285,6 +316,7 @@ LatDesc make_desc(const lbm_ctx *c, const LatHost &L, int block_begin, const Gro
     d.block_begin = block_begin;
     d.ring_cap = std::max(c->ring_cap, 1);
     d.q = L.q;
+    d.prog_off = L.prog_off;
     const long long nstrip = (long long)d.nsx * d.nsy;
     d.nchunk = std::min(L.nchunk_max, std::max(1, ceil_div(std::max<long long>({L.lat.nx, L.lat.ny, nstrip}), CHUNK_COLS)));
     // 1/tau in FP32 such that 1 - 1/tau is exact too (the noisy update weighs f*
@@ -338,6 +370,25 @@ lbm_status upload_descs(lbm_ctx *c)
         CK(cudaMemcpyAsync(c->scratch + g.desc_off, gd.data(), gd.size() * sizeof(LatDesc),
                            cudaMemcpyHostToDevice, c->stream),
            "upload group descriptors");
+        // lattice groups of the persistent launch: consecutive members whose
+        // two population buffers each fit the L2 budget together (at least one
+        // lattice per group); entry i is the group's first block of the step grid
+        std::vector<int> pg;
+        const size_t budget = (size_t)c->persist_l2_mib << 20;
+        size_t bytes = 0;
+        for (int m : g.members) {
+            const LatHost &L = c->lats[m];
+            if (pg.empty() || bytes + 2 * L.buf_bytes > budget) {
+                pg.push_back(L.block_begin);
+                bytes = 0;
+            }
+            bytes += 2 * L.buf_bytes;
+        }
+        g.npg = (int)pg.size();
+        pg.push_back(blocks);
+        CK(cudaMemcpyAsync(c->scratch + g.pg_off, pg.data(), pg.size() * sizeof(int), cudaMemcpyHostToDevice,
+                           c->stream),
+           "upload lattice groups");
     }
     CK(cudaMemcpyAsync(c->scratch + c->all_desc_off, all.data(), all.size() * sizeof(LatDesc),
                        cudaMemcpyHostToDevice, c->stream),
@@ -353,8 +404,7 @@ const LatDesc *all_desc(const lbm_ctx *c)
 uint32_t *t_dev(const lbm_ctx *c) { return reinterpret_cast<uint32_t *>(c->scratch); }
 unsigned *err_dev(const lbm_ctx *c) { return reinterpret_cast<unsigned *>(c->scratch + 4); }
 
-cudaError_t launch_group_step(const lbm_ctx *c, const GroupHost &g, int src, uint32_t k, bool sample,
-                              cudaStream_t stream)
+StepArgs step_args(const lbm_ctx *c, const GroupHost &g, int src, uint32_t k)
 {
     StepArgs a;
     a.desc = reinterpret_cast<const LatDesc *>(c->scratch + g.desc_off);
@@ -370,10 +420,23 @@ cudaError_t launch_group_step(const lbm_ctx *c, const GroupHost &g, int src, uin
         a.rk[2 * r] = a.key0 + (uint32_t)r * 0x9E3779B9u;
         a.rk[2 * r + 1] = a.key1 + (uint32_t)r * 0xBB67AE85u;
     }
-    // noise form of the launch: compile-time when the group is uniform in sigma
+    return a;
+}
+
+// Noise form of a group's launches: compile-time when the group is uniform in
+// sigma (0: none, 1: all), else decided per lattice (2).
+int group_noise(const lbm_ctx *c, const GroupHost &g)
+{
     int with = 0;
     for (int m : g.members) with += (float)(2.0 * c->lats[m].p.sigma) > 0.f ? 1 : 0;  // as the kernel sees sigma_q
-    const int noise = with == 0 ? 0 : (with == (int)g.members.size() ? 1 : 2);
+    return with == 0 ? 0 : (with == (int)g.members.size() ? 1 : 2);
+}
+
+cudaError_t launch_group_step(const lbm_ctx *c, const GroupHost &g, int src, uint32_t k, bool sample,
+                              cudaStream_t stream)
+{
+    const StepArgs a = step_args(c, g, src, k);
+    const int noise = group_noise(c, g);
     const int kind = g.stages > 0 ? 1 : 0;
     if (g.q == 7) {
         if (g.storage == LBM_F32)
@@ -387,6 +450,36 @@ cudaError_t launch_group_step(const lbm_ctx *c, const GroupHost &g, int src, uin
     if (g.storage == LBM_F16_SHIFTED)
         return launch_step_f16(g.model, kind, g.vec, sample, noise, a, g.blocks, g.warps, stream);
     return launch_step_bf16(g.model, kind, g.vec, sample, noise, a, g.blocks, g.warps, stream);
+}
+
+// Groups the persistent launch takes: D2Q9 on the direct kernel.
+bool persistent_ok(const lbm_ctx *c, const GroupHost &g) { return c->persistent && g.stages == 0 && g.q == 9; }
+
+// Most steps one persistent launch of the group may run (its items stay below 2^31).
+int64_t persist_steps_max(const GroupHost &g)
+{
+    return std::max<int64_t>(1, std::min<int64_t>(PERSIST_STEPS_MAX, ((int64_t(1) << 31) - 1) / std::max(1, g.blocks)));
+}
+
+// m steps k .. k+m-1 of group g in one persistent launch: clear its counters,
+// then launch.
+cudaError_t launch_group_persistent(const lbm_ctx *c, const GroupHost &g, int src, uint32_t k, int64_t m,
+                                    cudaStream_t stream)
+{
+    const StepArgs a = step_args(c, g, src, k);
+    PersistArgs p;
+    p.work = reinterpret_cast<unsigned *>(c->scratch + g.persist_off);
+    p.prog = p.work + 256 / sizeof(unsigned);
+    p.pg = reinterpret_cast<const int *>(c->scratch + g.pg_off);
+    p.npg = g.npg;
+    p.nsteps = (int)m;
+    cudaError_t e = cudaMemsetAsync(c->scratch + g.persist_off, 0, g.persist_bytes, stream);
+    if (e != cudaSuccess) return e;
+    const int noise = group_noise(c, g);
+    if (g.storage == LBM_F32) return launch_persistent_f32(g.model, g.vec, noise, a, p, g.blocks, g.warps, stream);
+    if (g.storage == LBM_F16_SHIFTED)
+        return launch_persistent_f16(g.model, g.vec, noise, a, p, g.blocks, g.warps, stream);
+    return launch_persistent_bf16(g.model, g.vec, noise, a, p, g.blocks, g.warps, stream);
 }
 
 cudaError_t launch_group_observe(const lbm_ctx *c, const GroupHost &g, int src)
@@ -412,7 +505,7 @@ cudaError_t launch_group_observe(const lbm_ctx *c, const GroupHost &g, int src)
 }
 
 // Kernel timing: an event pair around a launch when profiling is on.
-cudaError_t prof_begin(lbm_ctx *c, bool is_step)
+cudaError_t prof_begin(lbm_ctx *c, bool is_step, int64_t steps = 1)
 {
     if (!c->profiling) return cudaSuccess;
     while (c->ev_pool.size() < c->ev_used + 2) {
@@ -421,7 +514,7 @@ cudaError_t prof_begin(lbm_ctx *c, bool is_step)
         if (err != cudaSuccess) return err;
         c->ev_pool.push_back(e);
     }
-    c->ev_marks.push_back({(int)c->ev_used, is_step});
+    c->ev_marks.push_back({(int)c->ev_used, is_step, steps});
     cudaError_t err = cudaEventRecord(c->ev_pool[c->ev_used], c->stream);
     c->ev_used += 2;
     return err;
@@ -430,7 +523,7 @@ cudaError_t prof_begin(lbm_ctx *c, bool is_step)
 cudaError_t prof_end(lbm_ctx *c)
 {
     if (!c->profiling) return cudaSuccess;
-    return cudaEventRecord(c->ev_pool[c->ev_marks.back().first + 1], c->stream);
+    return cudaEventRecord(c->ev_pool[c->ev_marks.back().ev + 1], c->stream);
 }
 
 // Enqueue n steps starting at host time t0 from buffer parity p0.
@@ -478,6 +571,12 @@ cudaError_t join_groups(lbm_ctx *c)
     return e;
 }
 
+// Enqueue n steps starting at host time t0 from buffer parity p0.  The steps
+// fall into runs without a sample step, each followed by its sample step (if
+// it lies within the n).  Per run, every group steps on its own stream (see
+// fork_groups): a group the persistent launch takes runs as few launches as its
+// step limit allows, any other launches once per step.  Then the sample step
+// of every group, the join, and the finaliser.
 lbm_status enqueue_steps(lbm_ctx *c, int64_t n, int64_t t0, int p0, int64_t *launches)
 {
     const bool par = c->groups.size() > 1 && !c->profiling && c->aux.size() + 1 >= c->groups.size();
@@ -491,27 +590,50 @@ lbm_status enqueue_steps(lbm_ctx *c, int64_t n, int64_t t0, int p0, int64_t *lau
         forked = false;
         return join_groups(c);
     };
-    for (int64_t k = 0; k < n; ++k) {
-        const bool sample = c->sample_every > 0 && ((t0 + k + 1) % c->sample_every == 0);
+    auto stream_of = [&](size_t gi) { return par && gi > 0 ? c->aux[gi - 1] : c->stream; };
+    int64_t k = 0;
+    while (k < n) {
+        // steps k .. e-1 have no sample step; step e is one (if e < n)
+        int64_t e = n;
+        if (c->sample_every > 0) {
+            const int64_t r = (t0 + k + 1) % c->sample_every;
+            e = std::min(n, k + (r == 0 ? 0 : c->sample_every - r));
+        }
         if (par && !forked) CK(fork(), "fork launch groups");
         for (size_t gi = 0; gi < c->groups.size(); ++gi) {
             const GroupHost &g = c->groups[gi];
-            CK(prof_begin(c, true), "record event");
-            CK(launch_group_step(c, g, (int)((p0 + k) & 1), (uint32_t)k, sample,
-                                 par && gi > 0 ? c->aux[gi - 1] : c->stream),
-               "launch step kernel");
-            CK(prof_end(c), "record event");
-            ++*launches;
+            const int64_t mmax = persistent_ok(c, g) ? persist_steps_max(g) : 1;
+            for (int64_t kk = k; kk < e;) {
+                const int64_t m = std::min(e - kk, mmax);
+                CK(prof_begin(c, true, m), "record event");
+                if (m >= 2)
+                    CK(launch_group_persistent(c, g, (int)((p0 + kk) & 1), (uint32_t)kk, m, stream_of(gi)),
+                       "launch persistent step kernel");
+                else
+                    CK(launch_group_step(c, g, (int)((p0 + kk) & 1), (uint32_t)kk, false, stream_of(gi)),
+                       "launch step kernel");
+                CK(prof_end(c), "record event");
+                ++*launches;
+                kk += m;
+            }
         }
-        if (sample) {
+        if (e < n) {
+            for (size_t gi = 0; gi < c->groups.size(); ++gi) {
+                CK(prof_begin(c, true), "record event");
+                CK(launch_group_step(c, c->groups[gi], (int)((p0 + e) & 1), (uint32_t)e, true, stream_of(gi)),
+                   "launch step kernel");
+                CK(prof_end(c), "record event");
+                ++*launches;
+            }
             if (par) CK(join(), "join launch groups");
             CK(prof_begin(c, false), "record event");
-            CK(launch_finalize(all_desc(c), (int)c->lats.size(), c->max_chunk, t_dev(c), (uint32_t)k, 1,
+            CK(launch_finalize(all_desc(c), (int)c->lats.size(), c->max_chunk, t_dev(c), (uint32_t)e, 1,
                                err_dev(c), c->stream),
                "launch finaliser");
             CK(prof_end(c), "record event");
             ++*launches;
         }
+        k = e + 1;
     }
     if (forked) CK(join(), "join launch groups");
     CK(prof_begin(c, false), "record event");
@@ -1320,6 +1442,18 @@ lbm_status lbm_set_graphs(lbm_ctx *c, int32_t enabled)
     return LBM_OK;
 }
 
+lbm_status lbm_set_persistent(lbm_ctx *c, int32_t enabled, int32_t l2_group_mib)
+{
+    if (!c) return LBM_ERR_INVALID_ARG;
+    if (l2_group_mib < 0 || l2_group_mib > (1 << 20))
+        return fail(c, LBM_ERR_INVALID_ARG, "l2_group_mib must be in [0, 2^20]");
+    c->persistent = enabled != 0;
+    c->persist_l2_mib = l2_group_mib > 0 ? l2_group_mib : PERSIST_L2_MIB_DEFAULT;
+    drop_graphs(c);
+    if (c->bound) return upload_descs(c);
+    return LBM_OK;
+}
+
 lbm_status lbm_last_launch_count(const lbm_ctx *c, int64_t *count)
 {
     if (!c || !count) return LBM_ERR_INVALID_ARG;
@@ -1343,13 +1477,13 @@ lbm_status lbm_profile_read(lbm_ctx *c, double *step_ms, int64_t *step_launches,
     *other_ms = 0.0;
     *step_launches = 0;
     if (!c->ev_marks.empty()) {
-        CK(cudaEventSynchronize(c->ev_pool[c->ev_marks.back().first + 1]), "synchronise event");
+        CK(cudaEventSynchronize(c->ev_pool[c->ev_marks.back().ev + 1]), "synchronise event");
         for (const auto &m : c->ev_marks) {
             float ms = 0.f;
-            CK(cudaEventElapsedTime(&ms, c->ev_pool[m.first], c->ev_pool[m.first + 1]), "event time");
-            if (m.second) {
+            CK(cudaEventElapsedTime(&ms, c->ev_pool[m.ev], c->ev_pool[m.ev + 1]), "event time");
+            if (m.step) {
                 *step_ms += ms;
-                ++*step_launches;
+                *step_launches += m.steps;
             } else {
                 *other_ms += ms;
             }

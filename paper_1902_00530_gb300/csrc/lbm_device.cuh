@@ -67,7 +67,7 @@ struct LatDesc {
     int nsx, nsy, rows, block_begin;
     int ring_cap, nchunk;
     int q;               // populations per site: 9 (D2Q9) or 7 (D2Q7)
-    int pad1;
+    int prog_off;        // persistent launch: index of this lattice's first strip-row progress counter
     float omega;         // 1/tau
     float sigma_q;       // 2 sigma: noise scale of u in [1, 2) (0 = no noise)
     float C, inv_rho_star, rho_star, u_max, u_max2, A, B;
@@ -141,6 +141,16 @@ struct StepArgs {
     int stages;           // staged kernel: shared-memory row buffers per warp
     unsigned *err;        // device error word (bounded waits report here)
     uint32_t rk[20];      // Philox round keys: (key0 + r W0, key1 + r W1), r = 0..9
+};
+
+// The persistent launch's work list (lbm_step_persistent.cuh): items are the
+// blocks of the per-step grid, one per step, taken in order by a counter.
+struct PersistArgs {
+    unsigned *work;  // item counter, zero at launch
+    unsigned *prog;  // strips finished per strip row (summed over the launch), zero at launch
+    const int *pg;   // first block of each lattice group; pg[npg] = blocks of the step grid
+    int npg;         // lattice groups
+    int nsteps;      // steps of the launch: items = nsteps * pg[npg] < 2^31 (host check)
 };
 
 // ---------------------------------------------------------------------------

@@ -629,15 +629,15 @@ template <int MODEL, int ST, int VEC, bool SAMPLE> constexpr int direct_min_bloc
     return MODEL == MODEL_MIPS ? 2 : 3;
 }
 
+// One warp's strip s (< nsx nsy) of lattice dp for the step at time t, read
+// from buffer `src` and written to the other: the body of the direct kernel,
+// shared by the per-step launch and the persistent launch.
 template <int MODEL, int ST, int VEC, bool SAMPLE, int NOISE>
-__global__ void __launch_bounds__(256, direct_min_blocks<MODEL, ST, VEC, SAMPLE>()) step_kernel(const StepArgs a)
+__device__ __forceinline__ void direct_strip(const StepArgs &a, const LatDesc *dp, int s, int src_buf, uint32_t t)
 {
     using T = typename Store<ST>::T;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const LatDesc *dp = a.desc + find_lattice(a.desc, a.nlat, blockIdx.x);
-    const int nsx = dp->nsx, nsy = dp->nsy;
-    const int s = (blockIdx.x - dp->block_begin) * (blockDim.x >> 5) + warp;
-    if (s >= nsx * nsy) return;  // whole warp leaves together
+    const int lane = threadIdx.x & 31;
+    const int nsx = dp->nsx;
     const int nx = dp->nx, ny = dp->ny, pitch = dp->pitch, rows = dp->rows;
     const SiteParams d = load_params(dp);
     const int sx = s % nsx, sy = s / nsx;
@@ -649,11 +649,10 @@ __global__ void __launch_bounds__(256, direct_min_blocks<MODEL, ST, VEC, SAMPLE>
     const uint32_t plane32 = (uint32_t)plane;  // q ny pitch <= 2^32 (host check) where used
     // 64-bit pointer steps only in the copy-bound noise-free kernels (see pull_pop_wide)
     constexpr bool WIDE = MODEL != MODEL_MIPS && NOISE == 0 && !SAMPLE;
-    const T *src = reinterpret_cast<const T *>(dp->f[a.src]);
-    T *dst = reinterpret_cast<T *>(dp->f[a.src ^ 1]);
+    const T *src = reinterpret_cast<const T *>(dp->f[src_buf]);
+    T *dst = reinterpret_cast<T *>(dp->f[src_buf ^ 1]);
     const Shift3 sh = load_shift(dp);
     const uint32_t id = (uint32_t)dp->id;
-    const uint32_t t = *a.t_ptr + a.k;
     const bool noise = NOISE == 2 ? d.sigma_q > 0.f : NOISE == 1;
 
     double col[VEC], acc[5];
@@ -745,6 +744,15 @@ __global__ void __launch_bounds__(256, direct_min_blocks<MODEL, ST, VEC, SAMPLE>
         }
     }
     if constexpr (SAMPLE) observe_flush<VEC>(dp->colp, dp->scal, nx, s, sy, x0, valid, col, acc, lane);
+}
+
+template <int MODEL, int ST, int VEC, bool SAMPLE, int NOISE>
+__global__ void __launch_bounds__(256, direct_min_blocks<MODEL, ST, VEC, SAMPLE>()) step_kernel(const StepArgs a)
+{
+    const LatDesc *dp = a.desc + find_lattice(a.desc, a.nlat, blockIdx.x);
+    const int s = (blockIdx.x - dp->block_begin) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (s >= dp->nsx * dp->nsy) return;  // whole warp leaves together
+    direct_strip<MODEL, ST, VEC, SAMPLE, NOISE>(a, dp, s, a.src, *a.t_ptr + a.k);
 }
 
 // Observable partials of the stored state without stepping (same strip

@@ -1,5 +1,8 @@
-// lbm_step_f32.cu -- fused step and observe kernels for f32 population storage.
+// lbm_step_f32.cu -- fused step (per-step and persistent launches) and observe kernels
+// for f32 population storage.
 #include "lbm_internal.h"
 #include "lbm_step_staged.cuh"
+#include "lbm_step_persistent.cuh"
 
 LBM_INSTANTIATE_STORAGE(lbm::ST_F32, f32)
+LBM_INSTANTIATE_PERSISTENT(lbm::ST_F32, f32)

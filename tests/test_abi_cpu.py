@@ -91,6 +91,11 @@ def test_host_only_calls_and_status_codes(lib):
     t = ctypes.c_int64(-1)
     assert lib.lbm_get_time(ctx, ctypes.byref(t)) == 0 and t.value == 0
     assert lib.lbm_check_wait_timeout(ctx) == 2            # the failure-path check needs bound buffers
+    assert lib.lbm_set_persistent(None, 1, 0) == 1
+    assert lib.lbm_set_persistent(ctx, 1, -1) == 1         # lattice-group budget out of range
+    assert lib.lbm_set_persistent(ctx, 1, (1 << 20) + 1) == 1
+    assert lib.lbm_set_persistent(ctx, 1, 0) == 0          # host only before binding
+    assert lib.lbm_set_persistent(ctx, 0, 16) == 0
     assert lib.lbm_bind(ctx, None, None, None) == 1
     assert lib.lbm_bind(ctx, ctypes.c_void_p(0x1001), ctypes.c_void_p(0x2000), None) == 1  # misaligned
     lib.lbm_destroy(ctx)
