@@ -230,6 +230,7 @@ def run_gpu(args, world, rank, local):
     else:
         sim.tune()
     shape = sim.get_tuning()
+    persistent = sim.get_persistent()
     sim.step(args.warmup)
     sim.synchronize()
     cells = wl["nx"] * wl["ny"] * nlat
@@ -268,7 +269,8 @@ def run_gpu(args, world, rank, local):
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic, "peak_source": peak_kind,
                 "algorithmic_bytes_per_launch": bytes_per_update(storage, q) * cells,
-                "kernel": ("lbm::step_staged_kernel" if sim.get_tuning()[3] > 0 else "lbm::step_kernel") +
+                "kernel": ("lbm::step_staged_kernel" if shape[3] > 0 else
+                           "lbm::step_persistent_kernel" if persistent else "lbm::step_kernel") +
                           ("_q7" if q == 7 else ""), "avg_launch_ms": round(step_avg_ms, 5),
                 "step_kernel_share": round(prof["step_ms"] / max(prof["step_ms"] + prof["other_ms"], 1e-9), 4),
                 "frac_of_8TBps": round(achieved / 8000.0, 4)}
@@ -309,7 +311,7 @@ def run_gpu(args, world, rank, local):
     if rank == 0 and not args.quick:
         extra = secondary_lines(args, wl)
     return dict(value=value, ms=ms_max, clocks=clocks, roofline=roofline, e2e=e2e, launches=launches,
-                obs=obs, extra=extra, wl=wl, shape=shape, cells=cells, nlat=nlat, q=q)
+                obs=obs, extra=extra, wl=wl, shape=shape, persistent=persistent, cells=cells, nlat=nlat, q=q)
 
 
 def secondary_lines(args, wl):
@@ -529,6 +531,8 @@ def main():
                    "launch_shape": {"vec": r["shape"][0], "rows": r["shape"][1], "warps": r["shape"][2],
                                     "stages": r["shape"][3],
                                     "kernel": "staged (bulk-copy rows in shared memory)" if r["shape"][3]
+                                    else "persistent (direct-kernel steps, one launch per stretch of steps "
+                                         "between samples)" if r["persistent"]
                                     else "direct (vector loads + shuffles)",
                                     "chosen_by": "fixed" if args.shape else "tuner"}},
         "gpu_launches": r["launches"],

@@ -251,27 +251,42 @@ lbm_status lbm_set_graphs(lbm_ctx *ctx, int32_t enabled);
 
 /* Persistent launches (the paper's many independent runs per parameter point,
  * App. C.3-C.4, advanced together; each step is App. A.2's update, unchanged).
- * enabled = 1: every launch group on the direct D2Q9 kernel (stages = 0 in
+ * A launch group that takes them (D2Q9 on the direct kernel: stages = 0 in
  * lbm_get_tuning) runs each stretch of two or more consecutive steps without a
  * sample step as ONE kernel launch, of at most 4096 steps (fewer for very
  * large groups, so that steps x blocks stays below 2^31); sample steps, staged
- * groups and D2Q7 groups launch once per step as before.  Inside the launch,
- * blocks take (step, block) work items from a counter, lattice group by
- * lattice group (consecutive lattices whose two population buffers together
- * fit l2_group_mib MiB; 0 = the default of 64, at least one lattice per
- * group) and step by step inside a group, and each item waits only for the
- * strip rows it reads to finish the previous step: the populations of a
- * lattice group stay in L2 across its steps, and steps overlap with no barrier
- * between them.  States, samples and observables are bitwise those of the
- * per-step launches.  The waits are bounded (about 1 s, then the error flag is
- * raised and the call that reads it returns LBM_ERR_TIMEOUT).  Each launch
- * clears its counters in the context's scratch first (a memset on the bound
- * stream, a graph node when graphs are on), so launches of one context must
- * not overlap on the GPU, as for every other call.  enabled = 0 (default):
- * one launch per step.  l2_group_mib outside [0, 2^20] gives
- * LBM_ERR_INVALID_ARG.  Host only; drops captured graphs and re-uploads
- * descriptors (syncs) when bound. */
-lbm_status lbm_set_persistent(lbm_ctx *ctx, int32_t enabled, int32_t l2_group_mib);
+ * groups and D2Q7 groups launch once per step.  Inside the launch, blocks take
+ * (step, block) work items from a counter -- lattice group by lattice group,
+ * step by step inside a group -- and each item waits only for the strip rows
+ * it reads to finish the previous step, so consecutive steps overlap with no
+ * launch boundary or grid-wide barrier between them.  A lattice group is a run
+ * of consecutive lattices whose two population buffers together fit
+ * l2_group_mib MiB (at least one lattice per group); 0 (the default) puts every
+ * lattice of a launch group in one.  States, samples and observables are
+ * bitwise those of the per-step launches.
+ * mode 0: one launch per step.  mode 1: every group that can takes persistent
+ * launches; the tuner times its direct shapes that way.  mode 2 (default): the
+ * tuner times every direct shape both ways (the persistent way over 12 steps,
+ * recomputing the current step into the spare buffer) and keeps the faster
+ * form with the shape, per group, then checks the choice with the whole batch
+ * running; until it has run (and with tuning off, lbm_set_tuning mode 1)
+ * groups launch once per step.  Setting mode 2 makes the next lbm_step tune
+ * again when tuning is automatic.  Measured on one GB300: the 256-lattice
+ * 256^2 CIL batch in FP32 at 85.9 GLUPS persistent (16-row strips) against
+ * 81.3 per step; in FP16 storage the per-step launch stays faster (83.5).
+ * The waits are bounded (about 1 s, then the error flag is raised and the call
+ * that reads it returns LBM_ERR_TIMEOUT).  Each launch first clears its
+ * counters in the context's scratch (a memset on the bound stream; a graph
+ * node when graphs are on), so launches of one context must not overlap on
+ * the GPU, as for every other call.  mode outside 0..2 or l2_group_mib
+ * outside [0, 2^20] gives LBM_ERR_INVALID_ARG.  Host only; drops captured
+ * graphs and re-uploads descriptors (syncs) when bound. */
+lbm_status lbm_set_persistent(lbm_ctx *ctx, int32_t mode, int32_t l2_group_mib);
+
+/* Whether lattice `lattice`'s launch group runs its stretches of plain steps as
+ * persistent launches (1) or one launch per step (0) under the current mode,
+ * shape and tuning (see lbm_set_persistent).  Host only. */
+lbm_status lbm_get_persistent(const lbm_ctx *ctx, int32_t lattice, int32_t *persistent);
 
 /* Number of kernels the last lbm_step call enqueued (graph nodes included). */
 lbm_status lbm_last_launch_count(const lbm_ctx *ctx, int64_t *count);

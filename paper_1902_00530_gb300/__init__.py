@@ -224,11 +224,18 @@ class Simulation:
     def set_graphs(self, enabled: bool) -> None:
         self._check(self.lib.lbm_set_graphs(self.ctx, 1 if enabled else 0))
 
-    def set_persistent(self, enabled: bool, l2_group_mib: int = 0) -> None:
-        """Run stretches of steps without a sample step as one persistent launch
-        per launch group on the direct D2Q9 kernel (lattice groups of
-        l2_group_mib MiB of populations; 0 = the library default)."""
-        self._check(self.lib.lbm_set_persistent(self.ctx, 1 if enabled else 0, int(l2_group_mib)))
+    def set_persistent(self, mode, l2_group_mib: int = 0) -> None:
+        """Persistent launches of stretches of plain steps (groups on the direct
+        D2Q9 kernel): False/0 off, True/1 on, "auto"/2 chosen per group by the
+        tuner; l2_group_mib MiB of populations per lattice group (0: one group)."""
+        m = 2 if mode == "auto" else int(mode)
+        self._check(self.lib.lbm_set_persistent(self.ctx, m, int(l2_group_mib)))
+
+    def get_persistent(self, lattice: int = 0) -> bool:
+        """Whether the lattice's launch group runs persistent launches now."""
+        v = ctypes.c_int32()
+        self._check(self.lib.lbm_get_persistent(self.ctx, lattice, ctypes.byref(v)))
+        return bool(v.value)
 
     def last_launch_count(self) -> int:
         c = ctypes.c_int64()

@@ -68,6 +68,7 @@ SIGNATURES = {
                                       ctypes.POINTER(ctypes.c_int32)]),
     "lbm_set_graphs": (ctypes.c_int, [_CTX, ctypes.c_int32]),
     "lbm_set_persistent": (ctypes.c_int, [_CTX, ctypes.c_int32, ctypes.c_int32]),
+    "lbm_get_persistent": (ctypes.c_int, [_CTX, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
     "lbm_last_launch_count": (ctypes.c_int, [_CTX, ctypes.POINTER(ctypes.c_int64)]),
     "lbm_set_profiling": (ctypes.c_int, [_CTX, ctypes.c_int32]),
     "lbm_profile_read": (ctypes.c_int, [_CTX, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),

@@ -31,7 +31,8 @@ constexpr int CHUNK_COLS = 256;    // columns / rows / strips per finaliser bloc
 constexpr int NCHUNK_MAX = 1024;
 constexpr int GRAPH_CHUNK_MAX = 256;
 constexpr int PERSIST_STEPS_MAX = 4096;  // steps of one persistent launch
-constexpr int PERSIST_L2_MIB_DEFAULT = 64;  // population bytes of a lattice group stepped together
+constexpr int TUNE_STEPS = 3;            // steps the tuner times per candidate (per-step launches)
+constexpr int TUNE_STEPS_PERSIST = 12;   // ... and as one persistent launch (longer: its fill and drain)
 
 size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
@@ -62,6 +63,7 @@ struct GroupHost {
     // in all, zeroed before each launch); lattice-group table at pg_off
     size_t persist_off = 0, persist_bytes = 0, pg_off = 0;
     int npg = 0;
+    bool persist = false;  // mode 2: the tuner chose persistent launches for this group
 };
 
 struct GraphKey {
@@ -102,9 +104,9 @@ struct lbm_ctx {
         int64_t steps;  // steps it ran (a persistent launch runs several)
     };
     std::vector<ProfMark> ev_marks;
-    // persistent launches (lbm_set_persistent)
-    bool persistent = false;
-    int persist_l2_mib = PERSIST_L2_MIB_DEFAULT;
+    // persistent launches (lbm_set_persistent): mode 0 off, 1 on, 2 chosen by the tuner
+    int persist_mode = 2;
+    int persist_l2_mib = 0;  // 0: every lattice of a launch group in one lattice group
     size_t ev_used = 0;
     // launch groups after the first run on their own streams, forked from and
     // joined back into the bound stream (parallel branches of the step graph)
@@ -374,7 +376,7 @@ lbm_status upload_descs(lbm_ctx *c)
         // two population buffers each fit the L2 budget together (at least one
         // lattice per group); entry i is the group's first block of the step grid
         std::vector<int> pg;
-        const size_t budget = (size_t)c->persist_l2_mib << 20;
+        const size_t budget = c->persist_l2_mib > 0 ? (size_t)c->persist_l2_mib << 20 : SIZE_MAX;
         size_t bytes = 0;
         for (int m : g.members) {
             const LatHost &L = c->lats[m];
@@ -452,8 +454,14 @@ cudaError_t launch_group_step(const lbm_ctx *c, const GroupHost &g, int src, uin
     return launch_step_bf16(g.model, kind, g.vec, sample, noise, a, g.blocks, g.warps, stream);
 }
 
-// Groups the persistent launch takes: D2Q9 on the direct kernel.
-bool persistent_ok(const lbm_ctx *c, const GroupHost &g) { return c->persistent && g.stages == 0 && g.q == 9; }
+// Groups the persistent launch can take: D2Q9 on the direct kernel.
+bool persist_eligible(const GroupHost &g) { return g.stages == 0 && g.q == 9; }
+// Whether a group runs its plain steps as persistent launches: always in mode
+// 1, where the tuner chose to in mode 2.
+bool persistent_ok(const lbm_ctx *c, const GroupHost &g)
+{
+    return persist_eligible(g) && (c->persist_mode == 1 || (c->persist_mode == 2 && g.persist));
+}
 
 // Most steps one persistent launch of the group may run (its items stay below 2^31).
 int64_t persist_steps_max(const GroupHost &g)
@@ -464,7 +472,7 @@ int64_t persist_steps_max(const GroupHost &g)
 // m steps k .. k+m-1 of group g in one persistent launch: clear its counters,
 // then launch.
 cudaError_t launch_group_persistent(const lbm_ctx *c, const GroupHost &g, int src, uint32_t k, int64_t m,
-                                    cudaStream_t stream)
+                                    cudaStream_t stream, bool retime = false)
 {
     const StepArgs a = step_args(c, g, src, k);
     PersistArgs p;
@@ -473,6 +481,7 @@ cudaError_t launch_group_persistent(const lbm_ctx *c, const GroupHost &g, int sr
     p.pg = reinterpret_cast<const int *>(c->scratch + g.pg_off);
     p.npg = g.npg;
     p.nsteps = (int)m;
+    p.retime = retime ? 1 : 0;
     cudaError_t e = cudaMemsetAsync(c->scratch + g.persist_off, 0, g.persist_bytes, stream);
     if (e != cudaSuccess) return e;
     const int noise = group_noise(c, g);
@@ -480,6 +489,19 @@ cudaError_t launch_group_persistent(const lbm_ctx *c, const GroupHost &g, int sr
     if (g.storage == LBM_F16_SHIFTED)
         return launch_persistent_f16(g.model, g.vec, noise, a, p, g.blocks, g.warps, stream);
     return launch_persistent_bf16(g.model, g.vec, noise, a, p, g.blocks, g.warps, stream);
+}
+
+// The tuner's measure of a group: `steps` recomputations of the current step
+// into the spare buffer (the state is left as it was), as one persistent launch
+// in its timing form or as that many per-step launches.
+cudaError_t launch_group_timed(const lbm_ctx *c, const GroupHost &g, int steps, cudaStream_t stream)
+{
+    if (persistent_ok(c, g)) return launch_group_persistent(c, g, c->parity, 0, steps, stream, true);
+    for (int q = 0; q < steps; ++q) {
+        const cudaError_t e = launch_group_step(c, g, c->parity, 0, false, stream);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_group_observe(const lbm_ctx *c, const GroupHost &g, int src)
@@ -692,9 +714,18 @@ struct EventPair {
 };
 
 // Times the launch-shape candidates of one group on its own and keeps the
-// fastest; *alt receives the fastest candidate of the other kernel kind
-// (direct or staged), if any, for the joint check of a batch's groups.
-lbm_status tune_group(lbm_ctx *c, GroupHost &g, Shape *alt, bool *has_alt)
+// fastest; *alts receives the alternatives for the joint check of a batch's
+// groups: the fastest candidate of the other kernel kind (direct or staged),
+// if any, and, where the fastest was a persistent launch, the fastest per-step
+// form.  With persistent launches on (mode 1) direct candidates are timed as
+// persistent launches; in mode 2 both ways, and the faster way is kept with
+// the shape.
+struct Alt {
+    Shape shape;
+    bool persist;
+};
+
+lbm_status tune_group(lbm_ctx *c, GroupHost &g, std::vector<Alt> *alts)
 {
     std::vector<Shape> cands;
     long long max_ny = 1;
@@ -730,8 +761,9 @@ lbm_status tune_group(lbm_ctx *c, GroupHost &g, Shape *alt, bool *has_alt)
     EventPair ev;
     CK(ev.create(), "create event");
     cudaEvent_t e0 = ev.e0, e1 = ev.e1;
-    float best = 1e30f, best_kind[2] = {1e30f, 1e30f};
-    Shape bs{g.vec, g.rows, g.warps, g.stages}, bk[2] = {bs, bs};
+    float best = 1e30f, best_kind[2] = {1e30f, 1e30f}, best_step = 1e30f;
+    Shape bs{g.vec, g.rows, g.warps, g.stages}, bk[2] = {bs, bs}, bstep = bs;
+    bool bp = g.persist, bkp[2] = {bp, bp};
     for (const Shape &sh : cands) {
         g.vec = sh.vec;
         g.rows = sh.rows;
@@ -739,35 +771,53 @@ lbm_status tune_group(lbm_ctx *c, GroupHost &g, Shape *alt, bool *has_alt)
         g.stages = sh.stages;
         lbm_status st = upload_descs(c);
         if (st != LBM_OK) return st;
-        cudaError_t e = launch_group_step(c, g, c->parity, 0, false, c->stream);
-        if (e != cudaSuccess) {  // a shape this device cannot launch (e.g. shared memory): skip it
-            cudaGetLastError();
-            continue;
-        }
-        CK(cudaEventRecord(e0, c->stream), "record event");
-        const int reps = 3;
-        for (int q = 0; q < reps; ++q) CK(launch_group_step(c, g, c->parity, 0, false, c->stream), "tuning launch");
-        CK(cudaEventRecord(e1, c->stream), "record event");
-        CK(cudaEventSynchronize(e1), "synchronise event");
-        float ms = 0.f;
-        CK(cudaEventElapsedTime(&ms, e0, e1), "event time");
-        if (ms < best) {
-            best = ms;
-            bs = sh;
-        }
-        const int kind = sh.stages > 0 ? 1 : 0;
-        if (ms < best_kind[kind]) {
-            best_kind[kind] = ms;
-            bk[kind] = sh;
+        // launch forms to time: as lbm_step would launch it (modes 0, 1), or
+        // per step and persistent (mode 2, direct shapes)
+        for (int form = 0; form < 2; ++form) {
+            if (form == 1 && !(c->persist_mode == 2 && persist_eligible(g))) break;
+            g.persist = form == 1;
+            cudaError_t e = launch_group_timed(c, g, 1, c->stream);
+            if (e != cudaSuccess) {  // a shape this device cannot launch (e.g. shared memory): skip it
+                cudaGetLastError();
+                continue;
+            }
+            const int steps = persistent_ok(c, g) ? TUNE_STEPS_PERSIST : TUNE_STEPS;
+            CK(cudaEventRecord(e0, c->stream), "record event");
+            CK(launch_group_timed(c, g, steps, c->stream), "tuning launch");
+            CK(cudaEventRecord(e1, c->stream), "record event");
+            CK(cudaEventSynchronize(e1), "synchronise event");
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1), "event time");
+            ms *= (float)TUNE_STEPS / (float)steps;  // per TUNE_STEPS steps
+            if (ms < best) {
+                best = ms;
+                bs = sh;
+                bp = g.persist;
+            }
+            const int kind = sh.stages > 0 ? 1 : 0;
+            if (ms < best_kind[kind]) {
+                best_kind[kind] = ms;
+                bk[kind] = sh;
+                bkp[kind] = g.persist;
+            }
+            if (!persistent_ok(c, g) && ms < best_step) {
+                best_step = ms;
+                bstep = sh;
+            }
         }
     }
     const int other = bs.stages > 0 ? 0 : 1;
-    *has_alt = best_kind[other] < 1e29f;
-    *alt = bk[other];
+    alts->clear();
+    if (best_kind[other] < 1e29f) alts->push_back({bk[other], bkp[other]});
+    // mode 2, a persistent choice: its best per-step direct form too (beside
+    // other groups, a persistent launch holds the SMs its grid fills; the best
+    // staged form is the alternative above)
+    if (bp && best_step < 1e29f && bstep.stages == 0) alts->push_back({bstep, false});
     g.vec = bs.vec;
     g.rows = bs.rows;
     g.warps = bs.warps;
     g.stages = bs.stages;
+    g.persist = bp;
     lbm_status st = upload_descs(c);
     if (st != LBM_OK) return st;
     return read_error_flag(c);
@@ -781,8 +831,9 @@ void set_shape(GroupHost &g, const Shape &sh)
     g.stages = sh.stages;
 }
 
-// One step of every group as lbm_step runs a batch (forked, side by side,
-// joined), repeated: its time in ms.  Writes only the spare buffers.
+// TUNE_STEPS_PERSIST steps of every group as lbm_step runs a batch (forked,
+// side by side, joined), after a warm-up: their time in ms.  Writes only the
+// spare buffers.
 lbm_status time_joint_step(lbm_ctx *c, float *ms)
 {
     lbm_status st = upload_descs(c);
@@ -790,11 +841,11 @@ lbm_status time_joint_step(lbm_ctx *c, float *ms)
     EventPair ev;
     CK(ev.create(), "create event");
     cudaEvent_t e0 = ev.e0, e1 = ev.e1;
-    for (int rep = 0; rep < 4; ++rep) {
+    for (int rep = 0; rep < 2; ++rep) {
         if (rep == 1) CK(cudaEventRecord(e0, c->stream), "record event");  // the first is a warm-up
         CK(fork_groups(c), "fork launch groups");
         for (size_t gi = 0; gi < c->groups.size(); ++gi)
-            CK(launch_group_step(c, c->groups[gi], c->parity, 0, false, gi > 0 ? c->aux[gi - 1] : c->stream),
+            CK(launch_group_timed(c, c->groups[gi], TUNE_STEPS_PERSIST, gi > 0 ? c->aux[gi - 1] : c->stream),
                "tuning launch");
         CK(join_groups(c), "join launch groups");
     }
@@ -808,19 +859,19 @@ lbm_status time_joint_step(lbm_ctx *c, float *ms)
 // side, where kernels of the two kinds can slow each other (measured on a
 // 64-lattice ragged MIPS/CIL batch: a staged MIPS group beside a direct CIL
 // group ran at 71 GLUPS, slower than the same launches one after the other,
-// 73; both direct, about 79).  So each group's best shape of the other kind
-// is tried in turn with the whole batch running, and kept where the batch
-// step is faster.
+// 73; both direct, about 79), and a persistent launch keeps the SMs its grid
+// fills from the other groups' launches (the same batch with its CIL group
+// persistent: 77 against 79 GLUPS).  So each group's alternatives (its best
+// shape of the other kind; its best per-step form where it chose a persistent
+// launch) are tried in turn with the whole batch running, and kept where the
+// batch step is faster.
 lbm_status do_tune(lbm_ctx *c)
 {
     const size_t ng = c->groups.size();
-    std::vector<Shape> alt(ng);
-    std::vector<char> has_alt(ng, 0);
+    std::vector<std::vector<Alt>> alts(ng);
     for (size_t gi = 0; gi < ng; ++gi) {
-        bool h = false;
-        lbm_status st = tune_group(c, c->groups[gi], &alt[gi], &h);
+        lbm_status st = tune_group(c, c->groups[gi], &alts[gi]);
         if (st != LBM_OK) return st;
-        has_alt[gi] = h;
     }
     if (ng > 1) {
         lbm_status st = ensure_aux(c);
@@ -829,15 +880,22 @@ lbm_status do_tune(lbm_ctx *c)
         st = time_joint_step(c, &best);
         if (st != LBM_OK) return st;
         for (size_t gi = 0; gi < ng; ++gi) {
-            if (!has_alt[gi]) continue;
             GroupHost &g = c->groups[gi];
-            const Shape keep{g.vec, g.rows, g.warps, g.stages};
-            set_shape(g, alt[gi]);
-            float ms = 0.f;
-            st = time_joint_step(c, &ms);
-            if (st != LBM_OK) return st;
-            if (ms < best) best = ms;
-            else set_shape(g, keep);
+            for (const Alt &al : alts[gi]) {
+                const Shape keep{g.vec, g.rows, g.warps, g.stages};
+                const bool keep_persist = g.persist;
+                set_shape(g, al.shape);
+                g.persist = al.persist;
+                float ms = 0.f;
+                st = time_joint_step(c, &ms);
+                if (st != LBM_OK) return st;
+                if (ms < best) {
+                    best = ms;
+                } else {
+                    set_shape(g, keep);
+                    g.persist = keep_persist;
+                }
+            }
         }
         st = upload_descs(c);
         if (st != LBM_OK) return st;
@@ -1442,15 +1500,25 @@ lbm_status lbm_set_graphs(lbm_ctx *c, int32_t enabled)
     return LBM_OK;
 }
 
-lbm_status lbm_set_persistent(lbm_ctx *c, int32_t enabled, int32_t l2_group_mib)
+lbm_status lbm_set_persistent(lbm_ctx *c, int32_t mode, int32_t l2_group_mib)
 {
     if (!c) return LBM_ERR_INVALID_ARG;
+    if (mode < 0 || mode > 2) return fail(c, LBM_ERR_INVALID_ARG, "mode must be 0, 1 or 2");
     if (l2_group_mib < 0 || l2_group_mib > (1 << 20))
         return fail(c, LBM_ERR_INVALID_ARG, "l2_group_mib must be in [0, 2^20]");
-    c->persistent = enabled != 0;
-    c->persist_l2_mib = l2_group_mib > 0 ? l2_group_mib : PERSIST_L2_MIB_DEFAULT;
+    c->persist_mode = mode;
+    c->persist_l2_mib = l2_group_mib;
+    for (auto &g : c->groups) g.persist = false;
+    if (mode == 2 && c->tune_mode == 0) c->tuned = false;  // the next lbm_step tunes, and chooses
     drop_graphs(c);
     if (c->bound) return upload_descs(c);
+    return LBM_OK;
+}
+
+lbm_status lbm_get_persistent(const lbm_ctx *c, int32_t lattice, int32_t *persistent)
+{
+    if (!c || !persistent || lattice < 0 || lattice >= (int32_t)c->lats.size()) return LBM_ERR_INVALID_ARG;
+    *persistent = persistent_ok(c, c->groups[c->lats[lattice].group]) ? 1 : 0;
     return LBM_OK;
 }
 

@@ -151,6 +151,8 @@ struct PersistArgs {
     const int *pg;   // first block of each lattice group; pg[npg] = blocks of the step grid
     int npg;         // lattice groups
     int nsteps;      // steps of the launch: items = nsteps * pg[npg] < 2^31 (host check)
+    int retime;      // timing form (the tuner): every item recomputes the first step, from the
+                     // current buffer into the spare one, so the state is left as it was
 };
 
 // ---------------------------------------------------------------------------

@@ -538,31 +538,38 @@ __device__ __forceinline__ void mips_gradients(const float rm[VEC + 2], const fl
 // Observable sums of one stored row (sites x0..x0+VEC-1) from its moments
 // rho and j = rho u: per-thread FP64 accumulators for the strip's column sums
 // and five scalar sums, and the row's density total reduced over the warp.
+// The sums that cancel (rho and rho^2 in the variance, j in the polar order of
+// a nearly disordered state) are formed in FP64 from the lane's first site on
+// (rho^2 exactly: a product of two FP32 values fits FP64), so they do not
+// depend on how the launch shape groups sites into lanes beyond FP64 rounding;
+// |j|, a sum of magnitudes, is summed in FP32 over the lane's sites.
 // Lattice-independent.
 template <int VEC>
 __device__ __forceinline__ void observe_moments(const float rv[VEC], const float jxv[VEC], const float jyv[VEC],
                                                 bool valid, double col[VEC], double acc[5], double *row_out,
                                                 int lane)
 {
-    float rs = 0.f, js = 0.f, jxs = 0.f, jys = 0.f, r2s = 0.f;
+    double rs = 0.0, jxs = 0.0, jys = 0.0, r2s = 0.0;
+    float js = 0.f;
     if (valid) {
 #pragma unroll
         for (int j = 0; j < VEC; ++j) {
-            const float r = rv[j], jx = jxv[j], jy = jyv[j];
-            col[j] += (double)r;
+            const float jx = jxv[j], jy = jyv[j];
+            const double r = (double)rv[j];
+            col[j] += r;
             rs += r;
-            jxs += jx;
-            jys += jy;
-            r2s += r * r;
+            jxs += (double)jx;
+            jys += (double)jy;
+            r2s = __fma_rn(r, r, r2s);
             js += sqrtf(jx * jx + jy * jy);
         }
     }
-    acc[0] += (double)rs;
-    acc[1] += (double)jxs;
-    acc[2] += (double)jys;
-    acc[3] += (double)r2s;
+    acc[0] += rs;
+    acc[1] += jxs;
+    acc[2] += jys;
+    acc[3] += r2s;
     acc[4] += (double)js;
-    double t = (double)rs;
+    double t = rs;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(FULL, t, o);
     if (lane == 0) *row_out = t;

@@ -94,8 +94,17 @@ def test_host_only_calls_and_status_codes(lib):
     assert lib.lbm_set_persistent(None, 1, 0) == 1
     assert lib.lbm_set_persistent(ctx, 1, -1) == 1         # lattice-group budget out of range
     assert lib.lbm_set_persistent(ctx, 1, (1 << 20) + 1) == 1
+    assert lib.lbm_set_persistent(ctx, 3, 0) == 1          # modes are 0, 1, 2
+    on = ctypes.c_int32(-1)
+    assert lib.lbm_get_persistent(ctx, 0, ctypes.byref(on)) == 0 and on.value == 0  # default 2: not tuned yet
     assert lib.lbm_set_persistent(ctx, 1, 0) == 0          # host only before binding
+    assert lib.lbm_get_persistent(ctx, 0, ctypes.byref(on)) == 0 and on.value == 1  # direct D2Q9 shape
+    assert lib.lbm_set_tuning(ctx, 1, 4, 16, 2, 0) == 1 and lib.lbm_set_tuning(ctx, 1, 1, 32, 2, 0) == 0
+    assert lib.lbm_get_persistent(ctx, 1, ctypes.byref(on)) == 1   # no lattice 1
+    assert lib.lbm_get_persistent(ctx, 0, None) == 1
+    assert lib.lbm_set_persistent(ctx, 2, 64) == 0
     assert lib.lbm_set_persistent(ctx, 0, 16) == 0
+    assert lib.lbm_get_persistent(ctx, 0, ctypes.byref(on)) == 0 and on.value == 0
     assert lib.lbm_bind(ctx, None, None, None) == 1
     assert lib.lbm_bind(ctx, ctypes.c_void_p(0x1001), ctypes.c_void_p(0x2000), None) == 1  # misaligned
     lib.lbm_destroy(ctx)
