@@ -224,6 +224,7 @@ def run_gpu(args, world, rank, local):
     sim = Simulation(lats, [wl["model"]] * nlat, [m["params"] for m in members],
                      sample_every=wl["sample_every"], ring_capacity=max(16, args.steps // wl["sample_every"] + 4))
     sim.init(wl["seed"], [m["init"] for m in members])
+    sim.set_persistent({"auto": 2, "on": 1, "off": 0}[args.persistent])
     if args.shape:
         sh = [int(x) for x in args.shape.split(",")]
         sim.set_tuning(1, *sh)
@@ -501,6 +502,8 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip the secondary (16-bit, batched) lines")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--shape", default="", help="fixed launch shape vec,rows,warps[,stages] instead of tuning")
+    ap.add_argument("--persistent", default="auto", choices=["auto", "on", "off"],
+                    help="persistent launches of the direct kernel: chosen by the tuner (default), always, never")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
