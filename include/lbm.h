@@ -265,8 +265,10 @@ lbm_status lbm_set_graphs(lbm_ctx *ctx, int32_t enabled);
  * lattice of a launch group in one.  States, samples and observables are
  * bitwise those of the per-step launches.
  * mode 0: one launch per step.  mode 1: every group that can takes persistent
- * launches; the tuner times its direct shapes that way.  mode 2 (default): the
- * tuner times every direct shape both ways (the persistent way over 12 steps,
+ * launches; the tuner times its direct shapes that way.  mode 2 (default): for
+ * a group of at least 2^20 sites (smaller steps cannot fill the GPU in either
+ * form, and there one launch per step measured faster), the tuner times every
+ * direct shape both ways (the persistent way over 12 steps,
  * recomputing the current step into the spare buffer) and keeps the faster
  * form with the shape, per group, then checks the choice with the whole batch
  * running; until it has run (and with tuning off, lbm_set_tuning mode 1)

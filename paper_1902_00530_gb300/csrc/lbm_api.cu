@@ -33,6 +33,15 @@ constexpr int GRAPH_CHUNK_MAX = 256;
 constexpr int PERSIST_STEPS_MAX = 4096;  // steps of one persistent launch
 constexpr int TUNE_STEPS = 3;            // steps the tuner times per candidate (per-step launches)
 constexpr int TUNE_STEPS_PERSIST = 12;   // ... and as one persistent launch (longer: its fill and drain)
+constexpr float TUNE_MIN_MS = 0.25f;     // shorter timings are repeated over more steps (event resolution, noise)
+constexpr int TUNE_STEPS_MAX = 256;
+// Mode 2 considers persistent launches only for groups with at least this
+// many sites per step.  Below it a step's items cannot fill the GPU in either
+// form and the persistent launch's dependency waits cost more than a launch
+// boundary; measured, 32 lattices of 180 x 60 (0.35 M sites): 26.6 GLUPS
+// persistent against 29.0 per step, while the tuner's timing form preferred
+// it; 256 of 128^2 (4.2 M): 82.6 against 64.2.
+constexpr long long PERSIST_AUTO_MIN_SITES = 1LL << 20;
 
 size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
@@ -728,8 +737,11 @@ struct Alt {
 lbm_status tune_group(lbm_ctx *c, GroupHost &g, std::vector<Alt> *alts)
 {
     std::vector<Shape> cands;
-    long long max_ny = 1;
-    for (int m : g.members) max_ny = std::max<long long>(max_ny, c->lats[m].lat.ny);
+    long long max_ny = 1, group_sites = 0;
+    for (int m : g.members) {
+        max_ny = std::max<long long>(max_ny, c->lats[m].lat.ny);
+        group_sites += (long long)c->lats[m].lat.nx * c->lats[m].lat.ny;
+    }
     const int all_v[] = {1, 2, 4, 8};
     const bool staged = staged_ok(c, g);
     const bool direct = direct_ok(c, g);
@@ -772,22 +784,27 @@ lbm_status tune_group(lbm_ctx *c, GroupHost &g, std::vector<Alt> *alts)
         lbm_status st = upload_descs(c);
         if (st != LBM_OK) return st;
         // launch forms to time: as lbm_step would launch it (modes 0, 1), or
-        // per step and persistent (mode 2, direct shapes)
+        // per step and persistent (mode 2, direct shapes, enough sites)
         for (int form = 0; form < 2; ++form) {
-            if (form == 1 && !(c->persist_mode == 2 && persist_eligible(g))) break;
+            if (form == 1 && !(c->persist_mode == 2 && persist_eligible(g) && group_sites >= PERSIST_AUTO_MIN_SITES))
+                break;
             g.persist = form == 1;
             cudaError_t e = launch_group_timed(c, g, 1, c->stream);
             if (e != cudaSuccess) {  // a shape this device cannot launch (e.g. shared memory): skip it
                 cudaGetLastError();
                 continue;
             }
-            const int steps = persistent_ok(c, g) ? TUNE_STEPS_PERSIST : TUNE_STEPS;
-            CK(cudaEventRecord(e0, c->stream), "record event");
-            CK(launch_group_timed(c, g, steps, c->stream), "tuning launch");
-            CK(cudaEventRecord(e1, c->stream), "record event");
-            CK(cudaEventSynchronize(e1), "synchronise event");
+            int steps = persistent_ok(c, g) ? TUNE_STEPS_PERSIST : TUNE_STEPS;
             float ms = 0.f;
-            CK(cudaEventElapsedTime(&ms, e0, e1), "event time");
+            while (true) {
+                CK(cudaEventRecord(e0, c->stream), "record event");
+                CK(launch_group_timed(c, g, steps, c->stream), "tuning launch");
+                CK(cudaEventRecord(e1, c->stream), "record event");
+                CK(cudaEventSynchronize(e1), "synchronise event");
+                CK(cudaEventElapsedTime(&ms, e0, e1), "event time");
+                if (ms >= TUNE_MIN_MS || steps >= TUNE_STEPS_MAX) break;
+                steps = std::min(TUNE_STEPS_MAX, (int)std::ceil(steps * TUNE_MIN_MS / std::max(ms, 1e-3f)) + 1);
+            }
             ms *= (float)TUNE_STEPS / (float)steps;  // per TUNE_STEPS steps
             if (ms < best) {
                 best = ms;
@@ -832,7 +849,8 @@ void set_shape(GroupHost &g, const Shape &sh)
 }
 
 // TUNE_STEPS_PERSIST steps of every group as lbm_step runs a batch (forked,
-// side by side, joined), after a warm-up: their time in ms.  Writes only the
+// side by side, joined), after a warm-up: their time in ms (timed over more
+// steps when that is under TUNE_MIN_MS, and scaled back).  Writes only the
 // spare buffers.
 lbm_status time_joint_step(lbm_ctx *c, float *ms)
 {
@@ -841,17 +859,22 @@ lbm_status time_joint_step(lbm_ctx *c, float *ms)
     EventPair ev;
     CK(ev.create(), "create event");
     cudaEvent_t e0 = ev.e0, e1 = ev.e1;
-    for (int rep = 0; rep < 2; ++rep) {
-        if (rep == 1) CK(cudaEventRecord(e0, c->stream), "record event");  // the first is a warm-up
-        CK(fork_groups(c), "fork launch groups");
-        for (size_t gi = 0; gi < c->groups.size(); ++gi)
-            CK(launch_group_timed(c, c->groups[gi], TUNE_STEPS_PERSIST, gi > 0 ? c->aux[gi - 1] : c->stream),
-               "tuning launch");
-        CK(join_groups(c), "join launch groups");
+    int steps = TUNE_STEPS_PERSIST;
+    while (true) {
+        for (int rep = 0; rep < 2; ++rep) {
+            if (rep == 1) CK(cudaEventRecord(e0, c->stream), "record event");  // the first is a warm-up
+            CK(fork_groups(c), "fork launch groups");
+            for (size_t gi = 0; gi < c->groups.size(); ++gi)
+                CK(launch_group_timed(c, c->groups[gi], steps, gi > 0 ? c->aux[gi - 1] : c->stream), "tuning launch");
+            CK(join_groups(c), "join launch groups");
+        }
+        CK(cudaEventRecord(e1, c->stream), "record event");
+        CK(cudaEventSynchronize(e1), "synchronise event");
+        CK(cudaEventElapsedTime(ms, e0, e1), "event time");
+        if (*ms >= TUNE_MIN_MS || steps >= TUNE_STEPS_MAX) break;
+        steps = std::min(TUNE_STEPS_MAX, (int)std::ceil(steps * TUNE_MIN_MS / std::max(*ms, 1e-3f)) + 1);
     }
-    CK(cudaEventRecord(e1, c->stream), "record event");
-    CK(cudaEventSynchronize(e1), "synchronise event");
-    CK(cudaEventElapsedTime(ms, e0, e1), "event time");
+    *ms *= (float)TUNE_STEPS_PERSIST / (float)steps;
     return LBM_OK;
 }
 
