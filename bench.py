@@ -270,8 +270,8 @@ def run_gpu(args, world, rank, local):
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic, "peak_source": peak_kind,
                 "algorithmic_bytes_per_launch": bytes_per_update(storage, q) * cells,
-                "kernel": ("lbm::step_staged_kernel" if shape[3] > 0 else
-                           "lbm::step_persistent_kernel" if persistent else "lbm::step_kernel") +
+                "kernel": "lbm::step_persistent_kernel" if persistent and shape[3] == 0 else
+                          ("lbm::step_staged_kernel" if shape[3] > 0 else "lbm::step_kernel") +
                           ("_q7" if q == 7 else ""), "avg_launch_ms": round(step_avg_ms, 5),
                 "step_kernel_share": round(prof["step_ms"] / max(prof["step_ms"] + prof["other_ms"], 1e-9), 4),
                 "frac_of_8TBps": round(achieved / 8000.0, 4)}

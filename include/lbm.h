@@ -251,11 +251,11 @@ lbm_status lbm_set_graphs(lbm_ctx *ctx, int32_t enabled);
 
 /* Persistent launches (the paper's many independent runs per parameter point,
  * App. C.3-C.4, advanced together; each step is App. A.2's update, unchanged).
- * A launch group that takes them (D2Q9 on the direct kernel: stages = 0 in
- * lbm_get_tuning) runs each stretch of two or more consecutive steps without a
- * sample step as ONE kernel launch, of at most 4096 steps (fewer for very
- * large groups, so that steps x blocks stays below 2^31); sample steps, staged
- * groups and D2Q7 groups launch once per step.  Inside the launch, blocks take
+ * A launch group that takes them (either lattice, on the direct kernel:
+ * stages = 0 in lbm_get_tuning) runs each stretch of two or more consecutive
+ * steps without a sample step as ONE kernel launch, of at most 4096 steps
+ * (fewer for very large groups, so that steps x blocks stays below 2^31);
+ * sample steps and staged groups launch once per step.  Inside the launch, blocks take
  * (step, block) work items from a counter -- lattice group by lattice group,
  * step by step inside a group -- and each item waits only for the strip rows
  * it reads to finish the previous step, so consecutive steps overlap with no

@@ -225,9 +225,10 @@ class Simulation:
         self._check(self.lib.lbm_set_graphs(self.ctx, 1 if enabled else 0))
 
     def set_persistent(self, mode, l2_group_mib: int = 0) -> None:
-        """Persistent launches of stretches of plain steps (groups on the direct
-        D2Q9 kernel): False/0 off, True/1 on, "auto"/2 chosen per group by the
-        tuner; l2_group_mib MiB of populations per lattice group (0: one group)."""
+        """Persistent launches of stretches of plain steps (groups on a direct
+        kernel, either lattice): False/0 off, True/1 on, "auto"/2 chosen per
+        group by the tuner; l2_group_mib MiB of populations per lattice group
+        (0: one group)."""
         m = 2 if mode == "auto" else int(mode)
         self._check(self.lib.lbm_set_persistent(self.ctx, m, int(l2_group_mib)))
 

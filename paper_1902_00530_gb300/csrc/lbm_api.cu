@@ -463,8 +463,8 @@ cudaError_t launch_group_step(const lbm_ctx *c, const GroupHost &g, int src, uin
     return launch_step_bf16(g.model, kind, g.vec, sample, noise, a, g.blocks, g.warps, stream);
 }
 
-// Groups the persistent launch can take: D2Q9 on the direct kernel.
-bool persist_eligible(const GroupHost &g) { return g.stages == 0 && g.q == 9; }
+// Groups the persistent launch can take: those on a direct kernel (D2Q9 or D2Q7).
+bool persist_eligible(const GroupHost &g) { return g.stages == 0; }
 // Whether a group runs its plain steps as persistent launches: always in mode
 // 1, where the tuner chose to in mode 2.
 bool persistent_ok(const lbm_ctx *c, const GroupHost &g)
@@ -494,6 +494,13 @@ cudaError_t launch_group_persistent(const lbm_ctx *c, const GroupHost &g, int sr
     cudaError_t e = cudaMemsetAsync(c->scratch + g.persist_off, 0, g.persist_bytes, stream);
     if (e != cudaSuccess) return e;
     const int noise = group_noise(c, g);
+    if (g.q == 7) {
+        if (g.storage == LBM_F32)
+            return launch_persistent_q7_f32(g.model, g.vec, noise, a, p, g.blocks, g.warps, stream);
+        if (g.storage == LBM_F16_SHIFTED)
+            return launch_persistent_q7_f16(g.model, g.vec, noise, a, p, g.blocks, g.warps, stream);
+        return launch_persistent_q7_bf16(g.model, g.vec, noise, a, p, g.blocks, g.warps, stream);
+    }
     if (g.storage == LBM_F32) return launch_persistent_f32(g.model, g.vec, noise, a, p, g.blocks, g.warps, stream);
     if (g.storage == LBM_F16_SHIFTED)
         return launch_persistent_f16(g.model, g.vec, noise, a, p, g.blocks, g.warps, stream);

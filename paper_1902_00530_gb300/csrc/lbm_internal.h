@@ -14,14 +14,21 @@ cudaError_t launch_step_f16(int model, int kind, int vec, bool sample, int noise
                             int warps, cudaStream_t stream);
 cudaError_t launch_step_bf16(int model, int kind, int vec, bool sample, int noise, const StepArgs &a, int blocks,
                              int warps, cudaStream_t stream);
-// the persistent launch of the direct D2Q9 kernel over `p.nsteps` steps
-// (lbm_step_persistent.cuh); step_blocks = blocks of the per-step grid
+// the persistent launch of the direct kernels over `p.nsteps` steps
+// (lbm_step_persistent.cuh), D2Q9 and D2Q7 (q7_); step_blocks = blocks of
+// the per-step grid
 cudaError_t launch_persistent_f32(int model, int vec, int noise, const StepArgs &a, const PersistArgs &p,
                                   int step_blocks, int warps, cudaStream_t stream);
 cudaError_t launch_persistent_f16(int model, int vec, int noise, const StepArgs &a, const PersistArgs &p,
                                   int step_blocks, int warps, cudaStream_t stream);
 cudaError_t launch_persistent_bf16(int model, int vec, int noise, const StepArgs &a, const PersistArgs &p,
                                    int step_blocks, int warps, cudaStream_t stream);
+cudaError_t launch_persistent_q7_f32(int model, int vec, int noise, const StepArgs &a, const PersistArgs &p,
+                                     int step_blocks, int warps, cudaStream_t stream);
+cudaError_t launch_persistent_q7_f16(int model, int vec, int noise, const StepArgs &a, const PersistArgs &p,
+                                     int step_blocks, int warps, cudaStream_t stream);
+cudaError_t launch_persistent_q7_bf16(int model, int vec, int noise, const StepArgs &a, const PersistArgs &p,
+                                      int step_blocks, int warps, cudaStream_t stream);
 cudaError_t launch_observe_f32(int vec, const StepArgs &a, int blocks, int warps, cudaStream_t stream);
 cudaError_t launch_observe_f16(int vec, const StepArgs &a, int blocks, int warps, cudaStream_t stream);
 cudaError_t launch_observe_bf16(int vec, const StepArgs &a, int blocks, int warps, cudaStream_t stream);

@@ -5,4 +5,4 @@
 #include "lbm_step_persistent.cuh"
 
 LBM_INSTANTIATE_STORAGE(lbm::ST_F16, f16)
-LBM_INSTANTIATE_PERSISTENT(lbm::ST_F16, f16)
+LBM_INSTANTIATE_PERSISTENT(9, lbm::ST_F16, f16)

@@ -2,8 +2,9 @@
 //
 // The paper advances many independent lattices per parameter point (App.
 // C.3-C.4); each of their steps is the App. A.2 update, here the body of the
-// direct kernel (direct_strip, lbm_step.cuh) unchanged.  One persistent launch
-// runs `nsteps` consecutive steps, none of them a sample step, of every
+// direct kernel of the group's lattice unchanged (direct_strip, lbm_step.cuh,
+// for D2Q9; direct_strip_q7, lbm_step_q7.cuh, for D2Q7).  One persistent
+// launch runs `nsteps` consecutive steps, none of them a sample step, of every
 // lattice of a launch group.
 //
 // Work items are the blocks of the per-step grid, one per step: item (j, b) is
@@ -110,7 +111,18 @@ __device__ __forceinline__ void persist_setup(const StepArgs &a, const PersistAr
 #endif
 template <int MODEL> constexpr int persist_max_regs() { return MODEL == MODEL_MIPS ? 128 : LBM_PERSIST_REGS; }
 
-template <int MODEL, int ST, int VEC, int NOISE>
+// The strip update of lattice Q (9: D2Q9, 7: D2Q7); the D2Q7 form is defined
+// beside its direct kernel.
+template <int Q> struct PersistStrip;
+template <> struct PersistStrip<9> {
+    template <int MODEL, int ST, int VEC, int NOISE>
+    static __device__ __forceinline__ void run(const StepArgs &a, const LatDesc *dp, int s, int src, uint32_t t)
+    {
+        direct_strip<MODEL, ST, VEC, false, NOISE>(a, dp, s, src, t);
+    }
+};
+
+template <int Q, int MODEL, int ST, int VEC, int NOISE>
 __global__ void __maxnreg__(persist_max_regs<MODEL>()) step_persistent_kernel(const StepArgs a, const PersistArgs p)
 {
     __shared__ PersistItem it;
@@ -167,7 +179,8 @@ __global__ void __maxnreg__(persist_max_regs<MODEL>()) step_persistent_kernel(co
         if (it.abort) return;  // block-uniform
         const int s = it.s0 + warp;
         const int jj = p.retime ? 0 : it.j;  // the timing form repeats step 0: same reads, same values written
-        if (s < it.s1) direct_strip<MODEL, ST, VEC, false, NOISE>(a, dp, s, a.src ^ (jj & 1), *a.t_ptr + a.k + (uint32_t)jj);
+        if (s < it.s1)
+            PersistStrip<Q>::template run<MODEL, ST, VEC, NOISE>(a, dp, s, a.src ^ (jj & 1), *a.t_ptr + a.k + (uint32_t)jj);
         __syncthreads();  // every strip of the block is stored
         if (threadIdx.x == 0) {
             // publish the block's strips per strip row: one fence orders the
@@ -187,11 +200,11 @@ __global__ void __maxnreg__(persist_max_regs<MODEL>()) step_persistent_kernel(co
 // Launch with as many blocks as fit on the GPU at once (fewer if there are
 // fewer items); blocks that start later take items as they come.
 // step_blocks: blocks of the per-step grid (pg[npg]).
-template <int MODEL, int ST, int VEC, int NOISE>
+template <int Q, int MODEL, int ST, int VEC, int NOISE>
 static cudaError_t launch_persistent_one(const StepArgs &a, const PersistArgs &p, int step_blocks, int warps,
                                          cudaStream_t stream)
 {
-    auto kern = step_persistent_kernel<MODEL, ST, VEC, NOISE>;
+    auto kern = step_persistent_kernel<Q, MODEL, ST, VEC, NOISE>;
     int dev = 0, sms = 0, per_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -203,50 +216,50 @@ static cudaError_t launch_persistent_one(const StepArgs &a, const PersistArgs &p
     return cudaGetLastError();
 }
 
-template <int MODEL, int ST, int VEC>
+template <int Q, int MODEL, int ST, int VEC>
 static cudaError_t launch_persistent_mv(int noise, const StepArgs &a, const PersistArgs &p, int step_blocks,
                                         int warps, cudaStream_t stream)
 {
-    if (noise == 0) return launch_persistent_one<MODEL, ST, VEC, 0>(a, p, step_blocks, warps, stream);
-    if (noise == 1) return launch_persistent_one<MODEL, ST, VEC, 1>(a, p, step_blocks, warps, stream);
-    return launch_persistent_one<MODEL, ST, VEC, 2>(a, p, step_blocks, warps, stream);
+    if (noise == 0) return launch_persistent_one<Q, MODEL, ST, VEC, 0>(a, p, step_blocks, warps, stream);
+    if (noise == 1) return launch_persistent_one<Q, MODEL, ST, VEC, 1>(a, p, step_blocks, warps, stream);
+    return launch_persistent_one<Q, MODEL, ST, VEC, 2>(a, p, step_blocks, warps, stream);
 }
 
-template <int MODEL, int ST>
+template <int Q, int MODEL, int ST>
 static cudaError_t launch_persistent_m(int vec, int noise, const StepArgs &a, const PersistArgs &p, int step_blocks,
                                        int warps, cudaStream_t stream)
 {
     switch (vec) {
-    case 1: return launch_persistent_mv<MODEL, ST, 1>(noise, a, p, step_blocks, warps, stream);
-    case 2: return launch_persistent_mv<MODEL, ST, 2>(noise, a, p, step_blocks, warps, stream);
-    case 4: return launch_persistent_mv<MODEL, ST, 4>(noise, a, p, step_blocks, warps, stream);
+    case 1: return launch_persistent_mv<Q, MODEL, ST, 1>(noise, a, p, step_blocks, warps, stream);
+    case 2: return launch_persistent_mv<Q, MODEL, ST, 2>(noise, a, p, step_blocks, warps, stream);
+    case 4: return launch_persistent_mv<Q, MODEL, ST, 4>(noise, a, p, step_blocks, warps, stream);
     case 8:
-        if constexpr (ST != ST_F32) return launch_persistent_mv<MODEL, ST, 8>(noise, a, p, step_blocks, warps, stream);
+        if constexpr (ST != ST_F32) return launch_persistent_mv<Q, MODEL, ST, 8>(noise, a, p, step_blocks, warps, stream);
         return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
     }
 }
 
-template <int ST>
+template <int Q, int ST>
 static cudaError_t launch_persistent_storage(int model, int vec, int noise, const StepArgs &a, const PersistArgs &p,
                                              int step_blocks, int warps, cudaStream_t stream)
 {
     switch (model) {
-    case MODEL_PASSIVE: return launch_persistent_m<MODEL_PASSIVE, ST>(vec, noise, a, p, step_blocks, warps, stream);
-    case MODEL_MIPS: return launch_persistent_m<MODEL_MIPS, ST>(vec, noise, a, p, step_blocks, warps, stream);
-    case MODEL_CIL: return launch_persistent_m<MODEL_CIL, ST>(vec, noise, a, p, step_blocks, warps, stream);
+    case MODEL_PASSIVE: return launch_persistent_m<Q, MODEL_PASSIVE, ST>(vec, noise, a, p, step_blocks, warps, stream);
+    case MODEL_MIPS: return launch_persistent_m<Q, MODEL_MIPS, ST>(vec, noise, a, p, step_blocks, warps, stream);
+    case MODEL_CIL: return launch_persistent_m<Q, MODEL_CIL, ST>(vec, noise, a, p, step_blocks, warps, stream);
     default: return cudaErrorInvalidValue;
     }
 }
 
 }  // namespace lbm
 
-#define LBM_INSTANTIATE_PERSISTENT(ST, SUFFIX)                                                              \
+#define LBM_INSTANTIATE_PERSISTENT(Q, ST, SUFFIX)                                                           \
     namespace lbm {                                                                                         \
     cudaError_t launch_persistent_##SUFFIX(int model, int vec, int noise, const StepArgs &a,                 \
                                            const PersistArgs &p, int step_blocks, int warps,                 \
                                            cudaStream_t stream)                                              \
     {                                                                                                       \
-        return launch_persistent_storage<ST>(model, vec, noise, a, p, step_blocks, warps, stream);           \
+        return launch_persistent_storage<Q, ST>(model, vec, noise, a, p, step_blocks, warps, stream);        \
     }                                                                                                       \
     }

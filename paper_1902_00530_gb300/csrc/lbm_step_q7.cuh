@@ -17,7 +17,7 @@
 // every pull is a vector load plus at most one neighbour shuffle, as on D2Q9.
 #pragma once
 
-#include "lbm_step.cuh"
+#include "lbm_step_persistent.cuh"
 
 namespace lbm {
 
@@ -310,15 +310,15 @@ __device__ __forceinline__ void q7_row(Q7Walk<VEC> &w, int y, const typename Sto
     }
 }
 
+// One warp's strip s (< nsx nsy) of D2Q7 lattice dp for the step at time t,
+// read from buffer `src` and written to the other: the body of the direct
+// D2Q7 kernel, shared by the per-step launch and the persistent launch.
 template <int MODEL, int ST, int VEC, bool SAMPLE, int NOISE>
-__global__ void __launch_bounds__(256) step_kernel_q7(const StepArgs a)
+__device__ __forceinline__ void direct_strip_q7(const StepArgs &a, const LatDesc *dp, int s, int src_buf, uint32_t t)
 {
     using T = typename Store<ST>::T;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const LatDesc *dp = a.desc + find_lattice(a.desc, a.nlat, blockIdx.x);
-    const int nsx = dp->nsx, nsy = dp->nsy;
-    const int s = (blockIdx.x - dp->block_begin) * (blockDim.x >> 5) + warp;
-    if (s >= nsx * nsy) return;
+    const int lane = threadIdx.x & 31;
+    const int nsx = dp->nsx;
     const int nx = dp->nx, ny = dp->ny, pitch = dp->pitch, rows = dp->rows;
     const SiteParams d = load_params(dp);
     const int sx = s % nsx, sy = s / nsx;
@@ -328,11 +328,10 @@ __global__ void __launch_bounds__(256) step_kernel_q7(const StepArgs a)
     // rows and ny are even, so every strip starts on an even row and holds whole (even, odd) pairs
     const int y_begin = sy * rows, y_end = min(y_begin + rows, ny);
     const size_t plane = (size_t)ny * pitch;
-    const T *src = reinterpret_cast<const T *>(dp->f[a.src]);
-    T *dst = reinterpret_cast<T *>(dp->f[a.src ^ 1]);
+    const T *src = reinterpret_cast<const T *>(dp->f[src_buf]);
+    T *dst = reinterpret_cast<T *>(dp->f[src_buf ^ 1]);
     const Shift3 sh = load_shift(dp);
     const uint32_t id = (uint32_t)dp->id;
-    const uint32_t t = *a.t_ptr + a.k;
     const bool noise = NOISE == 2 ? d.sigma_q > 0.f : NOISE == 1;  // as in step_kernel
     double *rowp = dp->rowp + (size_t)sx * ny;
 
@@ -359,6 +358,24 @@ __global__ void __launch_bounds__(256) step_kernel_q7(const StepArgs a)
     }
     if constexpr (SAMPLE) observe_flush<VEC>(dp->colp, dp->scal, nx, s, sy, x0, valid, w.col, w.acc, lane);
 }
+
+template <int MODEL, int ST, int VEC, bool SAMPLE, int NOISE>
+__global__ void __launch_bounds__(256) step_kernel_q7(const StepArgs a)
+{
+    const LatDesc *dp = a.desc + find_lattice(a.desc, a.nlat, blockIdx.x);
+    const int s = (blockIdx.x - dp->block_begin) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (s >= dp->nsx * dp->nsy) return;  // whole warp leaves together
+    direct_strip_q7<MODEL, ST, VEC, SAMPLE, NOISE>(a, dp, s, a.src, *a.t_ptr + a.k);
+}
+
+// The D2Q7 strip update of the persistent launch (lbm_step_persistent.cuh).
+template <> struct PersistStrip<7> {
+    template <int MODEL, int ST, int VEC, int NOISE>
+    static __device__ __forceinline__ void run(const StepArgs &a, const LatDesc *dp, int s, int src, uint32_t t)
+    {
+        direct_strip_q7<MODEL, ST, VEC, false, NOISE>(a, dp, s, src, t);
+    }
+};
 
 template <int ST, int VEC>
 __global__ void __launch_bounds__(256) observe_kernel_q7(const StepArgs a)

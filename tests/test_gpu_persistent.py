@@ -4,10 +4,11 @@ A persistent launch runs many steps of a launch group in one kernel, each step
 the same direct-kernel update of App. A.2, so every state, sampled observable
 series and on-demand record must be bitwise those of the per-step launches:
 across the three closures, the noise forms (none, all, mixed within a group),
-storage types, launch shapes (blocks spanning strip rows, lattices of one or
-two strip rows, a staged shape the persistent launch leaves alone), lattice
-groups smaller and larger than the batch, sample steps at every phase of a
-persistent stretch, with and without CUDA graphs.
+storage types, both lattices (D2Q9 and the paper's D2Q7), launch shapes
+(blocks spanning strip rows, lattices of one or two strip rows, a staged shape
+the persistent launch leaves alone), lattice groups smaller and larger than
+the batch, sample steps at every phase of a persistent stretch, with and
+without CUDA graphs.
 """
 import numpy as np
 import pytest
@@ -29,12 +30,21 @@ MIXED = [(64, 64, "CIL_RHO1", {}, W.INIT_CONFIG2),
          (64, 16, "PASSIVE", {}, W.INIT_CONFIG1)]
 
 
+# the paper's D2Q7 lattice (ny even), with one D2Q9 lattice in the same batch
+MIXED7 = [(64, 32, "CIL_Q7_RHO1", {}, W.INIT_CONFIG2, "d2q7"),
+          (96, 40, "MIPS_Q7_RHO1", dict(C=0.2), W.INIT_CONFIG1, "d2q7"),
+          (136, 24, "CIL_Q7_RHO1", dict(B=0.05, sigma=0.0), dict(W.INIT_CONFIG2, rho_mean=0.7), "d2q7"),
+          (72, 56, "PASSIVE", dict(sigma=0.01), W.INIT_CONFIG2, "d2q7"),
+          (180, 60, "CIL_Q7_PAPER", {}, dict(W.INIT_PAPER_CIL, rho_mean=0.185), "d2q7"),
+          (64, 48, "CIL_RHO1", {}, W.INIT_CONFIG2, "d2q9")]
+
+
 def _run(storage, persistent, tuning, l2_mib=1, graphs=True, every=9, calls=(37, 28), cfg=MIXED):
     from paper_1902_00530_gb300 import Lattice, Simulation
     lats, mods, prms, specs = [], [], [], []
-    for k, (nx, ny, name, over, init) in enumerate(cfg):
+    for k, (nx, ny, name, over, init, *vs) in enumerate(cfg):
         model, d = split_preset(name, **over)
-        lats.append(Lattice(nx, ny, storage, k))
+        lats.append(Lattice(nx, ny, storage, k, vs[0] if vs else "d2q9"))
         mods.append(model)
         prms.append(d)
         specs.append(init)
@@ -75,6 +85,17 @@ def test_persistent_equals_per_step_launches(storage, tuning):
         assert sum(got["launches"]) < sum(ref["launches"])
     else:               # staged groups are left to the per-step launches
         assert got["launches"] == ref["launches"]
+
+
+@pytest.mark.parametrize("tuning", [(1, 8, 4, 0), (4, 8, 4, 0), (2, 16, 8, 0), (1, 32, 1, 0)])
+@pytest.mark.parametrize("storage", ["f32", "bf16s"])
+def test_persistent_d2q7_equals_per_step_launches(storage, tuning):
+    """The paper's D2Q7 lattice: its direct kernel's strip update in the
+    persistent launch, beside a D2Q9 group of the same batch."""
+    ref = _run(storage, False, tuning, cfg=MIXED7)
+    got = _run(storage, True, tuning, cfg=MIXED7)
+    _assert_same(got, ref)
+    assert sum(got["launches"]) < sum(ref["launches"])
 
 
 @pytest.mark.parametrize("graphs", [True, False])
