@@ -252,3 +252,27 @@ def test_binding_names_the_unsupported_lattice(lib):
     with pytest.raises(LBMError) as e:
         Simulation([Lattice(65530, 8000, "f16s")], ["mips"], [dict(tau=1.0, C=6.0, rho_star=1.6, u_max=0.3)])
     assert e.value.status == 6 and "staged kernel" in str(e.value)
+
+
+def test_persistent_applies_to_direct_shapes_of_both_lattices(lib):
+    """lbm_get_persistent under mode 1: groups on a direct kernel (D2Q9 and
+    the paper's D2Q7) take persistent launches, staged groups do not; mode 0
+    turns them off and mode 2 waits for the tuner.  Host only, no GPU."""
+    from paper_1902_00530_gb300 import _abi
+    on = ctypes.c_int32(-1)
+    for vs, ny in ((0, 16), (1, 16)):
+        ctx = ctypes.c_void_p()
+        lat = _lat(64, ny, 0, 0, vs)
+        prm = _prm(tau=1.0, sigma=0.01, A=0.068, B=0.3)
+        assert lib.lbm_create(ctypes.byref(lat), _abi.MODELS["cil"], ctypes.byref(prm), ctypes.byref(ctx)) == 0
+        assert lib.lbm_set_persistent(ctx, 1, 0) == 0
+        assert lib.lbm_set_tuning(ctx, 1, 2, 8, 4, 0) == 0          # direct
+        assert lib.lbm_get_persistent(ctx, 0, ctypes.byref(on)) == 0 and on.value == 1
+        assert lib.lbm_set_tuning(ctx, 1, 2, 8, 4, 3) == 0          # staged
+        assert lib.lbm_get_persistent(ctx, 0, ctypes.byref(on)) == 0 and on.value == 0
+        assert lib.lbm_set_tuning(ctx, 1, 2, 8, 4, 0) == 0
+        assert lib.lbm_set_persistent(ctx, 2, 0) == 0               # the tuner has not chosen yet
+        assert lib.lbm_get_persistent(ctx, 0, ctypes.byref(on)) == 0 and on.value == 0
+        assert lib.lbm_set_persistent(ctx, 0, 0) == 0
+        assert lib.lbm_get_persistent(ctx, 0, ctypes.byref(on)) == 0 and on.value == 0
+        lib.lbm_destroy(ctx)
